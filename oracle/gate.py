@@ -1,0 +1,128 @@
+"""Oracle for the Risky Gate (Sec. II-B and Sec. V-D), plain numpy in fp64.
+
+TEST INFRASTRUCTURE ONLY: used by the tests and the benchmark's CPU baseline,
+never by the library.
+
+What the paper fixes:
+  * the CPU cost model is alpha*N*log N or alpha*N*K (Sec. II-B); the fitted
+    full-sort form is T_cpu(N) = a*N*log2(N) + b (Sec. V-D);
+  * key-only transfer is T_tx(N) = c*N + d (Sec. V-D), here in bytes so that a
+    wider row costs more (Sec. II-B, transfer bytes B);
+  * C_gpu = Transfer + Kernel + Post-processing (Sec. II-B), post-processing
+    being result return plus late materialization (Sec. V-D);
+  * offload only when C_cpu - C_gpu exceeds a threshold, the gate margin in ms
+    (Sec. II-B, Sec. IV "gate margin");
+  * the break-even N* solves T_cpu(N*) = T_tx(N*) + T_gpu(N*) (Sec. V-D).
+
+Readings where it is open (kept identical in the library's contract):
+  * fits are ordinary least squares y = slope*x + intercept on the given
+    points, in the centred closed form of the normal equations;
+  * Top-K fits both CPU forms, x = N*log2(N) and x = N*K, and keeps the one
+    with the smaller residual sum of squares (N*log2 N on a tie);
+  * probe CPU cost uses x = N*M, M the expected candidates per probe;
+  * kernel time is linear in N (e*N + f), post-processing linear in the
+    number of returned rows (g*out + h);
+  * "exceeds" is strict: offload iff C_cpu - C_gpu > margin;
+  * N* is the smallest integer N in [1, 2^34] with C_cpu(N) - C_gpu(N) >
+    margin, by bisection; 1 if that already holds at N = 1, 0 ("none") if it
+    does not hold at 2^34.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+TOPK, PROBE = 0, 1
+CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
+N_STAR_HI = 1 << 34
+
+
+def ols(x, y):
+    """Least-squares slope and intercept of y = slope*x + intercept."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    xm = x.mean()
+    ym = y.mean()
+    sxx = float(np.sum((x - xm) * (x - xm)))
+    sxy = float(np.sum((x - xm) * (y - ym)))
+    slope = sxy / sxx if sxx > 0.0 else 0.0
+    return slope, float(ym - slope * xm)
+
+
+def rss(x, y, slope, intercept):
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    r = y - (slope * x + intercept)
+    return float(np.sum(r * r))
+
+
+def cpu_x(form, n, k_or_m):
+    n = float(n)
+    if form == CPU_NLOGN:
+        return n * math.log2(n) if n > 0 else 0.0
+    return n * float(k_or_m)
+
+
+class Model:
+    def __init__(self, op, cpu_form, a, b, c, d, e, f, g, h, margin_ms):
+        self.op, self.cpu_form = op, cpu_form
+        self.a, self.b, self.c, self.d = a, b, c, d
+        self.e, self.f, self.g, self.h = e, f, g, h
+        self.margin_ms = margin_ms
+
+
+def calibrate(op, n, k_or_m, tx_bytes, out_rows, t_cpu, t_tx, t_ker, t_post, margin_ms=0.0):
+    """Fit every cost term from measured samples (all times in ms)."""
+    if op == TOPK:
+        xs = {f: [cpu_x(f, ni, ki) for ni, ki in zip(n, k_or_m)] for f in (CPU_NLOGN, CPU_NK)}
+        fits = {f: ols(xs[f], t_cpu) for f in xs}
+        res = {f: rss(xs[f], t_cpu, *fits[f]) for f in xs}
+        form = CPU_NLOGN if res[CPU_NLOGN] <= res[CPU_NK] else CPU_NK
+    else:
+        form = CPU_NM
+        fits = {form: ols([cpu_x(form, ni, mi) for ni, mi in zip(n, k_or_m)], t_cpu)}
+    a, b = fits[form]
+    c, d = ols(tx_bytes, t_tx)
+    e, f = ols(n, t_ker)
+    g, h = ols(out_rows, t_post)
+    return Model(op, form, a, b, c, d, e, f, g, h, margin_ms)
+
+
+def costs(m: Model, n, k_or_m, tx_bytes, out_rows):
+    c_cpu = m.a * cpu_x(m.cpu_form, n, k_or_m) + m.b
+    c_tx = m.c * float(tx_bytes) + m.d
+    c_ker = m.e * float(n) + m.f
+    c_post = m.g * float(out_rows) + m.h
+    return c_cpu, c_tx, c_ker, c_post
+
+
+def decide(m: Model, n, k_or_m, tx_bytes, out_rows):
+    c_cpu, c_tx, c_ker, c_post = costs(m, n, k_or_m, tx_bytes, out_rows)
+    return (c_cpu - (c_tx + c_ker + c_post)) > m.margin_ms
+
+
+def gain(m: Model, n, k_or_m, bytes_per_row, out_per_row, out_fixed):
+    """C_cpu - C_gpu - margin at size n, with transfer bytes and returned rows
+    growing with n as the query describes."""
+    out = out_fixed if out_fixed is not None else out_per_row * n
+    if m.op == TOPK and out_fixed is not None:
+        out = min(out_fixed, n)
+    c_cpu, c_tx, c_ker, c_post = costs(m, n, k_or_m, bytes_per_row * n, out)
+    return c_cpu - (c_tx + c_ker + c_post) - m.margin_ms
+
+
+def n_star(m: Model, k_or_m, bytes_per_row, out_per_row=0.0, out_fixed=None):
+    g = lambda nn: gain(m, nn, k_or_m, bytes_per_row, out_per_row, out_fixed)
+    if g(1) > 0.0:
+        return 1
+    if not g(N_STAR_HI) > 0.0:
+        return 0
+    lo, hi = 1, N_STAR_HI
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if g(mid) > 0.0:
+            hi = mid
+        else:
+            lo = mid
+    return hi

@@ -1,0 +1,88 @@
+"""Pins for the gate oracle (Sec. II-B cost models and decision; Sec. V-D
+least-squares fits and break-even N*): exact recovery of known coefficients,
+a closed-form N* for the linear CPU model, the defining sign change at N*,
+and the strictness of "exceeds"."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gate
+
+
+def _samples(a, b, c, d, e, f, g, h, form, bytes_per_row=8):
+    n = np.unique(np.floor(np.logspace(3, 8, 20)).astype(np.int64))
+    kk = np.array([10, 100, 1000, 37] * 5, dtype=np.int64)[: n.shape[0]]
+    if form == gate.CPU_NLOGN:
+        t_cpu = a * n * np.log2(n) + b
+    else:
+        t_cpu = a * n * kk + b
+    tx = bytes_per_row * n
+    out = np.minimum(kk, n)
+    return n, kk, tx, out, t_cpu, c * tx + d, e * n + f, g * out + h
+
+
+@pytest.mark.parametrize("form", [gate.CPU_NLOGN, gate.CPU_NK])
+def test_recovers_known_coefficients(form):
+    co = dict(a=3.1e-6, b=0.25, c=2.5e-9, d=0.04, e=1.5e-7, f=0.01, g=3e-6, h=0.002)
+    n, kk, tx, out, t_cpu, t_tx, t_ker, t_post = _samples(**co, form=form)
+    m = gate.calibrate(gate.TOPK, n, kk, tx, out, t_cpu, t_tx, t_ker, t_post)
+    assert m.cpu_form == form
+    for name, want in co.items():
+        assert math.isclose(getattr(m, name), want, rel_tol=1e-9, abs_tol=1e-12), name
+
+
+def test_linear_model_closed_form_n_star():
+    # T_cpu = a*N*K + b, C_gpu = (c*w + e)*N + (d + f + g*K + h): the root is
+    # N = (d + f + g*K + h + margin - b) / (a*K - c*w - e).
+    m = gate.Model(gate.TOPK, gate.CPU_NK, a=1e-6, b=0.0, c=1e-8, d=2.0, e=1e-7, f=0.5,
+                   g=0.0, h=0.25, margin_ms=5.0)
+    k, w = 100, 8
+    root = (2.0 + 0.5 + 0.25 + 5.0 - 0.0) / (1e-6 * k - 1e-8 * w - 1e-7)
+    ns = gate.n_star(m, k, w, out_fixed=k)
+    assert ns == math.floor(root) + 1
+    assert gate.gain(m, ns, k, w, 0.0, k) > 0.0 >= gate.gain(m, ns - 1, k, w, 0.0, k)
+
+
+def test_nlogn_bisection_defining_property():
+    m = gate.Model(gate.TOPK, gate.CPU_NLOGN, a=2e-6, b=0.01, c=2e-9, d=0.05, e=1e-7,
+                   f=0.02, g=1e-6, h=0.01, margin_ms=0.0)
+    for margin in (0.0, 5.0, 10.0):
+        m.margin_ms = margin
+        ns = gate.n_star(m, 100, 8, out_fixed=100)
+        assert 1 < ns < gate.N_STAR_HI
+        assert gate.gain(m, ns, 100, 8, 0.0, 100) > 0.0 >= gate.gain(m, ns - 1, 100, 8, 0.0, 100)
+    # a larger margin moves the switching point up (Sec. IV, gate margin)
+    ns0 = gate.n_star(gate.Model(**{**m.__dict__, "margin_ms": 0.0}), 100, 8, out_fixed=100)
+    ns10 = gate.n_star(gate.Model(**{**m.__dict__, "margin_ms": 10.0}), 100, 8, out_fixed=100)
+    assert ns10 > ns0
+
+
+def test_n_star_edges():
+    never = gate.Model(gate.TOPK, gate.CPU_NK, a=0.0, b=0.0, c=1.0, d=1.0, e=0.0, f=0.0,
+                       g=0.0, h=0.0, margin_ms=0.0)
+    assert gate.n_star(never, 10, 8, out_fixed=10) == 0
+    always = gate.Model(gate.TOPK, gate.CPU_NK, a=1.0, b=100.0, c=0.0, d=0.0, e=0.0, f=0.0,
+                        g=0.0, h=0.0, margin_ms=0.0)
+    assert gate.n_star(always, 10, 8, out_fixed=10) == 1
+
+
+def test_decision_is_strict():
+    # dyadic values so the sums are exact: C_cpu - C_gpu == margin exactly
+    m = gate.Model(gate.PROBE, gate.CPU_NM, a=0.5, b=1.0, c=0.25, d=0.5, e=0.125, f=0.0,
+                   g=0.0, h=0.0, margin_ms=2.0)
+    # n=8, M=2: c_cpu = 0.5*16+1 = 9; c_tx = 0.25*8+0.5 = 2.5; c_ker = 1; gpu = 3.5 -> gain 5.5
+    assert gate.decide(m, 8, 2, 8, 0)
+    m.margin_ms = 5.5
+    assert not gate.decide(m, 8, 2, 8, 0)
+    m.margin_ms = 5.25
+    assert gate.decide(m, 8, 2, 8, 0)
+
+
+def test_probe_fit():
+    n = np.array([1e3, 1e4, 1e5, 1e6, 1e7])
+    mm = np.array([1.1, 1.9, 2.5, 1.5, 3.0])
+    t_cpu = 4e-6 * n * mm + 0.3
+    m = gate.calibrate(gate.PROBE, n, mm, 8 * n, n, t_cpu, 1e-9 * 8 * n + 0.01, 1e-8 * n, 1e-9 * n)
+    assert m.cpu_form == gate.CPU_NM
+    assert math.isclose(m.a, 4e-6, rel_tol=1e-9) and math.isclose(m.b, 0.3, rel_tol=1e-9)
