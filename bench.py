@@ -1,0 +1,284 @@
+"""Benchmark of the key-only Top-K offload (and, as they land, the join probe,
+the batched executor and the gated serving loop) on GB300.
+
+One step = one Top-K query, ORDER BY key DESC LIMIT K, over N = 2^28 int64
+keys drawn uniformly over the full int64 range (K = 1000 by default), the
+Top-K-at-scale workload.  ``value`` is keys/s with the keys resident in HBM
+(one cooperative kernel launch per step); ``e2e`` is the same query through
+the public blocking call with the keys in pinned host memory, so the key-only
+H2D copy and the D2H of the K (key, row-id) results are inside the timed
+region.  The keys (2 GiB) are larger than L2 (129 MB), so no flush is needed
+between steps.
+
+``--impl reference`` times the CPU oracle (a full stable sort then the first
+K, single thread) on a bounded sample of the same workload instead.
+Under torchrun each rank runs an independent replica on its own GPU ("replicas
+only": the selection needs no exchange); rank 0 prints the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Top-K Gkeys/s & join probes/s (% HBM peak); batched vs per-query; gated P99"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(n_full: int, k: int, seconds: float = 12.0):
+    """The oracle as it stands, single thread, on a bounded sample of the
+    workload (the first 2^22 keys of the same column), scaled to keys/s."""
+    import oracle
+    from paper_2601_19911_gb300 import datagen
+    ns = 1 << 22
+    keys = datagen.topk_keys(ns, "uniform", "i64", seed=1)
+    oracle.topk(keys[:1000], k, oracle.DESC)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.topk(keys, k, oracle.DESC)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > seconds:
+            break
+    per = el / reps
+    return {"value": ns / per / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} x oracle Top-K (stable sort, first K={k}) of {ns} uniform int64 keys, "
+                      f"1 thread; {per * 1e3:.1f} ms each"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    k = args.k
+    import oracle
+    from paper_2601_19911_gb300 import datagen
+    ns = 1 << 22
+    keys = datagen.topk_keys(ns, "uniform", "i64", seed=1)
+    for _ in range(args.warmup):
+        oracle.topk(keys, k, oracle.DESC)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.topk(keys, k, oracle.DESC)
+    el = time.perf_counter() - t0
+    per = el / args.steps
+    v = ns / per / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gkeys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"topk_i64_uniform_n{ns}_k{k}_desc (bounded sample of the 2^28 workload)",
+                       "n": ns, "k": k},
+            "cpu_baseline": {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps of the oracle on {ns} keys"},
+            "e2e": {"value": v, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2601_19911_gb300 import datagen, olap
+
+    n, k = 1 << args.log2n, args.k
+    ctx = olap.Context(torch.cuda.current_device())
+    keys = datagen.topk_keys(n, "uniform", "i64", seed=1)
+    dk = torch.from_numpy(keys).cuda()
+    ok = torch.empty(k, dtype=torch.int64, device="cuda")
+    orow = torch.empty(k, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.ExternalStream(ctx.stream)
+
+    # -- kernel-only: device-resident keys, one launch per step ----------------
+    for _ in range(max(3, args.warmup)):
+        ctx.topk_async(dk, k, olap.DESC, ok, orow)
+    ctx.sync()
+    _barrier(world)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            ctx.topk_async(dk, k, olap.DESC, ok, orow)
+            evs[i][1].record(stream)
+        end.record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+    total_ms = start.elapsed_time(end)
+    per_launch = [a.elapsed_time(b) for a, b in evs]
+    total_ms = _max_over_ranks(total_ms, world)
+    ms = total_ms / args.steps
+    value = world * n / (ms * 1e-3) / 1e9
+
+    # -- end to end through the public blocking call, pinned host keys -----------
+    hk = torch.from_numpy(keys).pin_memory()
+    hok = torch.empty(k, dtype=torch.int64).pin_memory()
+    horow = torch.empty(k, dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        ctx.topk(hk, k, olap.DESC, out_keys=hok, out_rowids=horow)
+    _barrier(world)
+    e2e_steps = max(3, min(args.steps, args.e2e_steps))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.topk(hk, k, olap.DESC, out_keys=hok, out_rowids=horow)
+    e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    e2e_value = world * n / e2e_s / 1e9
+
+    peak, peak_kind = _peaks()
+    algo_bytes = n * 8 + 24 * k
+    kern_ms = float(np.mean(per_launch))
+    achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"topk_i64_uniform_n2^{args.log2n}_k{k}_desc", "n": n, "k": k,
+                   "order": "desc", "rowids": "implicit", "l2": "inputs larger than L2 (2 GiB keys)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": args.traffic, "peak_kind": peak_kind,
+                     "kernel": "olap::topk_kernel", "algorithmic_bytes_per_launch": algo_bytes,
+                     "kernel_ms": kern_ms},
+        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": k * 12 + 4, "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n, k)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=1000)
+    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the timed kernel, if captured")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,124 @@
+/*
+ * olap.h -- C ABI of the GB300 key-only OLAP offload library.
+ *
+ * The library implements the two execution-layer primitives the paper
+ * offloads to the GPU and the cost gate that decides when to offload
+ * ("GPU-Augmented OLAP Execution Engine: GPU Offloading", arXiv 2601.19911):
+ *
+ *   - Top-K selection, ORDER BY key LIMIT K (Sec. III-A): key-only input,
+ *     radix-based selection, the Top-K row pointers returned in order.
+ *   - Key-based hash join build and probe (Sec. III-B): a key-only hash table,
+ *     parallel probing, the set of matched (probe, build) row pointers returned
+ *     for late materialization on the host (Sec. II-C).
+ *   - The Risky Gate (Sec. II-B, Sec. V-D): fitted CPU / transfer / kernel /
+ *     post-processing cost models, the offload decision and the break-even N*.
+ *
+ * Key-only contract (Sec. II-C): only (key, row-id) crosses the host-device
+ * link; row-ids are uint32 and may be implicit (NULL => row-id = index), in
+ * which case only the keys cross.  Late materialization is the caller's job.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an olap_status; nothing throws across the ABI.
+ *     olap_last_error() describes the last failure on a context.
+ *   - The caller owns every input and output buffer.  The library owns the
+ *     context, its device scratch, its pinned staging buffers and join tables.
+ *   - Pointers tagged OLAP_MEM_DEVICE must be device memory of the context's
+ *     device; OLAP_MEM_HOST_PINNED must be page-locked host memory;
+ *     OLAP_MEM_HOST may be any host memory (staged through pinned buffers).
+ *   - Keys must be naturally aligned (8 bytes for int64, 4 for float32).
+ *   - Blocking calls return after the result is in the output buffers.
+ *     Calls suffixed _async only enqueue work on the given stream, take device
+ *     pointers only, and report device-side status through a device word.
+ *   - There is no CPU fallback: when no GPU is usable a call fails with
+ *     OLAP_E_CUDA.  The gate only advises; running the CPU path is the
+ *     caller's engine's job.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef OLAP_H
+#define OLAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OLAP_OK = 0,
+    OLAP_E_INVALID = 1,        /* bad argument (null pointer, bad enum, size limit) */
+    OLAP_E_NOMEM = 2,          /* device or pinned allocation failed / budget exceeded */
+    OLAP_E_CUDA = 3,           /* a CUDA runtime call failed (no device, launch error) */
+    OLAP_E_OVERFLOW = 4,       /* output capacity too small; required count reported */
+    OLAP_E_TIMEOUT = 5,        /* a bounded device-side wait expired; context reset */
+    OLAP_E_UNIMPLEMENTED = 6,
+    OLAP_E_DEVICE = 7          /* device-side validation rejected a descriptor */
+} olap_status;
+
+typedef enum { OLAP_KEY_I64 = 0, OLAP_KEY_F32 = 1 } olap_key_type;
+typedef enum { OLAP_ASC = 0, OLAP_DESC = 1 } olap_order;
+typedef enum { OLAP_MEM_HOST = 0, OLAP_MEM_HOST_PINNED = 1, OLAP_MEM_DEVICE = 2 } olap_mem;
+
+typedef struct olap_ctx olap_ctx;
+typedef struct olap_join_table olap_join_table;
+
+/* Context options.  Zero means "library default" for every field. */
+typedef struct {
+    int device;                 /* CUDA device ordinal */
+    void* stream;               /* cudaStream_t to run on; NULL => the context creates one */
+    uint64_t mem_budget_bytes;  /* cap on device scratch + tables held by the context */
+    double margin_ms;           /* gate margin (Sec. IV, gate margin 0/5/10 ms) */
+    int block_threads;          /* threads per CTA for streaming kernels (256/512/1024) */
+    double load_factor;         /* join table load factor in (0, 0.9]; 0 => 0.5 */
+    uint64_t staging_bytes;     /* size of each pinned staging buffer; 0 => 64 MiB */
+} olap_opts;
+
+/* Create a context on opts->device (opts may be NULL for all defaults).
+ * Fails with OLAP_E_CUDA when no CUDA device is usable. */
+olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out);
+void olap_ctx_destroy(olap_ctx* ctx);
+/* Message for the last failed call on ctx (never NULL; "" after success). */
+const char* olap_last_error(const olap_ctx* ctx);
+/* The cudaStream_t the context runs on. */
+void* olap_ctx_stream(const olap_ctx* ctx);
+/* Wait for all work the context enqueued. */
+olap_status olap_ctx_sync(olap_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Top-K selection, ORDER BY key {ASC|DESC} LIMIT k (Sec. III-A; Sec. V-B
+ * names the query form ORDER BY value DESC LIMIT 100).
+ *
+ * keys        n keys of `type` (int64, or float32 ordered by IEEE 754-2019
+ *             totalOrder, so -0 < +0 and NaNs sort outside +-inf by sign),
+ *             in memory `in_where`.
+ * rowids      n uint32 row-ids in the same memory kind, or NULL for
+ *             row-id = index.
+ * order       OLAP_ASC or OLAP_DESC on the key; ties on equal keys are always
+ *             broken by row-id ascending.
+ * out_keys    min(k, n) keys (original bit patterns, same type), in order.
+ * out_rowids  min(k, n) row-ids in the same order.
+ * out_where   memory kind of both outputs.
+ * out_count   (host) receives min(k, n).
+ * Limits: n < 2^32.  k = 0 or n = 0 => OLAP_OK with count 0.
+ * The result is bit-exact: it equals a stable sort by (key, row-id) cut at k.
+ * ------------------------------------------------------------------------ */
+olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const uint32_t* rowids,
+                      olap_mem in_where, uint64_t n, uint64_t k, olap_order order,
+                      void* out_keys, uint32_t* out_rowids, olap_mem out_where,
+                      uint64_t* out_count);
+
+/* Asynchronous Top-K on device pointers only, enqueued on `stream` (NULL =>
+ * the context's stream).  Writes min(k, n) results; `dev_status` (device
+ * int32, may be NULL) receives an olap_status from the device side.  The
+ * context's scratch is reused by the next call on the same context, so calls
+ * on one context must be serialised on one stream. */
+olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type type,
+                            const uint32_t* d_rowids, uint64_t n, uint64_t k, olap_order order,
+                            void* d_out_keys, uint32_t* d_out_rowids, int32_t* dev_status,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OLAP_H */

@@ -1,0 +1,369 @@
+// C ABI of the OLAP library: contexts, memory movement of the key-only
+// contract (Sec. II-C: only (key, row-id) crosses the link, only row pointers
+// come back) and the Top-K entry points.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "ctx.h"
+#include "topk.cuh"
+
+namespace olap {
+
+olap_status fail(olap_ctx* ctx, olap_status st, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+olap_status cuda_fail(olap_ctx* ctx, cudaError_t e, const char* what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    if (e == cudaErrorMemoryAllocation) return fail(ctx, OLAP_E_NOMEM, m);
+    return fail(ctx, OLAP_E_CUDA, m);
+}
+
+bool within_budget(const olap_ctx* ctx, size_t extra) {
+    if (ctx->opts.mem_budget_bytes == 0) return true;
+    const uint64_t held = ctx->scratch_bytes + ctx->dev_in_bytes + ctx->dev_out_bytes + ctx->table_bytes;
+    return held + extra <= ctx->opts.mem_budget_bytes;
+}
+
+static olap_status grow(olap_ctx* ctx, void** buf, size_t* have, size_t need, const char* what) {
+    if (*have >= need) return OLAP_OK;
+    size_t want = std::max(need, *have + *have / 2);
+    want = (want + 0xFFFFF) & ~static_cast<size_t>(0xFFFFF);
+    if (!within_budget(ctx, want - *have))
+        return fail(ctx, OLAP_E_NOMEM, std::string(what) + ": device memory budget exceeded");
+    // Work on any stream may still use the old buffer.
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    e = cudaMalloc(buf, want);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        cudaGetLastError();
+        return cuda_fail(ctx, e, what);
+    }
+    *have = want;
+    return OLAP_OK;
+}
+
+olap_status ensure_scratch(olap_ctx* ctx, size_t bytes) {
+    const bool fresh = ctx->scratch_bytes < bytes;
+    olap_status st = grow(ctx, &ctx->scratch, &ctx->scratch_bytes, bytes, "scratch allocation");
+    if (st != OLAP_OK) return st;
+    if (fresh || ctx->barrier_dirty) {
+        cudaError_t e = cudaMemsetAsync(ctx->scratch, 0, 256, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "barrier reset");
+        ctx->barrier_dirty = false;
+    }
+    return OLAP_OK;
+}
+
+olap_status ensure_dev_in(olap_ctx* ctx, size_t bytes) {
+    return grow(ctx, &ctx->dev_in, &ctx->dev_in_bytes, bytes, "input staging allocation");
+}
+
+olap_status ensure_dev_out(olap_ctx* ctx, size_t bytes) {
+    return grow(ctx, &ctx->dev_out, &ctx->dev_out_bytes, bytes, "output staging allocation");
+}
+
+olap_status ensure_pinned(olap_ctx* ctx) {
+    if (ctx->pinned[0]) return OLAP_OK;
+    const size_t b = ctx->opts.staging_bytes ? ctx->opts.staging_bytes : (64ull << 20);
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e = cudaMallocHost(&ctx->pinned[i], b);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(ctx, e, "pinned staging allocation");
+        }
+        e = cudaEventCreateWithFlags(&ctx->pinned_ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "staging event");
+    }
+    ctx->pinned_bytes = b;
+    return OLAP_OK;
+}
+
+olap_status copy_h2d(olap_ctx* ctx, void* dst, const void* src, size_t bytes, olap_mem where) {
+    if (bytes == 0) return OLAP_OK;
+    cudaError_t e;
+    if (where == OLAP_MEM_DEVICE) {
+        e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "device copy");
+    }
+    if (where == OLAP_MEM_HOST_PINNED) {
+        e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+        return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "pinned H2D copy");
+    }
+    // Pageable: host memcpy into one pinned buffer while the other one's DMA runs.
+    olap_status st = ensure_pinned(ctx);
+    if (st != OLAP_OK) return st;
+    const unsigned char* s = static_cast<const unsigned char*>(src);
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    size_t off = 0;
+    int slot = 0;
+    while (off < bytes) {
+        const size_t len = std::min(ctx->pinned_bytes, bytes - off);
+        e = cudaEventSynchronize(ctx->pinned_ev[slot]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "staging wait");
+        std::memcpy(ctx->pinned[slot], s + off, len);
+        e = cudaMemcpyAsync(d + off, ctx->pinned[slot], len, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "staged H2D copy");
+        e = cudaEventRecord(ctx->pinned_ev[slot], ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "staging event record");
+        off += len;
+        slot ^= 1;
+    }
+    return OLAP_OK;
+}
+
+olap_status copy_d2h(olap_ctx* ctx, void* dst, const void* src, size_t bytes, olap_mem where) {
+    if (bytes == 0) return OLAP_OK;
+    cudaError_t e;
+    if (where == OLAP_MEM_DEVICE) {
+        e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "device copy");
+    }
+    if (where == OLAP_MEM_HOST_PINNED) {
+        e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+        return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "pinned D2H copy");
+    }
+    olap_status st = ensure_pinned(ctx);
+    if (st != OLAP_OK) return st;
+    const unsigned char* s = static_cast<const unsigned char*>(src);
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    // Chunks alternate between the two pinned buffers; the host copies chunk
+    // i out of its buffer once that buffer's DMA has finished, while the DMA
+    // of chunk i+1 runs into the other buffer.
+    size_t off = 0, pend_off = 0, pend_len = 0;
+    int slot = 0, pend_slot = -1;
+    while (off < bytes || pend_slot >= 0) {
+        if (off < bytes) {
+            const size_t len = std::min(ctx->pinned_bytes, bytes - off);
+            e = cudaMemcpyAsync(ctx->pinned[slot], s + off, len, cudaMemcpyDeviceToHost, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "staged D2H copy");
+            e = cudaEventRecord(ctx->pinned_ev[slot], ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "staging event record");
+            if (pend_slot >= 0) {
+                e = cudaEventSynchronize(ctx->pinned_ev[pend_slot]);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "staging wait");
+                std::memcpy(d + pend_off, ctx->pinned[pend_slot], pend_len);
+            }
+            pend_slot = slot;
+            pend_off = off;
+            pend_len = len;
+            off += len;
+            slot ^= 1;
+        } else {
+            e = cudaEventSynchronize(ctx->pinned_ev[pend_slot]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "staging wait");
+            std::memcpy(d + pend_off, ctx->pinned[pend_slot], pend_len);
+            pend_slot = -1;
+        }
+    }
+    return OLAP_OK;
+}
+
+// Enqueue one Top-K on device pointers.  The caller has validated arguments.
+static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type type,
+                                const uint32_t* d_rowids, uint64_t n, uint64_t kk, olap_order order,
+                                void* d_out_keys, uint32_t* d_out_rowids, int32_t* dev_status,
+                                cudaStream_t stream, TopkCtl** ctl_out) {
+    const TopkPlan plan = topk_plan(n, kk);
+    const bool reset = ctx->barrier_dirty || ctx->scratch_bytes < topk_scratch_bytes(plan, kk);
+    olap_status st = ensure_scratch(ctx, topk_scratch_bytes(plan, kk));
+    if (st != OLAP_OK) return st;
+    if (reset && stream != ctx->stream) {
+        // The barrier reset ran on the context stream; order the launch after it.
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "barrier reset wait");
+    }
+    TopkArgs a{};
+    a.keys = d_keys;
+    a.rowids = d_rowids;
+    a.n = n;
+    a.k = kk;
+    a.f32 = type == OLAP_KEY_F32;
+    a.desc = order == OLAP_DESC;
+    topk_carve(a, plan, ctx->scratch);
+    a.out_keys = d_out_keys;
+    a.out_rowids = d_out_rowids;
+    a.dev_status = dev_status;
+    cudaError_t e = topk_launch(a, ctx->topk_grid, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(ctx, e, "Top-K launch");
+    }
+    if (ctl_out) *ctl_out = a.ctl;
+    return OLAP_OK;
+}
+
+static olap_status check_topk_args(olap_ctx* ctx, const void* keys, olap_key_type type, uint64_t n,
+                                   uint64_t kk, olap_order order, const void* out_keys,
+                                   const void* out_rowids) {
+    if (type != OLAP_KEY_I64 && type != OLAP_KEY_F32) return fail(ctx, OLAP_E_INVALID, "bad key type");
+    if (order != OLAP_ASC && order != OLAP_DESC) return fail(ctx, OLAP_E_INVALID, "bad order");
+    if (n >= (1ull << 32)) return fail(ctx, OLAP_E_INVALID, "n must be below 2^32");
+    if (n && !keys) return fail(ctx, OLAP_E_INVALID, "keys is NULL");
+    if (kk && (!out_keys || !out_rowids)) return fail(ctx, OLAP_E_INVALID, "output pointer is NULL");
+    const size_t w = type == OLAP_KEY_I64 ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(keys) % w) return fail(ctx, OLAP_E_INVALID, "keys misaligned");
+    return OLAP_OK;
+}
+
+}  // namespace olap
+
+using namespace olap;
+
+extern "C" {
+
+olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
+    if (!out) return OLAP_E_INVALID;
+    *out = nullptr;
+    olap_ctx* ctx = new olap_ctx();
+    if (opts) ctx->opts = *opts;
+    if (ctx->opts.load_factor < 0.0 || ctx->opts.load_factor > 0.9) {
+        delete ctx;
+        return OLAP_E_INVALID;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev <= ctx->opts.device || ctx->opts.device < 0) {
+        cudaGetLastError();
+        delete ctx;
+        return OLAP_E_CUDA;
+    }
+    ctx->device = ctx->opts.device;
+    auto bail = [&](cudaError_t) {
+        cudaGetLastError();
+        olap_ctx_destroy(ctx);
+        return OLAP_E_CUDA;
+    };
+    if ((e = cudaSetDevice(ctx->device)) != cudaSuccess) return bail(e);
+    if (ctx->opts.stream) {
+        ctx->stream = static_cast<cudaStream_t>(ctx->opts.stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+        ctx->own_stream = true;
+    }
+    if ((e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess)
+        return bail(e);
+    ctx->topk_grid = topk_grid(ctx->device, 2);
+    if (ctx->topk_grid <= 0) return bail(cudaErrorUnknown);
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&ctx->host_status), 64)) != cudaSuccess) return bail(e);
+    *out = ctx;
+    return OLAP_OK;
+}
+
+void olap_ctx_destroy(olap_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->dev_in) cudaFree(ctx->dev_in);
+    if (ctx->dev_out) cudaFree(ctx->dev_out);
+    for (int i = 0; i < 2; ++i) {
+        if (ctx->pinned[i]) cudaFreeHost(ctx->pinned[i]);
+        if (ctx->pinned_ev[i]) cudaEventDestroy(ctx->pinned_ev[i]);
+    }
+    if (ctx->host_status) cudaFreeHost(ctx->host_status);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char* olap_last_error(const olap_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+void* olap_ctx_stream(const olap_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
+
+olap_status olap_ctx_sync(olap_ctx* ctx) {
+    if (!ctx) return OLAP_E_INVALID;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "stream synchronize");
+}
+
+olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const uint32_t* rowids,
+                      olap_mem in_where, uint64_t n, uint64_t k, olap_order order, void* out_keys,
+                      uint32_t* out_rowids, olap_mem out_where, uint64_t* out_count) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (!out_count) return fail(ctx, OLAP_E_INVALID, "out_count is NULL");
+    *out_count = 0;
+    if (in_where < OLAP_MEM_HOST || in_where > OLAP_MEM_DEVICE || out_where < OLAP_MEM_HOST ||
+        out_where > OLAP_MEM_DEVICE)
+        return fail(ctx, OLAP_E_INVALID, "bad memory kind");
+    const uint64_t kk = std::min(k, n);
+    olap_status st = check_topk_args(ctx, keys, type, n, kk, order, out_keys, out_rowids);
+    if (st != OLAP_OK) return st;
+    if (kk == 0) return OLAP_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
+    const size_t w = type == OLAP_KEY_I64 ? 8 : 4;
+
+    // Key-only input: keys (and explicit row-ids) to the device.
+    const void* dk = keys;
+    const uint32_t* dr = rowids;
+    if (in_where != OLAP_MEM_DEVICE) {
+        const size_t kbytes = (n * w + 255) & ~static_cast<size_t>(255);
+        st = ensure_dev_in(ctx, kbytes + (rowids ? n * 4 : 0));
+        if (st != OLAP_OK) return st;
+        st = copy_h2d(ctx, ctx->dev_in, keys, n * w, in_where);
+        if (st != OLAP_OK) return st;
+        dk = ctx->dev_in;
+        if (rowids) {
+            dr = reinterpret_cast<const uint32_t*>(static_cast<unsigned char*>(ctx->dev_in) + kbytes);
+            st = copy_h2d(ctx, const_cast<uint32_t*>(dr), rowids, n * 4, in_where);
+            if (st != OLAP_OK) return st;
+        }
+    }
+    void* dok = out_keys;
+    uint32_t* dor = out_rowids;
+    const size_t okb = (kk * w + 255) & ~static_cast<size_t>(255);
+    if (out_where != OLAP_MEM_DEVICE) {
+        st = ensure_dev_out(ctx, okb + kk * 4);
+        if (st != OLAP_OK) return st;
+        dok = ctx->dev_out;
+        dor = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ctx->dev_out) + okb);
+    }
+    TopkCtl* ctl = nullptr;
+    st = topk_enqueue(ctx, dk, type, dr, n, kk, order, dok, dor, nullptr, ctx->stream, &ctl);
+    if (st != OLAP_OK) return st;
+    e = cudaMemcpyAsync(ctx->host_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
+    if (out_where != OLAP_MEM_DEVICE) {
+        st = copy_d2h(ctx, out_keys, dok, kk * w, out_where);
+        if (st != OLAP_OK) return st;
+        st = copy_d2h(ctx, out_rowids, dor, kk * 4, out_where);
+        if (st != OLAP_OK) return st;
+    }
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Top-K");
+    if (*ctx->host_status != OLAP_OK) {
+        ctx->barrier_dirty = true;
+        return fail(ctx, static_cast<olap_status>(*ctx->host_status), "Top-K device wait expired");
+    }
+    *out_count = kk;
+    return OLAP_OK;
+}
+
+olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type type, const uint32_t* d_rowids,
+                            uint64_t n, uint64_t k, olap_order order, void* d_out_keys,
+                            uint32_t* d_out_rowids, int32_t* dev_status, void* stream) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    const uint64_t kk = std::min(k, n);
+    olap_status st = check_topk_args(ctx, d_keys, type, n, kk, order, d_out_keys, d_out_rowids);
+    if (st != OLAP_OK) return st;
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    if (kk == 0) {
+        if (dev_status) {
+            cudaError_t e = cudaMemsetAsync(dev_status, 0, sizeof(int32_t), s);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "status reset");
+        }
+        return OLAP_OK;
+    }
+    return topk_enqueue(ctx, d_keys, type, d_rowids, n, kk, order, d_out_keys, d_out_rowids, dev_status, s,
+                        nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// Shared device helpers of the GB300 OLAP library: order-preserving key
+// transforms, (key, row-id) composite digits, warp-aggregated appends and a
+// grid barrier whose wait is bounded.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "olap.h"
+
+namespace olap {
+
+constexpr uint64_t SIGN64 = 0x8000000000000000ull;
+
+// Bound on any device-side wait: about one second at the GB300's clocks.
+constexpr long long WAIT_LIMIT_CYCLES = 2000000000ll;
+
+// ---------------------------------------------------------------------------
+// Order-preserving transform of a key into an unsigned "rank word".  Selection
+// in either order then becomes "smallest rank words first", with the row-id
+// ascending as the second field of the composite (key, row-id) order.
+//   int64: flip the sign bit (two's complement -> offset binary).
+//   float32: IEEE 754 totalOrder as an unsigned order: negative patterns are
+//   inverted, non-negative ones get the sign bit set.
+//   DESC: the word is complemented.
+// The float word is left-aligned in 64 bits, so every rank word is 64 bits and
+// its first `key_bits` bits are significant.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t rank_i64(uint64_t bits, bool desc) {
+    const uint64_t u = bits ^ SIGN64;
+    return desc ? ~u : u;
+}
+__host__ __device__ __forceinline__ uint64_t rank_f32(uint32_t bits, bool desc) {
+    uint32_t u = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+    if (desc) u = ~u;
+    return static_cast<uint64_t>(u) << 32;
+}
+__host__ __device__ __forceinline__ uint64_t unrank_i64(uint64_t r, bool desc) {
+    return (desc ? ~r : r) ^ SIGN64;
+}
+__host__ __device__ __forceinline__ uint32_t unrank_f32(uint64_t r, bool desc) {
+    uint32_t u = static_cast<uint32_t>(r >> 32);
+    if (desc) u = ~u;
+    return (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+}
+
+// ---------------------------------------------------------------------------
+// Composite (rank word, row-id) as a 128-bit big-endian bit string (w0, w1):
+// the key_bits significant bits of the rank word followed by the 32 row-id
+// bits.  Total significant bits: key_bits + 32 (96 for int64, 64 for float32).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void comp_words(uint64_t r, uint32_t rid, int key_bits, uint64_t& w0,
+                                           uint64_t& w1) {
+    if (key_bits == 64) {
+        w0 = r;
+        w1 = static_cast<uint64_t>(rid) << 32;
+    } else {
+        w0 = r | rid;
+        w1 = 0;
+    }
+}
+
+// Bits [L, L + d) of (w0, w1), MSB first; 1 <= d <= 32, L + d <= 128.
+__device__ __forceinline__ uint32_t comp_digit(uint64_t w0, uint64_t w1, int L, int d) {
+    uint64_t hi;
+    if (L == 0)
+        hi = w0;
+    else if (L < 64)
+        hi = (w0 << L) | (w1 >> (64 - L));
+    else
+        hi = w1 << (L - 64);
+    return static_cast<uint32_t>(hi >> (64 - d));
+}
+
+// Compare the first L bits of (w0, w1) with the prefix (p0, p1): -1, 0, +1.
+__device__ __forceinline__ int prefix_cmp(uint64_t w0, uint64_t w1, uint64_t p0, uint64_t p1, int L) {
+    if (L == 0) return 0;
+    if (L < 64) {
+        const uint64_t m = ~0ull << (64 - L);
+        const uint64_t a = w0 & m, b = p0 & m;
+        return a < b ? -1 : (a > b ? 1 : 0);
+    }
+    if (w0 != p0) return w0 < p0 ? -1 : 1;
+    if (L == 64) return 0;
+    const uint64_t m = ~0ull << (128 - L);
+    const uint64_t a = w1 & m, b = p1 & m;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+// Set bits [L, L + d) of (p0, p1) to `digit`.
+__device__ __forceinline__ void prefix_set(uint64_t& p0, uint64_t& p1, int L, int d, uint32_t digit) {
+    const uint64_t v = static_cast<uint64_t>(digit);
+    if (L + d <= 64) {
+        p0 |= v << (64 - L - d);
+    } else if (L >= 64) {
+        p1 |= v << (128 - L - d);
+    } else {                                  // straddles the word boundary
+        const int in0 = 64 - L;               // bits of the digit that land in p0
+        p0 |= v >> (d - in0);
+        p1 |= v << (64 - (d - in0));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Memory-order helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+// Grid barrier for cooperative launches (all CTAs co-resident).  Arrival is an
+// atomic count; the last CTA to arrive resets it and bumps a generation word
+// the others wait on.  The wait is bounded: after WAIT_LIMIT_CYCLES the CTA
+// records OLAP_E_TIMEOUT in *err and leaves; callers test the return value
+// and stop.  The counter returns to zero after every completed barrier.
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar* bar, int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
+        const unsigned g = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u32(&bar->gen, g + 1);
+        } else {
+            const long long t0 = clock64();
+            while (ld_acquire_u32(&bar->gen) == g) {
+                if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+                    atomicCAS(err, 0, static_cast<int>(OLAP_E_TIMEOUT));
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ld_volatile_i32(err) == 0;
+}
+
+// Warp-aggregated append: every lane contributes `cnt` items; returns the
+// lane's first slot in a global array advanced by one atomic per warp.
+__device__ __forceinline__ unsigned long long warp_append(unsigned long long* counter, unsigned cnt) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= static_cast<unsigned>(o)) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(counter, static_cast<unsigned long long>(total));
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    return base + (incl - cnt);
+}
+
+}  // namespace olap

@@ -1,0 +1,68 @@
+// Host-side context of the OLAP library: device, stream, device scratch
+// arena, pinned staging buffers and the last error message.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "olap.h"
+
+struct olap_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    olap_opts opts{};
+    int sm_count = 0;
+    int topk_grid = 0;                // CTAs of the cooperative Top-K grid
+
+    // Device scratch arena (grow-only).  Its first bytes hold the grid
+    // barrier of the cooperative kernels, which must start zeroed.
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    bool barrier_dirty = false;       // a device wait expired: re-zero before use
+
+    // Device copies of host inputs / outputs (grow-only).
+    void* dev_in = nullptr;
+    size_t dev_in_bytes = 0;
+    void* dev_out = nullptr;
+    size_t dev_out_bytes = 0;
+
+    // Pinned double buffers for pageable host data, and their copy events.
+    void* pinned[2] = {nullptr, nullptr};
+    size_t pinned_bytes = 0;
+    cudaEvent_t pinned_ev[2] = {nullptr, nullptr};
+
+    // Small pinned word for device status read-back.
+    int32_t* host_status = nullptr;
+
+    // Device memory held by join tables created through this context.
+    uint64_t table_bytes = 0;
+
+    std::string last_error;
+};
+
+namespace olap {
+
+// Record an error message on the context and return the status.
+olap_status fail(olap_ctx* ctx, olap_status st, const std::string& msg);
+// Map a CUDA error to OLAP_E_CUDA with the call site in the message.
+olap_status cuda_fail(olap_ctx* ctx, cudaError_t e, const char* what);
+
+// Grow-only device buffers of the context.
+olap_status ensure_scratch(olap_ctx* ctx, size_t bytes);
+olap_status ensure_dev_in(olap_ctx* ctx, size_t bytes);
+olap_status ensure_dev_out(olap_ctx* ctx, size_t bytes);
+olap_status ensure_pinned(olap_ctx* ctx);
+
+// Copy `bytes` from host memory of kind `where` to device `dst` on the
+// context stream; pageable memory goes through the pinned double buffers.
+olap_status copy_h2d(olap_ctx* ctx, void* dst, const void* src, size_t bytes, olap_mem where);
+// Copy device `src` to host memory of kind `where` (pageable through pinned).
+olap_status copy_d2h(olap_ctx* ctx, void* dst, const void* src, size_t bytes, olap_mem where);
+
+// Bytes of device memory the context may still allocate under its budget.
+bool within_budget(const olap_ctx* ctx, size_t extra);
+
+}  // namespace olap

@@ -1,0 +1,226 @@
+"""Thin ctypes binding of the C ABI in ``include/olap.h``.
+
+Argument marshalling only: every step of the offloaded path runs in the CUDA
+library ``_build/libolap.so``.  Loading fails loudly when that library is
+missing; there is no CPU fallback.  Buffers may be numpy arrays (pageable host
+memory), pinned CPU torch tensors or CUDA torch tensors; the memory kind is
+derived from the object and passed through the ABI.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# Status codes (olap_status)
+OK, E_INVALID, E_NOMEM, E_CUDA, E_OVERFLOW, E_TIMEOUT, E_UNIMPLEMENTED, E_DEVICE = range(8)
+STATUS_NAMES = ["OK", "E_INVALID", "E_NOMEM", "E_CUDA", "E_OVERFLOW", "E_TIMEOUT",
+                "E_UNIMPLEMENTED", "E_DEVICE"]
+KEY_I64, KEY_F32 = 0, 1
+ASC, DESC = 0, 1
+MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
+
+# Every symbol include/olap.h declares, checked by the ABI tests.
+EXPORTS = [
+    "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
+    "olap_topk", "olap_topk_async",
+]
+
+
+class OlapError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class olap_opts(ctypes.Structure):
+    _fields_ = [
+        ("device", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+        ("mem_budget_bytes", ctypes.c_uint64),
+        ("margin_ms", ctypes.c_double),
+        ("block_threads", ctypes.c_int),
+        ("load_factor", ctypes.c_double),
+        ("staging_bytes", ctypes.c_uint64),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libolap.so (built in-tree by ``build.build()``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or lib_path()
+        if not os.path.exists(p):
+            raise ImportError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+        lib = ctypes.CDLL(p)
+        vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+        lib.olap_ctx_create.restype = i32
+        lib.olap_ctx_create.argtypes = [ctypes.POINTER(olap_opts), ctypes.POINTER(vp)]
+        lib.olap_ctx_destroy.restype = None
+        lib.olap_ctx_destroy.argtypes = [vp]
+        lib.olap_last_error.restype = ctypes.c_char_p
+        lib.olap_last_error.argtypes = [vp]
+        lib.olap_ctx_stream.restype = vp
+        lib.olap_ctx_stream.argtypes = [vp]
+        lib.olap_ctx_sync.restype = i32
+        lib.olap_ctx_sync.argtypes = [vp]
+        lib.olap_topk.restype = i32
+        lib.olap_topk.argtypes = [vp, vp, i32, vp, i32, u64, u64, i32, vp, vp, i32, ctypes.POINTER(u64)]
+        lib.olap_topk_async.restype = i32
+        lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
+        _bind_more(lib)
+        _lib = lib
+        return lib
+
+
+def _bind_more(lib):
+    """Bindings of the entry points added after Top-K (join, gate, batch)."""
+    for fn in _EXTRA_BINDERS:
+        fn(lib)
+
+
+_EXTRA_BINDERS = []
+
+
+# ---------------------------------------------------------------------------
+# Buffer marshalling
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch  # noqa: WPS433 (torch is only plumbing: memory and streams)
+    return torch
+
+
+def mem_kind(buf) -> int:
+    if isinstance(buf, np.ndarray):
+        return MEM_HOST
+    torch = _torch()
+    if isinstance(buf, torch.Tensor):
+        if buf.is_cuda:
+            return MEM_DEVICE
+        return MEM_HOST_PINNED if buf.is_pinned() else MEM_HOST
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def ptr(buf) -> int | None:
+    if buf is None:
+        return None
+    if isinstance(buf, np.ndarray):
+        assert buf.flags["C_CONTIGUOUS"]
+        return buf.ctypes.data
+    assert buf.is_contiguous()
+    return buf.data_ptr()
+
+
+def key_type_of(buf) -> int:
+    dt = buf.dtype
+    if isinstance(buf, np.ndarray):
+        if dt == np.int64:
+            return KEY_I64
+        if dt == np.float32:
+            return KEY_F32
+    else:
+        torch = _torch()
+        if dt == torch.int64:
+            return KEY_I64
+        if dt == torch.float32:
+            return KEY_F32
+    raise TypeError(f"keys must be int64 or float32, got {dt}")
+
+
+def numel(buf) -> int:
+    return int(buf.shape[0]) if isinstance(buf, np.ndarray) else int(buf.numel())
+
+
+# ---------------------------------------------------------------------------
+# Context
+# ---------------------------------------------------------------------------
+
+class Context:
+    """An ``olap_ctx`` (one device, one stream, its scratch and staging)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None, mem_budget_bytes: int = 0,
+                 margin_ms: float = 0.0, load_factor: float = 0.0, staging_bytes: int = 0):
+        self.lib = load()
+        opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, 0, load_factor, staging_bytes)
+        h = ctypes.c_void_p()
+        st = self.lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h))
+        if st != OK:
+            raise OlapError(st, "olap_ctx_create failed (no usable CUDA device?)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.olap_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def stream(self) -> int:
+        return self.lib.olap_ctx_stream(self.h)
+
+    def last_error(self) -> str:
+        return self.lib.olap_last_error(self.h).decode()
+
+    def check(self, st: int):
+        if st != OK:
+            raise OlapError(st, self.last_error())
+
+    def sync(self):
+        self.check(self.lib.olap_ctx_sync(self.h))
+
+    # -- Top-K ---------------------------------------------------------------
+    def topk(self, keys, k: int, order: int = DESC, rowids=None, out_keys=None, out_rowids=None):
+        """olap_topk: returns (out_keys, out_rowids) cut to min(k, n).
+
+        Outputs default to numpy arrays (host); pass preallocated buffers
+        (numpy, pinned or CUDA torch tensors) to choose their memory kind."""
+        n = numel(keys)
+        kt = key_type_of(keys)
+        cnt = min(int(k), n)
+        if out_keys is None:
+            out_keys = np.empty(max(cnt, 1), dtype=np.int64 if kt == KEY_I64 else np.float32)
+            out_rowids = np.empty(max(cnt, 1), dtype=np.uint32)
+        where = mem_kind(keys)
+        if rowids is not None:
+            assert mem_kind(rowids) == where and numel(rowids) == n
+        ow = mem_kind(out_keys)
+        got = ctypes.c_uint64()
+        st = self.lib.olap_topk(self.h, ptr(keys), kt, ptr(rowids), where, n, int(k), int(order),
+                                ptr(out_keys), ptr(out_rowids), ow, ctypes.byref(got))
+        self.check(st)
+        assert got.value == cnt
+        return out_keys[:cnt], out_rowids[:cnt]
+
+    def topk_async(self, d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=None,
+                   dev_status=None, stream: int | None = None):
+        """olap_topk_async on CUDA tensors; enqueues only."""
+        st = self.lib.olap_topk_async(self.h, ptr(d_keys), key_type_of(d_keys), ptr(d_rowids),
+                                      numel(d_keys), int(k), int(order), ptr(d_out_keys),
+                                      ptr(d_out_rowids), ptr(dev_status), stream)
+        self.check(st)

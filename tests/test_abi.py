@@ -1,0 +1,50 @@
+"""The C-ABI library builds, loads and exports every symbol include/olap.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2601_19911_gb300 import build, olap
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "olap.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(olap_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return olap.load()
+
+
+def test_header_declares_the_binding_exports():
+    assert sorted(olap.EXPORTS) == declared_functions()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(olap.OlapError) as ei:
+        olap.Context(0)
+    assert ei.value.status == olap.E_CUDA
+
+
+def test_null_context_is_rejected(lib):
+    got = ctypes.c_uint64()
+    assert lib.olap_topk(None, None, 0, None, 0, 0, 0, 0, None, None, 0, ctypes.byref(got)) == olap.E_INVALID
+    assert lib.olap_ctx_sync(None) == olap.E_INVALID
+    assert lib.olap_last_error(None) == b"no context"

@@ -1,0 +1,263 @@
+"""GPU parity of Top-K (ORDER BY key LIMIT K, Sec. III-A) against the CPU
+oracle, bit-exact: the same K row-ids and key bits in the same order.
+
+Small and medium sizes compare element by element with the oracle; they span
+several 4096-entry tiles, ragged tails, the direct path (N <= 2^21), the
+sampled single-pass path and its fallback.  Full-size cases (N = 2^28) check
+properties that fix the answer uniquely: K real input rows, distinct row-ids,
+sorted, and exactly K-1 input rows strictly ahead of the last one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_19911_gb300 import datagen, olap
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0)
+    yield c
+    c.close()
+
+
+def _bits(a):
+    a = np.asarray(a)
+    return a.view(np.uint64 if a.dtype == np.int64 else np.uint32)
+
+
+def _gpu_topk(ctx, keys, k, order, rowids=None, where="device"):
+    if where == "device":
+        dk = torch.from_numpy(keys).cuda()
+        dr = None if rowids is None else torch.from_numpy(rowids.view(np.int32)).cuda()
+        cnt = min(k, keys.shape[0])
+        ok = torch.empty(max(cnt, 1), dtype=dk.dtype, device="cuda")
+        orow = torch.empty(max(cnt, 1), dtype=torch.int32, device="cuda")
+        got_k, got_r = ctx.topk(dk, k, order, rowids=dr, out_keys=ok, out_rowids=orow)
+        return got_k.cpu().numpy(), got_r.cpu().numpy().view(np.uint32)
+    if where == "pinned":
+        pk = torch.from_numpy(keys).pin_memory()
+        pr = None if rowids is None else torch.from_numpy(rowids.view(np.int32)).pin_memory()
+        cnt = min(k, keys.shape[0])
+        ok = torch.empty(max(cnt, 1), dtype=pk.dtype).pin_memory()
+        orow = torch.empty(max(cnt, 1), dtype=torch.int32).pin_memory()
+        got_k, got_r = ctx.topk(pk, k, order, rowids=pr, out_keys=ok, out_rowids=orow)
+        return got_k.numpy(), got_r.numpy().view(np.uint32)
+    got_k, got_r = ctx.topk(keys, k, order, rowids=rowids)
+    return got_k, got_r
+
+
+def _check(ctx, keys, k, order, rowids=None, where="device"):
+    gk, gr = _gpu_topk(ctx, keys, k, order, rowids, where)
+    ok, orow = oracle.topk(keys, k, order, rowids)
+    assert gr.shape == orow.shape
+    np.testing.assert_array_equal(gr, orow)
+    np.testing.assert_array_equal(_bits(gk), _bits(ok))
+
+
+SIZES = [1, 2, 31, 32, 33, 1000, 4095, 4096, 4097, 65537, 1 << 20]
+
+
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("kt", ["i64", "f32"])
+def test_small_sizes_all_k(ctx, n, kt):
+    keys = datagen.topk_keys(n, "uniform", kt, seed=n)
+    for k in sorted({1, 10, 100, 1000, 4096, 4097, n - 1, n, n + 1}):
+        if k < 1:
+            continue
+        for order in (olap.DESC, olap.ASC):
+            _check(ctx, keys, k, order)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "ascending", "dup1024"])
+@pytest.mark.parametrize("kt", ["i64", "f32"])
+@pytest.mark.parametrize("n", [100_000, (1 << 21) + 3, 3_000_001])
+def test_distributions(ctx, dist, kt, n):
+    keys = datagen.topk_keys(n, dist, kt, seed=7)
+    for k in (1, 10, 1000, 5000):
+        _check(ctx, keys, k, olap.DESC)
+    _check(ctx, keys, 100, olap.ASC)
+
+
+@pytest.mark.parametrize("n", [4097, (1 << 21) + 17, 5_000_000])
+def test_explicit_rowids_with_duplicates(ctx, n):
+    keys = datagen.topk_keys(n, "dup1024", "i64", seed=3)
+    rowids = (datagen.splitmix64(77, n) >> np.uint64(40)).astype(np.uint32)   # many repeats
+    for k in (1, 100, 4096, 20000):
+        _check(ctx, keys, k, olap.DESC, rowids)
+        _check(ctx, keys, k, olap.ASC, rowids)
+
+
+def test_large_k_merge_path(ctx):
+    n = 3_000_000
+    keys = datagen.topk_keys(n, "uniform", "i64", seed=11)
+    for k in (4097, 100_000, 262_144):
+        _check(ctx, keys, k, olap.DESC)
+    f = datagen.topk_keys(n, "dup1024", "f32", seed=11)
+    _check(ctx, f, 100_000, olap.ASC)
+
+
+def test_all_equal_keys_fallback(ctx):
+    # every key equal: the sampled threshold admits all N rows, more than the
+    # candidate buffer holds, so the selection falls back to the full input.
+    n = 4_000_000
+    keys = np.full(n, -5, dtype=np.int64)
+    _check(ctx, keys, 100, olap.DESC)
+    _check(ctx, keys, 5000, olap.ASC)
+
+
+def test_float_specials(ctx):
+    from tests.test_oracle_topk import f32_specials
+    bits, _ = f32_specials()
+    rng = np.random.default_rng(1)
+    for n in (7, 1000, 70_000):
+        keys = bits[rng.integers(0, len(bits), n)].view(np.float32)
+        for k in (1, 5, n // 2, n):
+            _check(ctx, keys, k, olap.DESC)
+            _check(ctx, keys, k, olap.ASC)
+
+
+def test_int64_extremes(ctx):
+    ext = np.array([-(1 << 63), (1 << 63) - 1, 0, -1, 1], dtype=np.int64)
+    rng = np.random.default_rng(2)
+    keys = ext[rng.integers(0, len(ext), 50_000)]
+    for k in (1, 3, 10_000, 50_000):
+        _check(ctx, keys, k, olap.DESC)
+        _check(ctx, keys, k, olap.ASC)
+
+
+@pytest.mark.parametrize("where", ["pinned", "pageable"])
+def test_host_memory_kinds(ctx, where):
+    n = 3_000_000
+    keys = datagen.topk_keys(n, "uniform", "i64", seed=5)
+    rowids = datagen.identity_rowids(n)[::-1].copy()
+    _check(ctx, keys, 100, olap.DESC, rowids, where=where)
+    f = datagen.topk_keys(n, "uniform", "f32", seed=5)
+    _check(ctx, f, 1000, olap.ASC, None, where=where)
+
+
+def test_empty_and_zero_k(ctx):
+    e = np.zeros(0, dtype=np.int64)
+    gk, gr = ctx.topk(e, 10)
+    assert gr.shape == (0,)
+    gk, gr = ctx.topk(np.arange(10, dtype=np.int64), 0)
+    assert gr.shape == (0,)
+
+
+def test_unaligned_device_pointer(ctx):
+    # keys starting 8 bytes past a 16-byte boundary: scalar head, vector body
+    n = (1 << 21) + 1001
+    keys = datagen.topk_keys(n + 1, "uniform", "i64", seed=9)
+    dk = torch.from_numpy(keys).cuda()[1:]
+    ok = torch.empty(100, dtype=torch.int64, device="cuda")
+    orow = torch.empty(100, dtype=torch.int32, device="cuda")
+    ctx.topk(dk, 100, olap.DESC, out_keys=ok, out_rowids=orow)
+    wk, wr = oracle.topk(keys[1:], 100, olap.DESC)
+    np.testing.assert_array_equal(orow.cpu().numpy().view(np.uint32), wr)
+    np.testing.assert_array_equal(ok.cpu().numpy(), wk)
+
+
+def test_golden_fixtures(ctx):
+    from tests.golden import make_golden
+    for case in make_golden.TOPK_CASES:
+        keys = make_golden.topk_input(case)
+        want = make_golden.read_topk(case["name"])
+        gk, gr = _gpu_topk(ctx, keys, case["k"], case["order"])
+        assert gr.tolist() == want["rowids"]
+        assert _bits(gk).tolist() == want["key_bits"]
+
+
+def test_async_matches_blocking_and_status(ctx):
+    n = 5_000_000
+    keys = datagen.topk_keys(n, "uniform", "f32", seed=21)
+    dk = torch.from_numpy(keys).cuda()
+    ok = torch.empty(1000, dtype=torch.float32, device="cuda")
+    orow = torch.empty(1000, dtype=torch.int32, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    ctx.topk_async(dk, 1000, olap.DESC, ok, orow, dev_status=status)
+    ctx.sync()
+    assert int(status.item()) == olap.OK
+    wk, wr = oracle.topk(keys, 1000, olap.DESC)
+    np.testing.assert_array_equal(orow.cpu().numpy().view(np.uint32), wr)
+    np.testing.assert_array_equal(_bits(ok.cpu().numpy()), _bits(wk))
+
+
+# ---------------------------------------------------------------------------
+# Full size: N = 2^28, the configuration the benchmark times.
+# ---------------------------------------------------------------------------
+
+def _total_order_i32(bits_u32):
+    """A signed int32 key that sorts float32 bit patterns by IEEE totalOrder
+    (negative patterns have their 31 magnitude bits flipped)."""
+    x = bits_u32.view(np.int32)
+    return x ^ ((x >> 31) & np.int32(0x7FFFFFFF))
+
+
+def test_total_order_key_matches_fixture():
+    from tests.test_oracle_topk import f32_specials
+    bits, _ = f32_specials()
+    k = _total_order_i32(bits)
+    assert np.all(k[1:] > k[:-1])
+
+
+def _full_size_properties(keys, k, order, gk, gr):
+    n = keys.shape[0]
+    assert gr.shape[0] == k
+    idx = gr.astype(np.int64)
+    assert np.all(idx < n)
+    assert np.unique(idx).shape[0] == k                               # distinct rows
+    np.testing.assert_array_equal(_bits(keys[idx]), _bits(gk))        # real input rows
+    if keys.dtype == np.int64:
+        sk = keys.astype(np.int64)
+        ko = gk.astype(np.int64)
+    else:
+        sk = _total_order_i32(keys.view(np.uint32)).astype(np.int64)
+        ko = _total_order_i32(gk.view(np.uint32)).astype(np.int64)
+    sgn = -1 if order == olap.DESC else 1
+    # sorted by (key in the requested order, row-id ascending)
+    a = ko[:-1] * 0
+    prev_k, next_k = ko[:-1], ko[1:]
+    if sgn < 0:
+        ok_order = (prev_k > next_k) | ((prev_k == next_k) & (idx[:-1] < idx[1:]))
+    else:
+        ok_order = (prev_k < next_k) | ((prev_k == next_k) & (idx[:-1] < idx[1:]))
+    assert np.all(ok_order), a
+    lk, lr = ko[-1], idx[-1]
+    ahead = 0
+    step = 1 << 25
+    for s in range(0, n, step):
+        blk = sk[s:s + step]
+        rows = np.arange(s, min(n, s + step), dtype=np.int64)
+        better = (blk > lk) if sgn < 0 else (blk < lk)
+        ahead += int(np.count_nonzero(better | ((blk == lk) & (rows < lr))))
+    assert ahead == k - 1
+
+
+FULL = [("i64", "uniform", 10), ("i64", "uniform", 1000), ("i64", "uniform", 100_000),
+        ("i64", "ascending", 1000), ("i64", "dup1024", 1000), ("i64", "dup1024", 100_000),
+        ("f32", "uniform", 10), ("f32", "uniform", 100_000), ("f32", "ascending", 1000),
+        ("f32", "dup1024", 1000)]
+
+
+@pytest.mark.parametrize("kt,dist,k", FULL)
+def test_full_size_2p28(ctx, kt, dist, k):
+    n = 1 << 28
+    keys = datagen.topk_keys(n, dist, kt, seed=1)
+    dk = torch.from_numpy(keys).cuda()
+    ok = torch.empty(k, dtype=dk.dtype, device="cuda")
+    orow = torch.empty(k, dtype=torch.int32, device="cuda")
+    for order in (olap.DESC, olap.ASC) if k == 1000 else (olap.DESC,):
+        ctx.topk(dk, k, order, out_keys=ok, out_rowids=orow)
+        gk = ok.cpu().numpy()
+        gr = orow.cpu().numpy().view(np.uint32)
+        _full_size_properties(keys, k, order, gk, gr)
+        if dist == "ascending":                                        # closed form
+            want = np.arange(n - 1, n - 1 - k, -1) if order == olap.DESC else np.arange(k)
+            np.testing.assert_array_equal(gr.astype(np.int64), want)
+    del dk
+    torch.cuda.empty_cache()
