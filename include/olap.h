@@ -117,6 +117,34 @@ olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type typ
                             void* d_out_keys, uint32_t* d_out_rowids, int32_t* dev_status,
                             void* stream);
 
+/* ------------------------------------------------------------------------
+ * Top-K that allocates nothing (no counterpart in the paper: a deployment
+ * entry point for callers that cannot let a library allocate GPU memory --
+ * engines whose device memory is wholly reserved by their own pool, plug-in
+ * or UDF hosts that forbid allocation inside an operator, and latency-critical
+ * paths that cannot accept the device-wide synchronisation cudaMalloc and
+ * cudaFree may cause).
+ *
+ * Same arguments and result as olap_topk_async, but without a context: the
+ * working memory is a fixed array of about 2 MiB built into the library,
+ * resident on every GPU the library is loaded on until the process exits.
+ * The call makes no cudaMalloc/cudaFree and no other allocation.
+ *   - Limits: n <= OLAP_NOALLOC_MAX_N and k <= OLAP_NOALLOC_MAX_K; larger
+ *     sizes return OLAP_E_INVALID before anything is launched.
+ *   - Runs on the current CUDA device, on `stream` (NULL = legacy default).
+ *   - The first call on a device looks up the array's device address with
+ *     that device current (one-time set-up); make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the one array and it keeps the previous
+ *     call's contents (the library clears what must start at zero).  Calls
+ *     whose work overlaps on the GPU race on it: order them on one stream.
+ * ------------------------------------------------------------------------ */
+#define OLAP_NOALLOC_MAX_N (1ull << 24)
+#define OLAP_NOALLOC_MAX_K 4096ull
+olap_status olap_topk_noalloc(const void* d_keys, olap_key_type type, const uint32_t* d_rowids,
+                              uint64_t n, uint64_t k, olap_order order, void* d_out_keys,
+                              uint32_t* d_out_rowids, int32_t* dev_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

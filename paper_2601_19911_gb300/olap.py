@@ -27,8 +27,10 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 # Every symbol include/olap.h declares, checked by the ABI tests.
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
-    "olap_topk", "olap_topk_async",
+    "olap_topk", "olap_topk_async", "olap_topk_noalloc",
 ]
+NOALLOC_MAX_N = 1 << 24
+NOALLOC_MAX_K = 4096
 
 
 class OlapError(RuntimeError):
@@ -82,6 +84,8 @@ def load(path: str | None = None):
         lib.olap_topk.argtypes = [vp, vp, i32, vp, i32, u64, u64, i32, vp, vp, i32, ctypes.POINTER(u64)]
         lib.olap_topk_async.restype = i32
         lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
+        lib.olap_topk_noalloc.restype = i32
+        lib.olap_topk_noalloc.argtypes = [vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         _bind_more(lib)
         _lib = lib
         return lib
@@ -224,3 +228,19 @@ class Context:
                                       numel(d_keys), int(k), int(order), ptr(d_out_keys),
                                       ptr(d_out_rowids), ptr(dev_status), stream)
         self.check(st)
+
+
+def topk_noalloc(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=None, dev_status=None,
+                 stream: int | None = None):
+    """olap_topk_noalloc on CUDA tensors of the current device: the Top-K for
+    callers that cannot let the library allocate device memory (its working
+    memory is a fixed array inside the library).  Enqueues only."""
+    lib = load()
+    n = numel(d_keys)
+    if n > NOALLOC_MAX_N or int(k) > NOALLOC_MAX_K:
+        raise ValueError(f"olap_topk_noalloc handles n <= {NOALLOC_MAX_N} and k <= {NOALLOC_MAX_K}; "
+                         f"got n={n}, k={k}")
+    st = lib.olap_topk_noalloc(ptr(d_keys), key_type_of(d_keys), ptr(d_rowids), n, int(k), int(order),
+                               ptr(d_out_keys), ptr(d_out_rowids), ptr(dev_status), stream)
+    if st != OK:
+        raise OlapError(st, "olap_topk_noalloc failed")
