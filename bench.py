@@ -45,7 +45,7 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks.mem,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -80,24 +80,25 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mem, mx, reasons = [], [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for l in self.lines:
             f = [x.strip() for x in l.split(",")]
-            if len(f) < 7:
+            if len(f) < 8:
                 continue
             try:
                 sm.append(float(f[0]))
                 mx = float(f[1])
+                mem.append(float(f[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[3:7]):
+            for nm, v in zip(names, f[4:8]):
                 if v.lower() == "active":
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "mem_mhz": float(np.median(mem)),
+                "mem_mhz_min": float(np.min(mem)), "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def _dist():
@@ -185,10 +186,13 @@ def run_ours(args):
     from paper_2601_19911_gb300 import datagen, olap
 
     n, k = 1 << args.log2n, args.k
-    ctx = olap.Context(torch.cuda.current_device())
-    keys = datagen.topk_keys(n, "uniform", "i64", seed=1)
+    filt = {"bulk": olap.FILTER_BULK, "regs": olap.FILTER_REGS}[args.filter]
+    ctx = olap.Context(torch.cuda.current_device(), topk_filter=filt, topk_tile_bytes=args.tile,
+                       topk_stages=args.stages, topk_ctas_per_sm=args.ctas_per_sm)
+    keys = datagen.topk_keys(n, args.dist, args.key_type, seed=1)
+    w = keys.dtype.itemsize
     dk = torch.from_numpy(keys).cuda()
-    ok = torch.empty(k, dtype=torch.int64, device="cuda")
+    ok = torch.empty(k, dtype=dk.dtype, device="cuda")
     orow = torch.empty(k, dtype=torch.int32, device="cuda")
     stream = torch.cuda.ExternalStream(ctx.stream)
 
@@ -213,13 +217,14 @@ def run_ours(args):
         torch.cuda.synchronize()
     total_ms = start.elapsed_time(end)
     per_launch = [a.elapsed_time(b) for a, b in evs]
+    phases = ctx.topk_info()
     total_ms = _max_over_ranks(total_ms, world)
     ms = total_ms / args.steps
     value = world * n / (ms * 1e-3) / 1e9
 
     # -- end to end through the public blocking call, pinned host keys -----------
     hk = torch.from_numpy(keys).pin_memory()
-    hok = torch.empty(k, dtype=torch.int64).pin_memory()
+    hok = torch.empty(k, dtype=dk.dtype).pin_memory()
     horow = torch.empty(k, dtype=torch.int32).pin_memory()
     for _ in range(2):
         ctx.topk(hk, k, olap.DESC, out_keys=hok, out_rowids=horow)
@@ -232,22 +237,24 @@ def run_ours(args):
     e2e_value = world * n / e2e_s / 1e9
 
     peak, peak_kind = _peaks()
-    algo_bytes = n * 8 + 24 * k
+    algo_bytes = n * w + 24 * k
     kern_ms = float(np.mean(per_launch))
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"topk_i64_uniform_n2^{args.log2n}_k{k}_desc", "n": n, "k": k,
-                   "order": "desc", "rowids": "implicit", "l2": "inputs larger than L2 (2 GiB keys)",
+        "vs_baseline": None, "dtype": {"i64": "int64", "f32": "float32"}[args.key_type], "data": "synthetic",
+        "config": {"workload": f"topk_{args.key_type}_{args.dist}_n2^{args.log2n}_k{k}_desc", "n": n, "k": k,
+                   "order": "desc", "rowids": "implicit",
+                   "l2": f"inputs larger than L2 ({n * w / 2**30:.2f} GiB keys)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": args.traffic, "peak_kind": peak_kind,
                      "kernel": "olap::topk_kernel", "algorithmic_bytes_per_launch": algo_bytes,
-                     "kernel_ms": kern_ms},
-        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * 8,
-                "d2h_bytes_per_step": k * 12 + 4, "ms_per_step": e2e_s * 1e3},
+                     "kernel_ms": kern_ms, "filter": args.filter, "last_launch": phases,
+                     "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
+        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w,
+                "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
@@ -270,10 +277,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=1000)
     ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--key-type", default="i64", choices=["i64", "f32"])
+    ap.add_argument("--dist", default="uniform", choices=["uniform", "ascending", "dup1024"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="bulk-copy bytes (0 = library default)")
+    ap.add_argument("--stages", type=int, default=0, help="copies in flight per CTA (0 = default)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM (0 = default)")
+    ap.add_argument("--filter", default="regs", choices=["bulk", "regs"],
+                    help="Top-K streaming pass: register loads (default) or bulk-copy ring")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

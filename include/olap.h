@@ -71,7 +71,16 @@ typedef struct {
     int block_threads;          /* threads per CTA for streaming kernels (256/512/1024) */
     double load_factor;         /* join table load factor in (0, 0.9]; 0 => 0.5 */
     uint64_t staging_bytes;     /* size of each pinned staging buffer; 0 => 64 MiB */
+    int topk_filter;            /* olap_filter: how the Top-K streaming pass reads keys */
+    int topk_tile_bytes;        /* bulk-copy size of the streaming pass (multiple of 8 KiB) */
+    int topk_stages;            /* bulk copies in flight per CTA (1..16) */
+    int topk_ctas_per_sm;       /* resident CTAs per SM of the Top-K grid (1..4) */
 } olap_opts;
+
+/* Streaming-pass flavour of Top-K: 16-byte register loads (the default), or
+ * bulk asynchronous copies (TMA engine) through a ring of shared-memory
+ * stages. */
+typedef enum { OLAP_FILTER_AUTO = 0, OLAP_FILTER_BULK = 1, OLAP_FILTER_REGS = 2 } olap_filter;
 
 /* Create a context on opts->device (opts may be NULL for all defaults).
  * Fails with OLAP_E_CUDA when no CUDA device is usable. */
@@ -116,6 +125,20 @@ olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type typ
                             const uint32_t* d_rowids, uint64_t n, uint64_t k, olap_order order,
                             void* d_out_keys, uint32_t* d_out_rowids, int32_t* dev_status,
                             void* stream);
+
+/* What the last Top-K on this context did (diagnostics; blocks until the
+ * context's stream is idle).  path: 0 = radix refine over the input (small n
+ * or large k), 1 = sampled threshold + one streaming pass + refine over the
+ * candidates, 2 = sample misjudged, refine over the input.  phase_ns:
+ * sample, filter, refine, split, finish/sort, total, and within finish the
+ * small-bucket sort and the survivor sort (device %globaltimer). */
+typedef struct {
+    int path;
+    int refine_passes;
+    uint64_t candidates;
+    uint64_t phase_ns[8];
+} olap_topk_info;
+olap_status olap_topk_info_last(olap_ctx* ctx, olap_topk_info* out);
 
 /* ------------------------------------------------------------------------
  * Top-K that allocates nothing (no counterpart in the paper: a deployment

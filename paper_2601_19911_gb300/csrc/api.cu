@@ -190,7 +190,9 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
     a.out_keys = d_out_keys;
     a.out_rowids = d_out_rowids;
     a.dev_status = dev_status;
-    cudaError_t e = topk_launch(a, ctx->topk_grid, stream);
+    a.filter = ctx->opts.topk_filter == OLAP_FILTER_BULK ? TK_FILTER_BULK : TK_FILTER_REGS;
+    ctx->last_topk_ctl = a.ctl;
+    cudaError_t e = topk_launch(a, ctx->topk_geom, stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(ctx, e, "Top-K launch");
@@ -223,7 +225,8 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     *out = nullptr;
     olap_ctx* ctx = new olap_ctx();
     if (opts) ctx->opts = *opts;
-    if (ctx->opts.load_factor < 0.0 || ctx->opts.load_factor > 0.9) {
+    if (ctx->opts.load_factor < 0.0 || ctx->opts.load_factor > 0.9 || ctx->opts.topk_filter < 0 ||
+        ctx->opts.topk_filter > OLAP_FILTER_REGS) {
         delete ctx;
         return OLAP_E_INVALID;
     }
@@ -249,8 +252,14 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     }
     if ((e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess)
         return bail(e);
-    ctx->topk_grid = topk_grid(ctx->device, 2);
-    if (ctx->topk_grid <= 0) return bail(cudaErrorUnknown);
+    TopkGeom g;
+    if (!topk_geometry(ctx->device, ctx->opts.topk_tile_bytes, ctx->opts.topk_stages,
+                       ctx->opts.topk_ctas_per_sm, &g)) {
+        cudaGetLastError();
+        olap_ctx_destroy(ctx);
+        return OLAP_E_INVALID;
+    }
+    ctx->topk_geom = g;
     if ((e = cudaMallocHost(reinterpret_cast<void**>(&ctx->host_status), 64)) != cudaSuccess) return bail(e);
     *out = ctx;
     return OLAP_OK;
@@ -367,3 +376,27 @@ olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type typ
 }
 
 }  // extern "C"
+
+extern "C" olap_status olap_topk_info_last(olap_ctx* ctx, olap_topk_info* out) {
+    if (!ctx || !out) return OLAP_E_INVALID;
+    std::memset(out, 0, sizeof(*out));
+    if (!ctx->last_topk_ctl) return fail(ctx, OLAP_E_INVALID, "no Top-K has run on this context");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Top-K info");
+    TopkCtl c;
+    e = cudaMemcpy(&c, ctx->last_topk_ctl, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Top-K info read-back");
+    out->path = c.path;
+    out->refine_passes = c.passes;
+    out->candidates = c.cand_count;
+    auto d = [&](int a, int b) { return c.ts[b] > c.ts[a] ? c.ts[b] - c.ts[a] : 0ull; };
+    out->phase_ns[0] = d(0, 1);
+    out->phase_ns[1] = d(1, 2);
+    out->phase_ns[2] = d(2, 4);
+    out->phase_ns[3] = d(4, 5);
+    out->phase_ns[4] = d(5, 6);
+    out->phase_ns[5] = d(0, 6);
+    out->phase_ns[6] = d(5, 7);
+    out->phase_ns[7] = d(7, 8);
+    return OLAP_OK;
+}

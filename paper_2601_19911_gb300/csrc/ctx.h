@@ -8,6 +8,7 @@
 #include <string>
 
 #include "olap.h"
+#include "topk.cuh"
 
 struct olap_ctx {
     int device = 0;
@@ -15,7 +16,7 @@ struct olap_ctx {
     bool own_stream = false;
     olap_opts opts{};
     int sm_count = 0;
-    int topk_grid = 0;                // CTAs of the cooperative Top-K grid
+    olap::TopkGeom topk_geom{};       // Top-K launch geometry
 
     // Device scratch arena (grow-only).  Its first bytes hold the grid
     // barrier of the cooperative kernels, which must start zeroed.
@@ -36,6 +37,9 @@ struct olap_ctx {
 
     // Small pinned word for device status read-back.
     int32_t* host_status = nullptr;
+
+    // Control block of the last Top-K launched (diagnostics).
+    void* last_topk_ctl = nullptr;
 
     // Device memory held by join tables created through this context.
     uint64_t table_bytes = 0;

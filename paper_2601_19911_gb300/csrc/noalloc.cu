@@ -5,7 +5,7 @@
 // database buffer manager, a framework's caching allocator), plug-in and UDF
 // hosts that forbid allocation inside an operator, and latency-critical paths
 // that cannot accept the device-wide synchronisation cudaMalloc/cudaFree may
-// cause.  olap_topk_noalloc serves them: it runs the same Top-K kernel as
+// cause.  olap_topk_noalloc serves them: it runs the same Top-K kernels as
 // olap_topk_async, but its working memory is a fixed array compiled into this
 // file, so the call itself allocates nothing.  The caller still provides the
 // input and output buffers.
@@ -39,7 +39,7 @@ constexpr int MAX_DEVICES = 64;
 struct DeviceSetup {
     bool done = false;
     void* scratch = nullptr;   // device address of g_noalloc_scratch on this device
-    int grid = 0;              // cooperative CTAs of the Top-K kernel
+    olap::TopkGeom geom{};     // launch geometry of the Top-K kernels
 };
 
 std::mutex g_setup_lock;
@@ -55,13 +55,13 @@ olap_status setup_device(int dev, DeviceSetup* out) {
             cudaGetLastError();
             return OLAP_E_CUDA;
         }
-        const int grid = olap::topk_grid(dev, 2);
-        if (grid <= 0) {
+        olap::TopkGeom g;
+        if (!olap::topk_geometry(dev, 0, 0, 0, &g)) {
             cudaGetLastError();
             return OLAP_E_CUDA;
         }
         s.scratch = p;
-        s.grid = grid;
+        s.geom = g;
         s.done = true;
     }
     *out = s;
@@ -109,6 +109,7 @@ extern "C" olap_status olap_topk_noalloc(const void* d_keys, olap_key_type type,
     a.f32 = type == OLAP_KEY_F32;
     a.desc = order == OLAP_DESC;
     olap::topk_carve(a, plan, ds.scratch);
+    a.filter = olap::TK_FILTER_REGS;
     a.out_keys = d_out_keys;
     a.out_rowids = d_out_rowids;
     a.dev_status = dev_status;
@@ -118,7 +119,7 @@ extern "C" olap_status olap_topk_noalloc(const void* d_keys, olap_key_type type,
         cudaGetLastError();
         return OLAP_E_CUDA;
     }
-    if (olap::topk_launch(a, ds.grid, s) != cudaSuccess) {
+    if (olap::topk_launch(a, ds.geom, s) != cudaSuccess) {
         cudaGetLastError();
         return OLAP_E_CUDA;
     }

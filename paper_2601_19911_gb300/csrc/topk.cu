@@ -176,7 +176,11 @@ __device__ __forceinline__ void write_result(const TopkArgs& a, uint64_t i, uint
     a.out_rowids[i] = rid;
 }
 
-// Phase 0 (CTA 0): rank word of the sample's r-th smallest entry.
+// Prepare kernel: a threshold rank word for the streaming pass from a
+// stratified sample of TK_SAMPLE keys.  Radix select with 12-bit digits on the
+// sample held in registers; it stops as soon as the upper edge of the chosen
+// bucket has between r and r + 8 samples at or below it (any such threshold
+// serves), which for spread-out keys is after the first digit.
 __device__ uint64_t sample_threshold(const TopkArgs& a, unsigned* sh, unsigned long long* sc) {
     uint64_t s[TK_SPT];
     const uint64_t n = a.n;
@@ -187,59 +191,191 @@ __device__ uint64_t sample_threshold(const TopkArgs& a, unsigned* sh, unsigned l
         s[j] = load_input(a, pos).r;
     }
     const int kb = a.f32 ? 32 : 64;
+    const unsigned long long r = a.sample_rank;
     uint64_t prefix = 0;
-    unsigned long long rem = a.sample_rank;
-    for (int L = 0; L < kb; L += 8) {
-        for (int b = threadIdx.x; b < 256; b += TK_TPB) sh[b] = 0;
+    unsigned long long rem = r, cum = 0;
+    for (int L = 0; L < kb; L += TK_DIG) {
+        const int d = min(TK_DIG, kb - L);
+        for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB) sh[b] = 0;
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < TK_SPT; ++j) {
             const bool match = (L == 0) || (((s[j] ^ prefix) >> (64 - L)) == 0);
-            if (match) atomicAdd(&sh[(s[j] >> (56 - L)) & 255u], 1u);
+            if (match) atomicAdd(&sh[static_cast<unsigned>((s[j] << L) >> (64 - d))], 1u);
         }
         __syncthreads();
-        if (threadIdx.x < 32) {
-            const unsigned lane = threadIdx.x;
-            unsigned v[8];
-            unsigned loc = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                v[j] = sh[lane * 8 + j];
-                loc += v[j];
-            }
-            unsigned incl = loc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= static_cast<unsigned>(o)) incl += t;
-            }
-            unsigned run = incl - loc;
-            if (run < rem && rem <= run + loc) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (run < rem && rem <= run + v[j]) {
-                        sc[0] = lane * 8 + j;
-                        sc[1] = run;
-                    }
-                    run += v[j];
-                }
-            }
-        }
-        __syncthreads();
-        prefix |= static_cast<uint64_t>(sc[0]) << (56 - L);
-        rem -= sc[1];
-        __syncthreads();
+        const Pick pk = pick_bucket(sh, rem, sc);
+        prefix |= static_cast<uint64_t>(pk.b) << (64 - L - d);
+        rem -= pk.below;
+        cum += pk.below;
+        if (cum + pk.in_b <= r + 8) return prefix | ((1ull << (64 - L - d)) - 1ull);
     }
     return prefix;
 }
 
+// The threshold of the streaming pass moved into the key domain, so that a
+// key is tested with one XOR and one unsigned comparison and no transform:
+// `rank <= t` holds exactly when `(key ^ m) >= c` for the (m, c) below.
+//   int64: rank = key ^ SIGN (ASC) or its complement (DESC); the signed key
+//     order is the unsigned order of key ^ SIGN, and "<=" becomes ">=" on
+//     the complement.
+//   float32: the rank's significant half u(x) is <= t32 = t >> 32 (its low
+//     half is zero).  With y = x ^ ((x >> 31) & 0x7FFFFFFF) the signed image of
+//     totalOrder and L the signed limit on y, each of the four cases (order x
+//     sign of L) is one unsigned comparison of x under a fixed XOR mask:
+//       DESC, L >= 0: y >= L  <=>  x ^ 0x80000000 >= L ^ 0x80000000
+//       DESC, L <  0: y >= L  <=>  ~x >= ~(L ^ 0x7FFFFFFF)
+//       ASC,  L >= 0: y <= L  <=>  x ^ 0x7FFFFFFF >= L ^ 0x7FFFFFFF
+//       ASC,  L <  0: y <= L  <=>  x >= L ^ 0x7FFFFFFF
+//     (XOR with 0x7FFFFFFF reverses the signed order among negative values.)
+struct KeyLimit {
+    uint64_t m64, c64;
+    uint32_t m32, c32;
+};
+__device__ __forceinline__ KeyLimit key_limit(uint64_t t, bool desc) {
+    KeyLimit k;
+    const uint64_t lim = (desc ? ~t : t) ^ SIGN64;              // signed limit on the int64 key
+    // DESC: key >= lim  <=> key ^ SIGN >= lim ^ SIGN;  ASC: key <= lim <=> key ^ ~SIGN >= lim ^ ~SIGN
+    k.m64 = desc ? SIGN64 : ~SIGN64;
+    k.c64 = lim ^ k.m64;
+    const uint32_t t32 = static_cast<uint32_t>(t >> 32);
+    const int32_t L = static_cast<int32_t>((desc ? ~t32 : t32) ^ 0x80000000u);
+    const uint32_t uL = static_cast<uint32_t>(L);
+    if (desc) {
+        if (L >= 0) { k.m32 = 0x80000000u; k.c32 = uL ^ 0x80000000u; }
+        else        { k.m32 = 0xFFFFFFFFu; k.c32 = ~(uL ^ 0x7FFFFFFFu); }
+    } else {
+        if (L >= 0) { k.m32 = 0x7FFFFFFFu; k.c32 = uL ^ 0x7FFFFFFFu; }
+        else        { k.m32 = 0u;          k.c32 = uL ^ 0x7FFFFFFFu; }
+    }
+    return k;
+}
+__device__ __forceinline__ bool pass_i64(uint64_t bits, const KeyLimit& k) { return (bits ^ k.m64) >= k.c64; }
+__device__ __forceinline__ bool pass_f32(uint32_t bits, const KeyLimit& k) { return (bits ^ k.m32) >= k.c32; }
+
+// Hits of the streaming pass are staged per warp in shared memory and
+// flushed to the global candidate buffer WS_CAP at a time: one atomic on the
+// global count per flush instead of one per warp-vector with a hit (a single
+// global counter hit by every SM serialises in L2), and coalesced writes.
+constexpr int WS_CAP = 256;
+struct WarpStage {
+    uint64_t* r;          // WS_CAP rank words (shared)
+    uint32_t* idx;        // WS_CAP key indices (shared)
+    unsigned count;       // entries held (the same in every lane)
+};
+constexpr int WS_BYTES = WS_CAP * 12;
+
+__device__ __forceinline__ WarpStage warp_stage(unsigned char* base) {
+    const unsigned w = threadIdx.x >> 5;
+    unsigned char* p = base + static_cast<size_t>(w) * WS_BYTES;
+    return WarpStage{reinterpret_cast<uint64_t*>(p), reinterpret_cast<uint32_t*>(p + WS_CAP * 8), 0u};
+}
+
+// Move the warp's staged hits to the candidate buffer (all 32 lanes call).
+__device__ __forceinline__ void stage_flush(const TopkArgs& a, WarpStage& ws) {
+    if (ws.count == 0) return;
+    __syncwarp();
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctl->cand_count, static_cast<unsigned long long>(ws.count));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (unsigned j = lane; j < ws.count; j += 32) {
+        const unsigned long long pos = base + j;
+        if (pos < a.cand_cap) {
+            const uint32_t idx = ws.idx[j];
+            a.cand_r[pos] = ws.r[j];
+            a.cand_rid[pos] = a.rowids ? a.rowids[idx] : idx;
+        }
+    }
+    __syncwarp();
+    ws.count = 0;
+}
+
+// Test the VEC keys of one 16-byte vector (keys idx0 .. idx0 + VEC - 1)
+// against the threshold and stage the hits.  Called by all 32 lanes of a
+// warp together.
+template <bool F32>
+__device__ __forceinline__ void filter_vector(const TopkArgs& a, const KeyLimit& lim, uint4 x, bool valid,
+                                              uint64_t idx0, WarpStage& ws) {
+    constexpr int VEC = F32 ? 4 : 2;
+    bool any;
+    if (F32) {
+        any = pass_f32(x.x, lim) | pass_f32(x.y, lim) | pass_f32(x.z, lim) | pass_f32(x.w, lim);
+    } else {
+        any = pass_i64(static_cast<uint64_t>(x.x) | (static_cast<uint64_t>(x.y) << 32), lim) |
+              pass_i64(static_cast<uint64_t>(x.z) | (static_cast<uint64_t>(x.w) << 32), lim);
+    }
+    if (!__any_sync(0xFFFFFFFFu, any && valid)) return;
+    unsigned hit = 0;
+    if (valid) {
+        if (F32) {
+            hit = (pass_f32(x.x, lim) ? 1u : 0u) | (pass_f32(x.y, lim) ? 2u : 0u) |
+                  (pass_f32(x.z, lim) ? 4u : 0u) | (pass_f32(x.w, lim) ? 8u : 0u);
+        } else {
+            hit = (pass_i64(static_cast<uint64_t>(x.x) | (static_cast<uint64_t>(x.y) << 32), lim) ? 1u : 0u) |
+                  (pass_i64(static_cast<uint64_t>(x.z) | (static_cast<uint64_t>(x.w) << 32), lim) ? 2u : 0u);
+        }
+    }
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned bal[VEC];
+    unsigned total = 0;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        bal[e] = __ballot_sync(0xFFFFFFFFu, (hit >> e) & 1u);
+        total += __popc(bal[e]);
+    }
+    if (ws.count + total > WS_CAP) stage_flush(a, ws);
+    unsigned before = ws.count;
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        if ((hit >> e) & 1u) {
+            const unsigned pos = before + __popc(bal[e] & lt);
+            uint64_t r;
+            if (F32) r = rank_f32(w[e], a.desc);
+            else r = rank_i64(static_cast<uint64_t>(w[2 * e]) | (static_cast<uint64_t>(w[2 * e + 1]) << 32), a.desc);
+            ws.r[pos] = r;
+            ws.idx[pos] = static_cast<uint32_t>(idx0 + e);
+        }
+        before += __popc(bal[e]);
+    }
+    ws.count += total;
+}
+
+// The unaligned head [0, head) and ragged tail [tail0, n) of the keys: at
+// most 2 * VEC - 2 keys, one per lane of warp 0 of CTA 0.
+__device__ __forceinline__ void filter_ends(const TopkArgs& a, uint64_t t, uint64_t head, uint64_t tail0) {
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const uint64_t rest = head + (a.n - tail0);
+    const uint64_t j = threadIdx.x;
+    const bool valid = j < rest;
+    uint64_t idx = 0, r = ~0ull;
+    if (valid) {
+        idx = j < head ? j : tail0 + (j - head);
+        r = load_input(a, idx).r;
+    }
+    const bool hit = valid && r <= t;
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
+    if (!bal) return;
+    unsigned long long base = 0;
+    if (threadIdx.x == 0) base = atomicAdd(&a.ctl->cand_count, static_cast<unsigned long long>(__popc(bal)));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (hit) {
+        const unsigned long long pos = base + __popc(bal & ((1u << threadIdx.x) - 1u));
+        if (pos < a.cand_cap) {
+            a.cand_r[pos] = r;
+            a.cand_rid[pos] = a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx);
+        }
+    }
+}
+
 // Phase 1: the single streaming pass.  Appends (rank word, row-id) of every
 // key whose rank word is <= t; counts all of them.
-template <bool F32>
-__device__ void filter_pass(const TopkArgs& a, uint64_t t) {
+template <bool F32, int TPB>
+__device__ void filter_pass(const TopkArgs& a, uint64_t t, unsigned char* stage_smem) {
     constexpr int W = F32 ? 4 : 8;
     constexpr int VEC = 16 / W;
-    TopkCtl* ctl = a.ctl;
     const uint64_t n = a.n;
     const uintptr_t addr = reinterpret_cast<uintptr_t>(a.keys);
     const uint64_t head0 = ((16 - (addr & 15)) & 15) / W;
@@ -247,79 +383,144 @@ __device__ void filter_pass(const TopkArgs& a, uint64_t t) {
     const uint64_t nvec = (n - head) / VEC;
     const uint64_t tail0 = head + nvec * VEC;
     const unsigned char* vbase = static_cast<const unsigned char*>(a.keys) + head * W;
+    const KeyLimit lim = key_limit(t, a.desc);
+    WarpStage ws = warp_stage(stage_smem);
 
-    auto emit = [&](unsigned cnt, const uint64_t* rs, const uint64_t* idxs) {
-        const unsigned long long pos = warp_append(&ctl->cand_count, cnt);
-        for (unsigned j = 0; j < cnt; ++j) {
-            if (pos + j < a.cand_cap) {
-                a.cand_r[pos + j] = rs[j];
-                a.cand_rid[pos + j] = a.rowids ? a.rowids[idxs[j]] : static_cast<uint32_t>(idxs[j]);
-            }
-        }
-    };
-
-    const uint64_t per_block = static_cast<uint64_t>(TK_TPB) * TK_UNROLL;
+    const uint64_t per_block = static_cast<uint64_t>(TPB) * TK_UNROLL;
     const uint64_t stride = per_block * gridDim.x;
     for (uint64_t bb = per_block * blockIdx.x; bb < nvec; bb += stride) {
         uint4 v[TK_UNROLL];
 #pragma unroll
         for (int u = 0; u < TK_UNROLL; ++u) {
-            const uint64_t vi = bb + static_cast<uint64_t>(u) * TK_TPB + threadIdx.x;
+            const uint64_t vi = bb + static_cast<uint64_t>(u) * TPB + threadIdx.x;
             if (vi < nvec) v[u] = ld_stream_v4(vbase + vi * 16);
             else v[u] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
         }
-        uint64_t rs[TK_UNROLL * VEC];
-        unsigned hit = 0;
 #pragma unroll
         for (int u = 0; u < TK_UNROLL; ++u) {
-            const uint64_t vi = bb + static_cast<uint64_t>(u) * TK_TPB + threadIdx.x;
-            const bool ok = vi < nvec;
-            if (F32) {
-                const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    rs[u * 4 + e] = rank_f32(w[e], a.desc);
-                    if (ok && rs[u * 4 + e] <= t) hit |= 1u << (u * 4 + e);
-                }
-            } else {
-                const uint64_t w0 = static_cast<uint64_t>(v[u].x) | (static_cast<uint64_t>(v[u].y) << 32);
-                const uint64_t w1 = static_cast<uint64_t>(v[u].z) | (static_cast<uint64_t>(v[u].w) << 32);
-                rs[u * 2 + 0] = rank_i64(w0, a.desc);
-                rs[u * 2 + 1] = rank_i64(w1, a.desc);
-                if (ok && rs[u * 2 + 0] <= t) hit |= 1u << (u * 2 + 0);
-                if (ok && rs[u * 2 + 1] <= t) hit |= 1u << (u * 2 + 1);
-            }
-        }
-        if (__any_sync(0xFFFFFFFFu, hit != 0)) {
-            uint64_t hr[TK_UNROLL * VEC], hi[TK_UNROLL * VEC];
-            unsigned c = 0;
-#pragma unroll
-            for (int j = 0; j < TK_UNROLL * VEC; ++j) {
-                if (hit & (1u << j)) {
-                    const int u = j / VEC, e = j % VEC;
-                    const uint64_t vi = bb + static_cast<uint64_t>(u) * TK_TPB + threadIdx.x;
-                    hr[c] = rs[j];
-                    hi[c] = head + vi * VEC + e;
-                    ++c;
-                }
-            }
-            emit(c, hr, hi);
+            const uint64_t vi = bb + static_cast<uint64_t>(u) * TPB + threadIdx.x;
+            filter_vector<F32>(a, lim, v[u], vi < nvec, head + vi * VEC, ws);
         }
     }
-    // Unaligned head and ragged tail: at most 2*VEC - 2 keys, one per lane of
-    // warp 0 of CTA 0.
-    if (blockIdx.x == 0 && threadIdx.x < 32) {
-        const uint64_t rest = head + (n - tail0);
-        const uint64_t j = threadIdx.x;
-        uint64_t r = 0, idx = 0;
-        unsigned c = 0;
-        if (j < rest) {
-            idx = j < head ? j : tail0 + (j - head);
-            r = load_input(a, idx).r;
-            c = r <= t ? 1u : 0u;
+    stage_flush(a, ws);
+    filter_ends(a, t, head, tail0);
+}
+
+// Issue the bulk copy of the tile at byte offset `off` of the key body into
+// ring slot `s` (the last tile of the body may be short).
+__device__ __forceinline__ void issue_tile(unsigned char* smem, uint64_t* full, const unsigned char* vbase,
+                                           uint64_t body, uint64_t off, uint32_t s, uint32_t tile,
+                                           uint64_t policy) {
+    const uint64_t left = body - off;
+    const uint32_t bytes = static_cast<uint32_t>(left < tile ? left : tile);
+    mbar_arrive_expect_tx(&full[s], bytes);
+    bulk_g2s(smem + static_cast<size_t>(s) * tile, vbase + off, bytes, &full[s], policy);
+}
+
+// Phase 1, bulk-copy flavour: each CTA streams its tiles (tile i of the
+// grid-interleaved order) through a ring of `stages` shared-memory slots.
+// Thread 0 issues cp.async.bulk copies; a slot's "full" mbarrier completes
+// when its bytes land, and its "empty" mbarrier when every warp has read it,
+// after which thread 0 refills it.  No CTA-wide barrier per tile.  Returns
+// false if a copy never landed (bounded waits).
+template <bool F32, int TPB>
+__device__ bool filter_pass_bulk(const TopkArgs& a, uint64_t t, unsigned char* smem) {
+    constexpr int W = F32 ? 4 : 8;
+    constexpr int VEC = 16 / W;
+    constexpr unsigned NWARPS = TPB / 32;
+    const uint32_t tile = static_cast<uint32_t>(a.tile_bytes);
+    const uint32_t stages = static_cast<uint32_t>(a.stages);
+    const uint64_t n = a.n;
+    const uintptr_t addr = reinterpret_cast<uintptr_t>(a.keys);
+    const uint64_t head0 = ((16 - (addr & 15)) & 15) / W;
+    const uint64_t head = head0 < n ? head0 : n;
+    const uint64_t nvec = (n - head) / VEC;
+    const uint64_t tail0 = head + nvec * VEC;
+    const unsigned char* vbase = static_cast<const unsigned char*>(a.keys) + head * W;
+    const uint64_t body = nvec * 16;
+    const uint64_t ntiles = (body + tile - 1) / tile;
+    const uint64_t my_n = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const KeyLimit lim = key_limit(t, a.desc);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(tile) * stages);
+    uint64_t* empty = full + TK_MAX_STAGES;
+    WarpStage ws = warp_stage(reinterpret_cast<unsigned char*>(empty + TK_MAX_STAGES));
+    const uint64_t step = static_cast<uint64_t>(gridDim.x) * tile;       // bytes between my tiles
+
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NWARPS);
         }
-        emit(c, &r, &idx);
+        mbar_fence_init();
     }
+    __syncthreads();
+    const uint64_t policy = l2_evict_first_policy();
+    uint64_t off = static_cast<uint64_t>(blockIdx.x) * tile;
+    uint64_t issued = 0;                                   // tiles issued (thread 0)
+    if (threadIdx.x == 0) {
+        const uint32_t pre = static_cast<uint32_t>(my_n < stages ? my_n : stages);
+        for (uint32_t s = 0; s < pre; ++s) issue_tile(smem, full, vbase, body, off + s * step, s, tile, policy);
+        issued = pre;
+    }
+    const uint64_t refill = static_cast<uint64_t>(stages) * step;
+    const unsigned lane = threadIdx.x & 31u;
+    uint32_t s = 0, par = 0;
+    bool ok = true;
+    for (uint64_t i = 0; i < my_n; ++i) {
+        if (!mbar_wait(&full[s], par)) {
+            ok = false;
+            break;
+        }
+        const uint64_t left = body - off;
+        const uint32_t nv = static_cast<uint32_t>((left < tile ? left : tile) / 16);
+        const unsigned char* st = smem + static_cast<size_t>(s) * tile;
+        const uint64_t idx_base = head + (off / 16) * VEC;
+        for (uint32_t vb = 0; vb < tile / 16; vb += TPB) {
+            const uint32_t v = vb + threadIdx.x;
+            const bool valid = v < nv;
+            uint4 x = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+            if (valid) x = ld_shared_v4(st + v * 16);
+            filter_vector<F32>(a, lim, x, valid, idx_base + static_cast<uint64_t>(v) * VEC, ws);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (threadIdx.x == 0 && i + stages < my_n) {
+            if (!mbar_wait(&empty[s], par)) {
+                ok = false;
+                break;
+            }
+            fence_proxy_async_smem();
+            issue_tile(smem, full, vbase, body, off + refill, s, tile, policy);
+            ++issued;
+        }
+        off += step;
+        if (++s == stages) {
+            s = 0;
+            par ^= 1u;
+        }
+    }
+    stage_flush(a, ws);
+    if (!__syncthreads_and(ok)) {
+        // Let the copies this CTA issued land before leaving.  Only the last
+        // `stages` issued tiles can still be in flight (every earlier fill of
+        // a slot was consumed before the slot was refilled).
+        if (threadIdx.x == 0) {
+            const uint64_t first = issued > stages ? issued - stages : 0;
+            for (uint64_t q = first; q < issued; ++q)
+                mbar_wait(&full[q % stages], static_cast<uint32_t>((q / stages) & 1));
+            atomicCAS(&a.ctl->err, 0, static_cast<int>(OLAP_E_TIMEOUT));
+        }
+        __syncthreads();
+        return false;
+    }
+    filter_ends(a, t, head, tail0);
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // One refine pass: histogram of digit [L, L+d) of the composites that match
@@ -427,7 +628,50 @@ __device__ __forceinline__ void report(const TopkArgs& a) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(TK_TPB, 2) topk_kernel(TopkArgs a) {
+// Kernel 1 of 3 (one CTA): reset the control block and the histograms, and
+// when the sampled path is taken estimate the filter threshold.
+__global__ void __launch_bounds__(TK_TPB) topk_prepare_kernel(TopkArgs a) {
+    __shared__ unsigned sh[TK_BINS];
+    __shared__ unsigned long long sc[24];
+    TopkCtl* ctl = a.ctl;
+    if (threadIdx.x == 0) {
+        ctl->ts[0] = gtimer();
+        ctl->cand_count = 0;
+        ctl->out_count = 0;
+        ctl->eq_count = 0;
+        ctl->small_count = 0;
+        ctl->err = 0;
+        ctl->path = a.use_sample ? 1 : 0;
+        ctl->passes = 0;
+        ctl->thresh = ~0ull;
+    }
+    for (int b = threadIdx.x; b < 3 * TK_BINS; b += TK_TPB) a.ghist[b] = 0;
+    if (a.use_sample) {
+        const uint64_t t = sample_threshold(a, sh, sc);
+        if (threadIdx.x == 0) ctl->thresh = t;
+    }
+    if (threadIdx.x == 0) ctl->ts[1] = gtimer();
+}
+
+// Kernel 2 of 3 (sampled path only): the single streaming pass over the keys,
+// bulk-copy flavour.  Independent CTAs, several per SM.
+template <bool F32>
+__global__ void __launch_bounds__(TKF_TPB, 4) topk_filter_bulk_kernel(TopkArgs a) {
+    extern __shared__ __align__(128) unsigned char fsmem[];
+    const uint64_t t = __ldcg(&a.ctl->thresh);
+    filter_pass_bulk<F32, TKF_TPB>(a, t, fsmem);
+}
+
+// Kernel 2 of 3, register-load flavour.
+template <bool F32>
+__global__ void __launch_bounds__(TKR_TPB) topk_filter_regs_kernel(TopkArgs a) {
+    __shared__ __align__(16) unsigned char stage[(TKR_TPB / 32) * WS_BYTES];
+    const uint64_t t = __ldcg(&a.ctl->thresh);
+    filter_pass<F32, TKR_TPB>(a, t, stage);
+}
+
+// Kernel 3 of 3 (cooperative): refine, split, finish and sort.
+__global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long sc[24];
     TopkCtl* ctl = a.ctl;
@@ -437,42 +681,30 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_kernel(TopkArgs a) {
     uint64_t* sr = reinterpret_cast<uint64_t*>(smem);
     uint32_t* srid = reinterpret_cast<uint32_t*>(smem + TK_SMALL * 8);
 
-    // Phase 0: reset the control block and histograms; estimate the threshold.
-    if (blockIdx.x == 0) {
-        if (threadIdx.x == 0) {
-            ctl->cand_count = 0;
-            ctl->out_count = 0;
-            ctl->eq_count = 0;
-            ctl->small_count = 0;
-            ctl->err = 0;
-            ctl->path = a.use_sample ? 1 : 0;
-            ctl->passes = 0;
-        }
-        for (int b = threadIdx.x; b < 3 * TK_BINS; b += TK_TPB) a.ghist[b] = 0;
-        if (a.use_sample) {
-            const uint64_t t = sample_threshold(a, sh, sc);
-            if (threadIdx.x == 0) ctl->thresh = t;
-        }
-    }
-    if (!grid_sync(a.bar, &ctl->err)) return report(a);
-
-    // Phase 1: one streaming pass that keeps the keys at or below the threshold.
+    const bool stamp = blockIdx.x == 0 && threadIdx.x == 0;
+    if (stamp) ctl->ts[2] = gtimer();
+    // Source of the selection: the candidates of the streaming pass when the
+    // sample judged well (at least k of them, all stored), else the input.
     bool cand = false;
     uint64_t src_n = a.n;
     if (a.use_sample) {
-        const uint64_t t = *reinterpret_cast<volatile unsigned long long*>(&ctl->thresh);
-        if (a.f32) filter_pass<true>(a, t);
-        else filter_pass<false>(a, t);
-        if (!grid_sync(a.bar, &ctl->err)) return report(a);
-        const uint64_t cnt = *reinterpret_cast<volatile unsigned long long*>(&ctl->cand_count);
+        if (ld_volatile_i32(&ctl->err) != 0) return report(a);
+        const uint64_t cnt = __ldcg(&ctl->cand_count);
         cand = cnt >= a.k && cnt <= a.cand_cap;
         if (cand) src_n = cnt;
-        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->path = cand ? 1 : 2;
+        if (stamp) ctl->path = cand ? 1 : 2;
     }
+    const unsigned long long use_ts3 = stamp ? gtimer() : 0ull;
 
-    // Phase 2: radix refine of the (rank word, row-id) prefix.
+    // Phase 2: radix refine of the (rank word, row-id) prefix.  Candidates are
+    // all at or below the threshold, so they share its leading zero bits: the
+    // refine starts below them.
     uint64_t p0 = 0, p1 = 0, krem = a.k, bcnt = src_n;
     int L = 0, pass = 0;
+    if (cand) {
+        const int lz = __clzll(static_cast<long long>(__ldcg(&ctl->thresh)));
+        L = lz < kb ? lz : kb;
+    }
     while (bcnt > TK_SMALL && L < TB && krem < bcnt) {
         const int d = min(TK_DIG, TB - L);
         unsigned* gh = a.ghist + (pass % 3) * TK_BINS;
@@ -486,12 +718,17 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_kernel(TopkArgs a) {
         L += d;
         ++pass;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->passes = pass;
+    if (stamp) {
+        ctl->passes = pass;
+        ctl->ts[3] = use_ts3;
+        ctl->ts[4] = gtimer();
+    }
 
     // Phase 3: split around the prefix.
     const bool take_all = (krem == bcnt) || (L >= TB);
     split_pass(a, cand, src_n, p0, p1, L, kb, take_all, krem);
     if (!grid_sync(a.bar, &ctl->err)) return report(a);
+    if (stamp) ctl->ts[5] = gtimer();
 
     // Phase 4: finish and sort.
     if (blockIdx.x == 0) {
@@ -510,6 +747,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_kernel(TopkArgs a) {
             }
             __syncthreads();
         }
+        if (stamp) ctl->ts[7] = gtimer();
         if (a.k <= TK_SMALL) {
             const int cnt = static_cast<int>(a.k);
             for (int i = threadIdx.x; i < cnt; i += TK_TPB) {
@@ -518,8 +756,10 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_kernel(TopkArgs a) {
             }
             __syncthreads();
             block_sort(sr, srid, cnt);
+            if (stamp) ctl->ts[8] = gtimer();
             for (int i = threadIdx.x; i < cnt; i += TK_TPB) write_result(a, i, sr[i], srid[i]);
             if (threadIdx.x == 0 && a.dev_status) *a.dev_status = ld_volatile_i32(&ctl->err);
+            if (threadIdx.x == 0) ctl->ts[6] = gtimer();
         }
     }
     if (a.k <= TK_SMALL) return;
@@ -588,6 +828,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_kernel(TopkArgs a) {
     }
     for (uint64_t i = gtid; i < k; i += nthreads) write_result(a, i, __ldcg(src_r + i), __ldcg(src_rid + i));
     if (gtid == 0 && a.dev_status) *a.dev_status = ld_volatile_i32(&ctl->err);
+    if (gtid == 0) ctl->ts[6] = gtimer();
 }
 
 // ---------------------------------------------------------------------------
@@ -651,25 +892,90 @@ void topk_carve(TopkArgs& a, const TopkPlan& p, void* base) {
     }
     a.use_sample = p.use_sample;
     a.sample_rank = p.sample_rank;
+    a.filter = TK_FILTER_BULK;
 }
 
-int topk_grid(int device, int max_ctas_per_sm) {
+static int g_smem_limit[64] = {};   // dynamic shared bytes the filter kernel may use, per device
+
+static bool set_kernel_attrs(int device) {
+    if (g_smem_limit[device]) return true;
+    // Opt-in limit per block, less the filter kernel's static shared memory.
+    int optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, topk_filter_bulk_kernel<false>) != cudaSuccess)
+        return false;
+    const int lim = std::min<int>(optin - static_cast<int>(fa.sharedSizeBytes) - 256, TK_SMEM_MAX);
+    if (cudaFuncSetAttribute(topk_filter_bulk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             lim) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_bulk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             lim) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TK_SORT_SMEM) != cudaSuccess)
+        return false;
+    g_smem_limit[device] = lim;
+    return true;
+}
+
+bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, TopkGeom* out) {
+    TopkGeom g;
+    g.tile_bytes = tile_bytes ? tile_bytes : TK_TILE_DEFAULT;
+    g.stages = stages ? stages : TK_STAGES_DEFAULT;
+    g.ctas_per_sm = ctas_per_sm ? ctas_per_sm : TK_CTAS_PER_SM_DEFAULT;
+    if (g.tile_bytes < 16 * TKF_TPB || g.tile_bytes % (16 * TKF_TPB) || g.stages < 1 ||
+        g.stages > TK_MAX_STAGES || g.ctas_per_sm < 1 || g.ctas_per_sm > 8)
+        return false;
+    if (device < 0 || device >= 64) return false;
+    g.smem_bytes = g.tile_bytes * g.stages + 16 * TK_MAX_STAGES + (TKF_TPB / 32) * WS_BYTES;
     int sms = 0, per_sm = 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM) !=
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return false;
+    if (!set_kernel_attrs(device)) return false;
+    if (g.smem_bytes > g_smem_limit[device]) return false;
+    // Streaming filter: independent CTAs, capped at ctas_per_sm per SM.
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_filter_bulk_kernel<false>, TKF_TPB,
+                                                      g.smem_bytes) != cudaSuccess)
+        return false;
+    per_sm = std::min(per_sm, g.ctas_per_sm);
+    if (per_sm < 1) return false;
+    g.filter_grid = sms * per_sm;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_filter_regs_kernel<false>, TKR_TPB, 0) !=
         cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_kernel, TK_TPB, TK_SMEM) !=
+        return false;
+    g.regs_grid = sms * std::max(1, std::min(per_sm, 2048 / TKR_TPB));
+    // Cooperative select kernel: every CTA resident, two per SM at most.
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_select_kernel, TK_TPB, TK_SORT_SMEM) !=
         cudaSuccess)
-        return 0;
-    per_sm = std::min(per_sm, max_ctas_per_sm);
-    return sms * per_sm;
+        return false;
+    per_sm = std::min(per_sm, 2);
+    if (per_sm < 1) return false;
+    g.grid = sms * per_sm;
+    *out = g;
+    return true;
 }
 
-cudaError_t topk_launch(const TopkArgs& args, int grid, cudaStream_t stream) {
-    void* params[] = {const_cast<TopkArgs*>(&args)};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(topk_kernel), dim3(grid), dim3(TK_TPB),
-                                       params, TK_SMEM, stream);
+cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t stream) {
+    TopkArgs a = args;
+    a.tile_bytes = geom.tile_bytes;
+    a.stages = geom.stages;
+    topk_prepare_kernel<<<1, TK_TPB, 0, stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.use_sample) {
+        if (a.filter == TK_FILTER_REGS) {
+            if (a.f32) topk_filter_regs_kernel<true><<<geom.regs_grid, TKR_TPB, 0, stream>>>(a);
+            else topk_filter_regs_kernel<false><<<geom.regs_grid, TKR_TPB, 0, stream>>>(a);
+        } else {
+            if (a.f32)
+                topk_filter_bulk_kernel<true><<<geom.filter_grid, TKF_TPB, geom.smem_bytes, stream>>>(a);
+            else
+                topk_filter_bulk_kernel<false><<<geom.filter_grid, TKF_TPB, geom.smem_bytes, stream>>>(a);
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    void* params[] = {&a};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(topk_select_kernel), dim3(geom.grid),
+                                       dim3(TK_TPB), params, TK_SORT_SMEM, stream);
 }
 
 }  // namespace olap

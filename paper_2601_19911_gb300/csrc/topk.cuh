@@ -14,9 +14,23 @@ constexpr int TK_BINS = 1 << TK_DIG;
 constexpr int TK_SMALL = 4096;            // entries one CTA sorts in shared memory
 constexpr int TK_SAMPLE = 8192;           // sample size of the threshold estimate
 constexpr int TK_SPT = TK_SAMPLE / TK_TPB;
-constexpr int TK_UNROLL = 4;              // 16-byte loads in flight per thread
+constexpr int TK_UNROLL = 4;              // 16-byte loads in flight per thread (register filter)
 constexpr uint64_t TK_DIRECT_N = 1ull << 21;   // at or below: no sample, refine the input
-constexpr int TK_SMEM = TK_SMALL * 12;    // shared bytes: sort tile (or histogram)
+constexpr int TK_SORT_SMEM = TK_SMALL * 12;   // shared bytes of the sort tile (or histogram)
+constexpr int TK_MAX_STAGES = 16;         // full + empty mbarrier pairs reserved after the ring
+constexpr int TK_SMEM_MAX = 227 * 1024;   // opt-in shared memory per CTA
+// The streaming filter runs as its own kernel: 256-thread CTAs, several per
+// SM, each with a ring of bulk copies (default 16 KB x 3, four CTAs per SM);
+// the register-load flavour uses 512-thread CTAs.
+constexpr int TKF_TPB = 256;
+constexpr int TKR_TPB = 512;
+constexpr int TK_TILE_DEFAULT = 16384;
+constexpr int TK_STAGES_DEFAULT = 3;
+constexpr int TK_CTAS_PER_SM_DEFAULT = 4;
+
+// Filter flavours: 16-byte register loads, or bulk copies through a ring of
+// shared-memory stages (the default).
+enum TopkFilter { TK_FILTER_REGS = 0, TK_FILTER_BULK = 1 };
 
 // Device control block, zeroed by CTA 0 at the start of every launch.
 struct TopkCtl {
@@ -29,6 +43,10 @@ struct TopkCtl {
     int path;                        // 0 direct, 1 sampled candidates, 2 fallback
     int passes;                      // refine passes run
     int pad;
+    // %globaltimer stamps: prepare start, prepare end (sample done), select
+    // start (filter done), source decided, refine done, split done, end,
+    // small-buffer finish done, survivor sort done.
+    unsigned long long ts[9];
 };
 
 struct TopkArgs {
@@ -40,6 +58,9 @@ struct TopkArgs {
     int desc;
     int use_sample;
     unsigned sample_rank;            // 1-based rank of the threshold in the sample
+    int filter;                      // TopkFilter
+    int tile_bytes;                  // bulk-copy size (multiple of 16 * TK_TPB)
+    int stages;                      // copies in flight per CTA (<= TK_MAX_STAGES)
     TopkCtl* ctl;
     GridBar* bar;
     unsigned* ghist;                 // 3 x TK_BINS
@@ -71,10 +92,24 @@ size_t topk_scratch_bytes(const TopkPlan& p, uint64_t k);
 // Carve the scratch buffers of `args` out of `base` (256-byte aligned pieces).
 void topk_carve(TopkArgs& args, const TopkPlan& p, void* base);
 
-// CTAs of the cooperative grid on `device` (SMs x resident CTAs, capped).
-int topk_grid(int device, int max_ctas_per_sm);
+// Launch geometry of one Top-K: the filter's copy ring (tile x stages), the
+// filter grids and the cooperative select grid.
+struct TopkGeom {
+    int tile_bytes;
+    int stages;
+    int ctas_per_sm;       // filter CTAs per SM (cap)
+    int smem_bytes;        // filter dynamic shared bytes: ring + mbarriers
+    int grid;              // cooperative select kernel CTAs
+    int filter_grid;       // bulk-copy filter CTAs
+    int regs_grid;         // register-load filter CTAs
+};
+// Fill in the geometry for the requested ring on `device`; 0 values take the
+// defaults.  Returns false if the ring does not fit or no CTA fits.
+bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, TopkGeom* out);
 
-// Enqueue the cooperative kernel.  Returns the CUDA launch error.
-cudaError_t topk_launch(const TopkArgs& args, int grid, cudaStream_t stream);
+// Enqueue one Top-K: prepare (1 CTA), the streaming filter when the sampled
+// path is taken, then the cooperative select kernel.  Returns the first CUDA
+// launch error.
+cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t stream);
 
 }  // namespace olap

@@ -27,8 +27,9 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 # Every symbol include/olap.h declares, checked by the ABI tests.
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
-    "olap_topk", "olap_topk_async", "olap_topk_noalloc",
+    "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
 ]
+FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
 NOALLOC_MAX_N = 1 << 24
 NOALLOC_MAX_K = 4096
 
@@ -48,6 +49,19 @@ class olap_opts(ctypes.Structure):
         ("block_threads", ctypes.c_int),
         ("load_factor", ctypes.c_double),
         ("staging_bytes", ctypes.c_uint64),
+        ("topk_filter", ctypes.c_int),
+        ("topk_tile_bytes", ctypes.c_int),
+        ("topk_stages", ctypes.c_int),
+        ("topk_ctas_per_sm", ctypes.c_int),
+    ]
+
+
+class olap_topk_info(ctypes.Structure):
+    _fields_ = [
+        ("path", ctypes.c_int),
+        ("refine_passes", ctypes.c_int),
+        ("candidates", ctypes.c_uint64),
+        ("phase_ns", ctypes.c_uint64 * 8),
     ]
 
 
@@ -84,6 +98,8 @@ def load(path: str | None = None):
         lib.olap_topk.argtypes = [vp, vp, i32, vp, i32, u64, u64, i32, vp, vp, i32, ctypes.POINTER(u64)]
         lib.olap_topk_async.restype = i32
         lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
+        lib.olap_topk_info_last.restype = i32
+        lib.olap_topk_info_last.argtypes = [vp, ctypes.POINTER(olap_topk_info)]
         lib.olap_topk_noalloc.restype = i32
         lib.olap_topk_noalloc.argtypes = [vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         _bind_more(lib)
@@ -158,9 +174,12 @@ class Context:
     """An ``olap_ctx`` (one device, one stream, its scratch and staging)."""
 
     def __init__(self, device: int = 0, stream: int | None = None, mem_budget_bytes: int = 0,
-                 margin_ms: float = 0.0, load_factor: float = 0.0, staging_bytes: int = 0):
+                 margin_ms: float = 0.0, load_factor: float = 0.0, staging_bytes: int = 0,
+                 topk_filter: int = FILTER_AUTO, topk_tile_bytes: int = 0, topk_stages: int = 0,
+                 topk_ctas_per_sm: int = 0):
         self.lib = load()
-        opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, 0, load_factor, staging_bytes)
+        opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, 0, load_factor, staging_bytes,
+                         topk_filter, topk_tile_bytes, topk_stages, topk_ctas_per_sm)
         h = ctypes.c_void_p()
         st = self.lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h))
         if st != OK:
@@ -220,6 +239,14 @@ class Context:
         self.check(st)
         assert got.value == cnt
         return out_keys[:cnt], out_rowids[:cnt]
+
+    def topk_info(self) -> dict:
+        """olap_topk_info_last as a dict (phase times in microseconds)."""
+        info = olap_topk_info()
+        self.check(self.lib.olap_topk_info_last(self.h, ctypes.byref(info)))
+        names = ["sample", "filter", "refine", "split", "finish", "total", "finish_small", "finish_sort"]
+        return {"path": info.path, "refine_passes": info.refine_passes, "candidates": info.candidates,
+                "phase_us": {nm: info.phase_ns[i] / 1e3 for i, nm in enumerate(names)}}
 
     def topk_async(self, d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=None,
                    dev_status=None, stream: int | None = None):

@@ -162,6 +162,25 @@ def test_unaligned_device_pointer(ctx):
     np.testing.assert_array_equal(ok.cpu().numpy(), wk)
 
 
+@pytest.mark.parametrize("kt", ["i64", "f32"])
+def test_filter_flavours_agree(ctx, kt):
+    """The register-load (default) and bulk-copy streaming passes give the same bits."""
+    regs = olap.Context(0, topk_filter=olap.FILTER_BULK)
+    try:
+        for n, dist, k in (((1 << 21) + 5, "uniform", 100), (6_000_011, "dup1024", 3000),
+                           (4_194_304, "ascending", 10)):
+            keys = datagen.topk_keys(n, dist, kt, seed=n)
+            wk, wr = oracle.topk(keys, k, olap.DESC)
+            for c in (ctx, regs):
+                gk, gr = _gpu_topk(c, keys, k, olap.DESC)
+                np.testing.assert_array_equal(gr, wr)
+                np.testing.assert_array_equal(_bits(gk), _bits(wk))
+                info = c.topk_info()
+                assert info["path"] in (1, 2) and info["candidates"] >= k
+    finally:
+        regs.close()
+
+
 def test_golden_fixtures(ctx):
     from tests.golden import make_golden
     for case in make_golden.TOPK_CASES:
