@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
     const int TB = kb + 32;
     unsigned* sh = reinterpret_cast<unsigned*>(smem);
     uint64_t* sr = reinterpret_cast<uint64_t*>(smem);
-    uint32_t* srid = reinterpret_cast<uint32_t*>(smem + TK_SMALL * 8);
+    uint32_t* srid = reinterpret_cast<uint32_t*>(smem + TK_RANK_MAX * 8);
 
     const bool stamp = blockIdx.x == 0 && threadIdx.x == 0;
     if (stamp) ctl->ts[2] = gtimer();
@@ -730,7 +730,193 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
     if (!grid_sync(a.bar, &ctl->err)) return report(a);
     if (stamp) ctl->ts[5] = gtimer();
 
-    // Phase 4: finish and sort.
+    // Phase 4, survivors that fit one CTA's shared memory (every K <= 4096):
+    // each warp of the grid takes survivors one at a time and computes its
+    // final position as its rank -- the number of entries of its own set
+    // that order before it (equal entries by position), so ranks are
+    // distinct.  The "below" entries (prefix < P) precede every bucket entry;
+    // a bucket entry is kept when its rank within the bucket is below krem.
+    {
+        const uint64_t nb = take_all ? a.k : a.k - krem;     // out_r0[0, nb)
+        const uint64_t ns = take_all ? 0 : bcnt;             // small buffer
+        if (nb + ns <= TK_RANK_MAX) {
+            const int nbi = static_cast<int>(nb), nsi = static_cast<int>(ns);
+            for (int i = threadIdx.x; i < nbi; i += TK_TPB) {
+                sr[i] = __ldcg(a.out_r0 + i);
+                srid[i] = __ldcg(a.out_rid0 + i);
+            }
+            for (int i = threadIdx.x; i < nsi; i += TK_TPB) {
+                sr[nbi + i] = __ldcg(a.small_r + i);
+                srid[nbi + i] = __ldcg(a.small_rid + i);
+            }
+            __syncthreads();
+            if (stamp) ctl->ts[7] = gtimer();
+            const unsigned lane = threadIdx.x & 31u;
+            const int nwarps = static_cast<int>(gridDim.x) * (TK_TPB / 32);
+            const int gw = static_cast<int>(blockIdx.x) * (TK_TPB / 32) + static_cast<int>(threadIdx.x >> 5);
+            for (int e = gw; e < nbi + nsi; e += nwarps) {
+                const bool below = e < nbi;
+                const int lo = below ? 0 : nbi, hi = below ? nbi : nbi + nsi;
+                const uint64_t er = sr[e];
+                const uint32_t erid = srid[e];
+                unsigned c = 0;
+                for (int j = lo + static_cast<int>(lane); j < hi; j += 32) {
+                    const uint64_t jr = sr[j];
+                    const uint32_t jrid = srid[j];
+                    c += (jr < er || (jr == er && (jrid < erid || (jrid == erid && j < e)))) ? 1u : 0u;
+                }
+                c = __reduce_add_sync(0xFFFFFFFFu, c);
+                if (lane == 0) {
+                    if (below) write_result(a, c, er, erid);
+                    else if (c < krem) write_result(a, nb + c, er, erid);
+                }
+            }
+            if (stamp) {
+                ctl->ts[8] = gtimer();
+                ctl->ts[6] = ctl->ts[8];
+                if (a.dev_status) *a.dev_status = ld_volatile_i32(&ctl->err);
+            }
+            return;
+        }
+    }
+
+    // Phase 4, larger K.  (a) The bucket entries (ns <= 4096) are ranked by
+    // the grid as above and the first krem written at their final positions.
+    // (b) The below entries are partitioned on the 12-bit digit at the refine
+    // start L0 -- a histogram, a scan, a scatter into out_r1 -- and every
+    // bucket of at most TK_SMALL entries is ranked in one CTA's shared memory
+    // and written at its final positions.  Skewed inputs with a larger bucket
+    // fall back to tile sorts and merge-path rounds.
+    {
+        const uint64_t nb = take_all ? a.k : a.k - krem;
+        const int nsi = take_all ? 0 : static_cast<int>(bcnt);
+        const unsigned lane = threadIdx.x & 31u;
+        const int nwarps = static_cast<int>(gridDim.x) * (TK_TPB / 32);
+        const int gw = static_cast<int>(blockIdx.x) * (TK_TPB / 32) + static_cast<int>(threadIdx.x >> 5);
+        if (nsi > 0) {
+            for (int i = threadIdx.x; i < nsi; i += TK_TPB) {
+                sr[i] = __ldcg(a.small_r + i);
+                srid[i] = __ldcg(a.small_rid + i);
+            }
+            __syncthreads();
+            for (int e = gw; e < nsi; e += nwarps) {
+                const uint64_t er = sr[e];
+                const uint32_t erid = srid[e];
+                unsigned c = 0;
+                for (int j = static_cast<int>(lane); j < nsi; j += 32) {
+                    const uint64_t jr = sr[j];
+                    const uint32_t jrid = srid[j];
+                    c += (jr < er || (jr == er && (jrid < erid || (jrid == erid && j < e)))) ? 1u : 0u;
+                }
+                c = __reduce_add_sync(0xFFFFFFFFu, c);
+                if (lane == 0 && c < krem) write_result(a, nb + c, er, erid);
+            }
+            __syncthreads();
+        }
+        // (b) partition histogram of the below entries.
+        const int L0 = cand ? (__clzll(static_cast<long long>(__ldcg(&ctl->thresh))) < kb
+                                   ? __clzll(static_cast<long long>(__ldcg(&ctl->thresh))) : kb)
+                            : 0;
+        const int dp = min(TK_DIG, TB - L0);
+        unsigned* ph = a.ghist + (pass % 3) * TK_BINS;          // clean (zeroed by the last pass or prepare)
+        unsigned* pc = a.ghist + ((pass + 1) % 3) * TK_BINS;    // cursors, zeroed here
+        for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB) sh[b] = 0;
+        if (blockIdx.x == 0)
+            for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB) pc[b] = 0;
+        __syncthreads();
+        const uint64_t gstride = static_cast<uint64_t>(TK_TPB) * gridDim.x;
+        for (uint64_t wb = static_cast<uint64_t>(blockIdx.x) * TK_TPB + (threadIdx.x & ~31u); wb < nb; wb += gstride) {
+            const uint64_t i = wb + lane;
+            unsigned dig = 0xFFFFFFFFu;
+            if (i < nb) {
+                uint64_t w0, w1;
+                comp_words(__ldcg(a.out_r0 + i), __ldcg(a.out_rid0 + i), kb, w0, w1);
+                dig = comp_digit(w0, w1, L0, dp);
+            }
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
+            if (dig != 0xFFFFFFFFu && lane == static_cast<unsigned>(__ffs(peers) - 1))
+                atomicAdd(&sh[dig], static_cast<unsigned>(__popc(peers)));
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB)
+            if (sh[b]) atomicAdd(&ph[b], sh[b]);
+        if (!grid_sync(a.bar, &ctl->err)) return report(a);
+        // Scan of the partition histogram (every CTA), largest bucket.
+        constexpr int PER = TK_BINS / TK_TPB;
+        unsigned v[PER];
+        unsigned long long local = 0;
+        unsigned mx = 0;
+        const volatile unsigned* hv = ph;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            v[j] = hv[threadIdx.x * PER + j];
+            local += v[j];
+            mx = max(mx, v[j]);
+        }
+        const unsigned long long before = block_excl_scan(local, reinterpret_cast<unsigned long long*>(sc),
+                                                          reinterpret_cast<unsigned long long*>(sc) + 16);
+        unsigned* off = sh;                                      // exclusive offsets per bucket
+        {
+            unsigned long long run = before;
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                off[threadIdx.x * PER + j] = static_cast<unsigned>(run);
+                run += v[j];
+            }
+        }
+        const bool fits = __syncthreads_and(mx <= static_cast<unsigned>(TK_SMALL));
+        if (fits) {
+            // Scatter the below entries into bucket order (out_r1).
+            for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * TK_TPB + threadIdx.x; i < nb; i += gstride) {
+                const uint64_t er = __ldcg(a.out_r0 + i);
+                const uint32_t erid = __ldcg(a.out_rid0 + i);
+                uint64_t w0, w1;
+                comp_words(er, erid, kb, w0, w1);
+                const unsigned d = comp_digit(w0, w1, L0, dp);
+                const unsigned pos = off[d] + atomicAdd(&pc[d], 1u);
+                a.out_r1[pos] = er;
+                a.out_rid1[pos] = erid;
+            }
+            if (!grid_sync(a.bar, &ctl->err)) return report(a);
+            // Rank every bucket in shared memory: one CTA per bucket.
+            uint64_t* br = reinterpret_cast<uint64_t*>(smem + TK_BINS * 4);
+            uint32_t* brid = reinterpret_cast<uint32_t*>(smem + TK_BINS * 4 + TK_SMALL * 8);
+            for (int b = blockIdx.x; b < TK_BINS; b += gridDim.x) {
+                const unsigned m = hv[b];
+                if (m == 0) continue;
+                const unsigned o = off[b];
+                for (unsigned i = threadIdx.x; i < m; i += TK_TPB) {
+                    br[i] = __ldcg(a.out_r1 + o + i);
+                    brid[i] = __ldcg(a.out_rid1 + o + i);
+                }
+                __syncthreads();
+                for (unsigned e = threadIdx.x >> 5; e < m; e += TK_TPB / 32) {
+                    const uint64_t er = br[e];
+                    const uint32_t erid = brid[e];
+                    unsigned c = 0;
+                    for (unsigned j = lane; j < m; j += 32) {
+                        const uint64_t jr = br[j];
+                        const uint32_t jrid = brid[j];
+                        c += (jr < er || (jr == er && (jrid < erid || (jrid == erid && j < e)))) ? 1u : 0u;
+                    }
+                    c = __reduce_add_sync(0xFFFFFFFFu, c);
+                    if (lane == 0) write_result(a, o + c, er, erid);
+                }
+                __syncthreads();
+            }
+            if (stamp) {
+                ctl->ts[7] = gtimer();
+                ctl->ts[8] = ctl->ts[7];
+                ctl->ts[6] = ctl->ts[7];
+                if (a.dev_status) *a.dev_status = ld_volatile_i32(&ctl->err);
+            }
+            return;
+        }
+        // Skewed: the bucket entries are already written; sort the below
+        // entries with the merge path (k below plus krem written above).
+    }
+
+    // Phase 4, fallback: CTA 0 finishes the bucket, then a grid merge sort.
     if (blockIdx.x == 0) {
         if (!take_all) {
             const int cnt = static_cast<int>(bcnt);

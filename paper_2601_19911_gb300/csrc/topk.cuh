@@ -16,7 +16,8 @@ constexpr int TK_SAMPLE = 8192;           // sample size of the threshold estima
 constexpr int TK_SPT = TK_SAMPLE / TK_TPB;
 constexpr int TK_UNROLL = 4;              // 16-byte loads in flight per thread (register filter)
 constexpr uint64_t TK_DIRECT_N = 1ull << 21;   // at or below: no sample, refine the input
-constexpr int TK_SORT_SMEM = TK_SMALL * 12;   // shared bytes of the sort tile (or histogram)
+constexpr int TK_RANK_MAX = 8192;         // survivors ranked in shared memory by the whole grid
+constexpr int TK_SORT_SMEM = TK_RANK_MAX * 12;  // select kernel shared bytes (ranking / sort tile / histogram)
 constexpr int TK_MAX_STAGES = 16;         // full + empty mbarrier pairs reserved after the ring
 constexpr int TK_SMEM_MAX = 227 * 1024;   // opt-in shared memory per CTA
 // The streaming filter runs as its own kernel: 256-thread CTAs, several per
