@@ -141,6 +141,60 @@ typedef struct {
 olap_status olap_topk_info_last(olap_ctx* ctx, olap_topk_info* out);
 
 /* ------------------------------------------------------------------------
+ * Key-based hash join, build and probe (Sec. III-B: "parallel probing using a
+ * key-only hash table", pointers returned for late materialization, Sec. II-C).
+ *
+ * The table is an open-addressing table of 16-byte slots {int64 key, uint32
+ * row-id}, two slots per 32-byte bucket, with linear probing over buckets
+ * (a bucket with a free slot ends every chain).  Capacity is the power of two
+ * of buckets that keeps n / (2 * buckets) at or below the load factor.  Build
+ * rows whose key equals the table's empty marker (all bits set, i.e. -1) are
+ * kept in a side list, so every int64 key value joins correctly.  The table
+ * stays resident on the device until olap_join_free; it may be probed any
+ * number of times, from any context on the same device.
+ *
+ * Result: every (probe row-id, build row-id) pair whose keys are equal, as a
+ * multiset (duplicate keys on either side multiply), in no particular order.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    uint32_t probe_rowid;
+    uint32_t build_rowid;
+} olap_pair;
+
+/* Build a table from n int64 keys (memory `where`) with row-ids (NULL =>
+ * index; n < 2^32 then).  load_factor in (0, 0.9]; 0 takes the context's
+ * option (default 0.5).  *out receives the table, owned by the caller until
+ * olap_join_free.  Blocking. */
+olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* rowids, olap_mem where,
+                            uint64_t n, double load_factor, olap_join_table** out);
+
+/* Probe: for n keys (memory `where`, row-ids or NULL => index) write the
+ * matching pairs to out (memory `out_where`, room for `capacity` pairs).
+ * *out_count receives the number of pairs.  If it exceeds capacity the call
+ * returns OLAP_E_OVERFLOW, *out_count holds the exact number needed and the
+ * contents of out are unspecified; retry with capacity >= *out_count.
+ * Blocking. */
+olap_status olap_join_probe(olap_ctx* ctx, const olap_join_table* table, const int64_t* keys,
+                            const uint32_t* rowids, olap_mem where, uint64_t n, olap_pair* out,
+                            olap_mem out_where, uint64_t capacity, uint64_t* out_count);
+
+/* Asynchronous probe on device pointers, enqueued on `stream` (NULL => the
+ * context's stream).  d_count (device uint64) receives the pair count, which
+ * may exceed capacity (then only `capacity` pairs were written).  Calls on
+ * one context must be serialised on one stream. */
+olap_status olap_join_probe_async(olap_ctx* ctx, const olap_join_table* table, const int64_t* d_keys,
+                                  const uint32_t* d_rowids, uint64_t n, olap_pair* d_out, uint64_t capacity,
+                                  uint64_t* d_count, void* stream);
+
+/* Table facts: build rows, buckets (2 slots each), rows in the side list. */
+olap_status olap_join_table_info(const olap_join_table* table, uint64_t* n_build, uint64_t* n_buckets,
+                                 uint64_t* n_side);
+
+/* Free a table (NULL is ignored).  Waits for the table's device to finish
+ * work that may still read it. */
+void olap_join_free(olap_join_table* table);
+
+/* ------------------------------------------------------------------------
  * Top-K that allocates nothing (no counterpart in the paper: a deployment
  * entry point for callers that cannot let a library allocate GPU memory --
  * engines whose device memory is wholly reserved by their own pool, plug-in

@@ -8,6 +8,10 @@
 #include "ctx.h"
 #include "topk.cuh"
 
+// Join tables outlive nothing: a context being destroyed forgets the tables it
+// built (they stay valid and are freed with olap_join_free).
+void detach_tables(olap_ctx* ctx);
+
 namespace olap {
 
 olap_status fail(olap_ctx* ctx, olap_status st, const std::string& msg) {
@@ -261,6 +265,8 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     }
     ctx->topk_geom = g;
     if ((e = cudaMallocHost(reinterpret_cast<void**>(&ctx->host_status), 64)) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&ctx->aux, 4096)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemset(ctx->aux, 0, 4096)) != cudaSuccess) return bail(e);
     *out = ctx;
     return OLAP_OK;
 }
@@ -277,6 +283,8 @@ void olap_ctx_destroy(olap_ctx* ctx) {
         if (ctx->pinned_ev[i]) cudaEventDestroy(ctx->pinned_ev[i]);
     }
     if (ctx->host_status) cudaFreeHost(ctx->host_status);
+    if (ctx->aux) cudaFree(ctx->aux);
+    detach_tables(ctx);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

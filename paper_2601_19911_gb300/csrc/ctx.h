@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <set>
 #include <string>
 
 #include "olap.h"
@@ -35,14 +36,17 @@ struct olap_ctx {
     size_t pinned_bytes = 0;
     cudaEvent_t pinned_ev[2] = {nullptr, nullptr};
 
-    // Small pinned word for device status read-back.
+    // Small pinned words for device status read-back, and a small device
+    // area for counters of blocking calls (4 KiB).
     int32_t* host_status = nullptr;
+    void* aux = nullptr;
 
     // Control block of the last Top-K launched (diagnostics).
     void* last_topk_ctl = nullptr;
 
-    // Device memory held by join tables created through this context.
+    // Device memory held by live join tables built through this context.
     uint64_t table_bytes = 0;
+    std::set<olap_join_table*> tables;
 
     std::string last_error;
 };

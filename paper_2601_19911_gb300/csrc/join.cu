@@ -1,0 +1,494 @@
+// Key-based hash join over key-only columns (Sec. III-B: "parallel probing
+// using a key-only hash table"; pointers returned for late materialization,
+// Sec. II-C).
+//
+// Table: open addressing, 16-byte slots {int64 key, row-id}, two slots per
+// 32-byte bucket (one DRAM sector), linear probing over buckets.  A key goes
+// to the first free slot at or after its home bucket, slot 0 before slot 1,
+// so a bucket with a free slot ends every chain.  The empty marker is the key
+// with all bits set; build rows carrying that key value live in a side list.
+// Hash: the 64-bit finalizer of MurmurHash3 (fmix64, A. Appleby).
+//
+// Probe: every thread takes JP_U probe keys per round (coalesced loads),
+// issues their first bucket loads together, then walks the chains in
+// warp-uniform steps.  Matches are appended per warp (one ballot per slot)
+// into a per-CTA shared-memory stage that is flushed to the output in blocks
+// of at least JP_FLUSH pairs with one atomic on the global count.
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "ctx.h"
+
+namespace olap {
+
+namespace {
+
+constexpr uint64_t JN_EMPTY = ~0ull;
+constexpr int JB_TPB = 256;
+constexpr int JP_TPB = 256;
+constexpr int JP_U = 4;
+constexpr int JP_STAGE = 6144;    // pairs staged per CTA (48 KB)
+constexpr int JP_FLUSH = 2048;    // flush once this many are staged; a round adds at most
+                                  // JP_TPB * JP_U * 2 per chain step, and the stage spills
+                                  // to direct global appends if a round overfills it
+constexpr int JP_SMEM = JP_STAGE * 8;
+
+struct JoinCtl {
+    unsigned long long side_count;   // build rows with the empty-marker key
+    unsigned long long side_fill;
+    int err;
+    int pad;
+};
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    return h;
+}
+
+__device__ __forceinline__ uint64_t ld_stream_u64(const void* p) {
+    uint64_t v;
+    asm volatile("ld.global.cs.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+__global__ void __launch_bounds__(JB_TPB) join_build_kernel(const int64_t* keys, const uint32_t* rowids,
+                                                            uint64_t n, ulonglong2* slots, uint64_t mask,
+                                                            JoinCtl* ctl) {
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * JB_TPB;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * JB_TPB + threadIdx.x; i < n; i += stride) {
+        const uint64_t key = static_cast<uint64_t>(keys[i]);
+        if (key == JN_EMPTY) {
+            atomicAdd(&ctl->side_count, 1ull);
+            continue;
+        }
+        const uint32_t rid = rowids ? rowids[i] : static_cast<uint32_t>(i);
+        uint64_t b = fmix64(key) & mask;
+        bool done = false;
+        for (uint64_t step = 0; step <= mask && !done; ++step) {
+            for (int s = 0; s < 2 && !done; ++s) {
+                unsigned long long* kp = reinterpret_cast<unsigned long long*>(&slots[b * 2 + s].x);
+                if (*reinterpret_cast<volatile unsigned long long*>(kp) != JN_EMPTY) continue;
+                if (atomicCAS(kp, JN_EMPTY, static_cast<unsigned long long>(key)) == JN_EMPTY) {
+                    slots[b * 2 + s].y = rid;
+                    done = true;
+                }
+            }
+            b = (b + 1) & mask;
+        }
+        if (!done) atomicCAS(&ctl->err, 0, static_cast<int>(OLAP_E_DEVICE));
+    }
+}
+
+__global__ void __launch_bounds__(JB_TPB) join_side_kernel(const int64_t* keys, const uint32_t* rowids,
+                                                           uint64_t n, uint32_t* side, JoinCtl* ctl) {
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * JB_TPB;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * JB_TPB + threadIdx.x; i < n; i += stride) {
+        if (static_cast<uint64_t>(keys[i]) == JN_EMPTY) {
+            const unsigned long long pos = atomicAdd(&ctl->side_fill, 1ull);
+            side[pos] = rowids ? rowids[i] : static_cast<uint32_t>(i);
+        }
+    }
+}
+
+struct ProbeArgs {
+    const int64_t* keys;
+    const uint32_t* rowids;
+    uint64_t n;
+    const ulonglong2* slots;
+    uint64_t mask;
+    const uint32_t* side;
+    uint64_t n_side;
+    uint2* out;
+    uint64_t cap;
+    unsigned long long* count;
+};
+
+// Place one pair at stage position pos, or append it to the output directly
+// once the stage is full.
+__device__ __forceinline__ void put_pair(const ProbeArgs& a, uint2* stage, unsigned pos, uint2 p) {
+    if (pos < JP_STAGE) {
+        stage[pos] = p;
+    } else {
+        const unsigned long long g = atomicAdd(a.count, 1ull);
+        if (g < a.cap) a.out[g] = p;
+    }
+}
+
+// Warp-aggregated append of up to two pairs per lane (all lanes call).
+__device__ __forceinline__ void warp_emit2(const ProbeArgs& a, uint2* stage, unsigned* scount, bool m0, uint2 p0,
+                                           bool m1, uint2 p1) {
+    const unsigned b0 = __ballot_sync(0xFFFFFFFFu, m0);
+    const unsigned b1 = __ballot_sync(0xFFFFFFFFu, m1);
+    const unsigned tot = __popc(b0) + __popc(b1);
+    if (tot == 0) return;
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(scount, tot);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (m0) put_pair(a, stage, base + __popc(b0 & lt), p0);
+    if (m1) put_pair(a, stage, base + __popc(b0) + __popc(b1 & lt), p1);
+}
+
+// Copy the staged pairs to the output (whole CTA; call between barriers).
+__device__ __forceinline__ void flush_stage(const ProbeArgs& a, uint2* stage, unsigned* scount,
+                                            unsigned long long* sbase) {
+    const unsigned c = min(*reinterpret_cast<volatile unsigned*>(scount), static_cast<unsigned>(JP_STAGE));
+    if (threadIdx.x == 0) *sbase = c ? atomicAdd(a.count, static_cast<unsigned long long>(c)) : 0ull;
+    __syncthreads();
+    const unsigned long long base = *sbase;
+    for (unsigned i = threadIdx.x; i < c; i += JP_TPB) {
+        const unsigned long long g = base + i;
+        if (g < a.cap) a.out[g] = stage[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *scount = 0;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs a) {
+    extern __shared__ __align__(16) uint2 stage[];
+    __shared__ unsigned scount;
+    __shared__ unsigned long long sbase;
+    if (threadIdx.x == 0) scount = 0;
+    __syncthreads();
+    const uint64_t per = static_cast<uint64_t>(JP_TPB) * JP_U;
+    for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * per; base < a.n;
+         base += static_cast<uint64_t>(gridDim.x) * per) {
+        uint64_t k[JP_U], bk[JP_U];
+        uint32_t prid[JP_U];
+        bool act[JP_U];
+        ulonglong2 x0[JP_U], x1[JP_U];
+#pragma unroll
+        for (int j = 0; j < JP_U; ++j) {
+            const uint64_t idx = base + static_cast<uint64_t>(j) * JP_TPB + threadIdx.x;
+            const bool v = idx < a.n;
+            k[j] = v ? ld_stream_u64(a.keys + idx) : JN_EMPTY;
+            prid[j] = v ? (a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx)) : 0u;
+            act[j] = v && k[j] != JN_EMPTY;
+            // Probe keys equal to the empty marker pair with the side list.
+            if (v && k[j] == JN_EMPTY)
+                for (uint64_t o = 0; o < a.n_side; ++o)
+                    put_pair(a, stage, atomicAdd(&scount, 1u), make_uint2(prid[j], a.side[o]));
+        }
+#pragma unroll
+        for (int j = 0; j < JP_U; ++j) {
+            bk[j] = act[j] ? (fmix64(k[j]) & a.mask) : 0;
+            if (act[j]) {
+                x0[j] = __ldg(a.slots + bk[j] * 2);
+                x1[j] = __ldg(a.slots + bk[j] * 2 + 1);
+            } else {
+                x0[j] = make_ulonglong2(JN_EMPTY, 0);
+                x1[j] = make_ulonglong2(JN_EMPTY, 0);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < JP_U; ++j) {
+            bool on = act[j];
+            while (__any_sync(0xFFFFFFFFu, on)) {
+                const bool m0 = on && x0[j].x == k[j];
+                const bool m1 = on && x1[j].x == k[j];
+                warp_emit2(a, stage, &scount, m0, make_uint2(prid[j], static_cast<uint32_t>(x0[j].y)), m1,
+                           make_uint2(prid[j], static_cast<uint32_t>(x1[j].y)));
+                on = on && x0[j].x != JN_EMPTY && x1[j].x != JN_EMPTY;
+                if (on) {
+                    bk[j] = (bk[j] + 1) & a.mask;
+                    x0[j] = __ldg(a.slots + bk[j] * 2);
+                    x1[j] = __ldg(a.slots + bk[j] * 2 + 1);
+                }
+            }
+        }
+        __syncthreads();
+        if (*reinterpret_cast<volatile unsigned*>(&scount) >= static_cast<unsigned>(JP_FLUSH))
+            flush_stage(a, stage, &scount, &sbase);
+    }
+    __syncthreads();
+    flush_stage(a, stage, &scount, &sbase);
+}
+
+uint64_t next_pow2(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+int probe_grid(int device) {
+    static int cached[64] = {};
+    if (device < 0 || device >= 64) return 0;
+    if (cached[device]) return cached[device];
+    int sms = 0, per = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(join_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, JP_SMEM) !=
+        cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, join_probe_kernel, JP_TPB, JP_SMEM) != cudaSuccess)
+        return 0;
+    cached[device] = sms * std::max(1, per);
+    return cached[device];
+}
+
+}  // namespace
+
+}  // namespace olap
+
+struct olap_join_table {
+    olap_ctx* owner = nullptr;        // context whose budget counts this table (or NULL)
+    int device = 0;
+    ulonglong2* slots = nullptr;      // n_buckets * 2 slots
+    uint64_t n_buckets = 0;
+    uint32_t* side = nullptr;         // row-ids of build rows with the empty-marker key
+    uint64_t n_side = 0;
+    uint64_t n_build = 0;
+    double load = 0.0;
+    size_t bytes = 0;
+};
+
+using namespace olap;
+
+namespace {
+
+olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t* d_keys, const uint32_t* d_rowids,
+                          uint64_t n, olap_pair* d_out, uint64_t capacity, uint64_t* d_count, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "probe count reset");
+    if (n == 0) return OLAP_OK;
+    const int grid = probe_grid(ctx->device);
+    if (grid <= 0) return fail(ctx, OLAP_E_CUDA, "probe kernel occupancy query failed");
+    ProbeArgs a;
+    a.keys = d_keys;
+    a.rowids = d_rowids;
+    a.n = n;
+    a.slots = t->slots;
+    a.mask = t->n_buckets - 1;
+    a.side = t->side;
+    a.n_side = t->n_side;
+    a.out = reinterpret_cast<uint2*>(d_out);
+    a.cap = capacity;
+    a.count = reinterpret_cast<unsigned long long*>(d_count);
+    join_probe_kernel<<<grid, JP_TPB, JP_SMEM, s>>>(a);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "probe launch");
+}
+
+olap_status check_join_table(olap_ctx* ctx, const olap_join_table* t) {
+    if (!t || !t->slots) return fail(ctx, OLAP_E_INVALID, "join table is NULL or freed");
+    if (t->device != ctx->device) return fail(ctx, OLAP_E_INVALID, "join table lives on another device");
+    return OLAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* rowids, olap_mem where, uint64_t n,
+                            double load_factor, olap_join_table** out) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (!out) return fail(ctx, OLAP_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (where < OLAP_MEM_HOST || where > OLAP_MEM_DEVICE) return fail(ctx, OLAP_E_INVALID, "bad memory kind");
+    if (n && !keys) return fail(ctx, OLAP_E_INVALID, "keys is NULL");
+    if (!rowids && n > (1ull << 32)) return fail(ctx, OLAP_E_INVALID, "implicit row-ids need n <= 2^32");
+    if (reinterpret_cast<uintptr_t>(keys) % 8) return fail(ctx, OLAP_E_INVALID, "keys misaligned");
+    double load = load_factor > 0.0 ? load_factor : (ctx->opts.load_factor > 0.0 ? ctx->opts.load_factor : 0.5);
+    if (!(load > 0.0 && load <= 0.9)) return fail(ctx, OLAP_E_INVALID, "load factor must be in (0, 0.9]");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
+
+    const uint64_t want_slots = static_cast<uint64_t>(static_cast<double>(n) / load) + 2;
+    const uint64_t buckets = next_pow2((want_slots + 1) / 2);
+    const size_t slot_bytes = buckets * 32;
+    const size_t bytes = slot_bytes + 256;
+    if (!within_budget(ctx, bytes)) return fail(ctx, OLAP_E_NOMEM, "join table: device memory budget exceeded");
+
+    // Key-only input: build keys (and row-ids) to the device.
+    const int64_t* dk = keys;
+    const uint32_t* dr = rowids;
+    if (where != OLAP_MEM_DEVICE && n) {
+        const size_t kb = (n * 8 + 255) & ~static_cast<size_t>(255);
+        olap_status st = ensure_dev_in(ctx, kb + (rowids ? n * 4 : 0));
+        if (st != OLAP_OK) return st;
+        st = copy_h2d(ctx, ctx->dev_in, keys, n * 8, where);
+        if (st != OLAP_OK) return st;
+        dk = static_cast<const int64_t*>(ctx->dev_in);
+        if (rowids) {
+            dr = reinterpret_cast<const uint32_t*>(static_cast<unsigned char*>(ctx->dev_in) + kb);
+            st = copy_h2d(ctx, const_cast<uint32_t*>(dr), rowids, n * 4, where);
+            if (st != OLAP_OK) return st;
+        }
+    }
+
+    olap_join_table* t = new olap_join_table();
+    t->device = ctx->device;
+    t->n_buckets = buckets;
+    t->n_build = n;
+    t->load = load;
+    void* mem = nullptr;
+    e = cudaMalloc(&mem, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete t;
+        return cuda_fail(ctx, e, "join table allocation");
+    }
+    t->slots = static_cast<ulonglong2*>(mem);
+    t->bytes = bytes;
+    JoinCtl* jc = reinterpret_cast<JoinCtl*>(static_cast<unsigned char*>(mem) + slot_bytes);
+    auto bail = [&](olap_status st) {
+        cudaFree(mem);
+        delete t;
+        return st;
+    };
+    e = cudaMemsetAsync(mem, 0xFF, slot_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(jc, 0, sizeof(JoinCtl), ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "join table init"));
+    if (n) {
+        const int grid = ctx->sm_count * 8;
+        join_build_kernel<<<grid, JB_TPB, 0, ctx->stream>>>(dk, dr, n, t->slots, buckets - 1, jc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build launch"));
+    }
+    JoinCtl hc;
+    e = cudaMemcpyAsync(&hc, jc, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "join build"));
+    if (hc.err) return bail(fail(ctx, static_cast<olap_status>(hc.err), "join build: table full"));
+    if (hc.side_count) {
+        e = cudaMalloc(reinterpret_cast<void**>(&t->side), hc.side_count * 4);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(cuda_fail(ctx, e, "join side list allocation"));
+        }
+        join_side_kernel<<<ctx->sm_count * 4, JB_TPB, 0, ctx->stream>>>(dk, dr, n, t->side, jc);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(t->side);
+            return bail(cuda_fail(ctx, e, "join side list"));
+        }
+        t->n_side = hc.side_count;
+        t->bytes += hc.side_count * 4;
+    }
+    ctx->table_bytes += t->bytes;
+    ctx->tables.insert(t);
+    t->owner = ctx;
+    *out = t;
+    return OLAP_OK;
+}
+
+olap_status olap_join_probe_async(olap_ctx* ctx, const olap_join_table* table, const int64_t* d_keys,
+                                  const uint32_t* d_rowids, uint64_t n, olap_pair* d_out, uint64_t capacity,
+                                  uint64_t* d_count, void* stream) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    olap_status st = check_join_table(ctx, table);
+    if (st != OLAP_OK) return st;
+    if (!d_count) return fail(ctx, OLAP_E_INVALID, "d_count is NULL");
+    if (n && !d_keys) return fail(ctx, OLAP_E_INVALID, "keys is NULL");
+    if (capacity && !d_out) return fail(ctx, OLAP_E_INVALID, "out is NULL");
+    if (!d_rowids && n > (1ull << 32)) return fail(ctx, OLAP_E_INVALID, "implicit row-ids need n <= 2^32");
+    cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->stream;
+    return probe_enqueue(ctx, table, d_keys, d_rowids, n, d_out, capacity, d_count, s);
+}
+
+olap_status olap_join_probe(olap_ctx* ctx, const olap_join_table* table, const int64_t* keys,
+                            const uint32_t* rowids, olap_mem where, uint64_t n, olap_pair* out, olap_mem out_where,
+                            uint64_t capacity, uint64_t* out_count) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (!out_count) return fail(ctx, OLAP_E_INVALID, "out_count is NULL");
+    *out_count = 0;
+    olap_status st = check_join_table(ctx, table);
+    if (st != OLAP_OK) return st;
+    if (where < OLAP_MEM_HOST || where > OLAP_MEM_DEVICE || out_where < OLAP_MEM_HOST ||
+        out_where > OLAP_MEM_DEVICE)
+        return fail(ctx, OLAP_E_INVALID, "bad memory kind");
+    if (n && !keys) return fail(ctx, OLAP_E_INVALID, "keys is NULL");
+    if (capacity && !out) return fail(ctx, OLAP_E_INVALID, "out is NULL");
+    if (!rowids && n > (1ull << 32)) return fail(ctx, OLAP_E_INVALID, "implicit row-ids need n <= 2^32");
+    if (reinterpret_cast<uintptr_t>(keys) % 8) return fail(ctx, OLAP_E_INVALID, "keys misaligned");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
+
+    const int64_t* dk = keys;
+    const uint32_t* dr = rowids;
+    if (where != OLAP_MEM_DEVICE && n) {
+        const size_t kb = (n * 8 + 255) & ~static_cast<size_t>(255);
+        st = ensure_dev_in(ctx, kb + (rowids ? n * 4 : 0));
+        if (st != OLAP_OK) return st;
+        st = copy_h2d(ctx, ctx->dev_in, keys, n * 8, where);
+        if (st != OLAP_OK) return st;
+        dk = static_cast<const int64_t*>(ctx->dev_in);
+        if (rowids) {
+            dr = reinterpret_cast<const uint32_t*>(static_cast<unsigned char*>(ctx->dev_in) + kb);
+            st = copy_h2d(ctx, const_cast<uint32_t*>(dr), rowids, n * 4, where);
+            if (st != OLAP_OK) return st;
+        }
+    }
+    olap_pair* dout = out;
+    // Device count word: a small slot at the end of the output staging area
+    // (host outputs) or of the context scratch (device outputs).
+    uint64_t* dcount = nullptr;
+    if (out_where != OLAP_MEM_DEVICE) {
+        const size_t ob = (capacity * 8 + 255) & ~static_cast<size_t>(255);
+        st = ensure_dev_out(ctx, ob + 256);
+        if (st != OLAP_OK) return st;
+        dout = static_cast<olap_pair*>(ctx->dev_out);
+        dcount = reinterpret_cast<uint64_t*>(static_cast<unsigned char*>(ctx->dev_out) + ob);
+    } else {
+        dcount = static_cast<uint64_t*>(ctx->aux);
+    }
+    st = probe_enqueue(ctx, table, dk, dr, n, dout, capacity, dcount, ctx->stream);
+    if (st != OLAP_OK) return st;
+    uint64_t cnt = 0;
+    e = cudaMemcpyAsync(ctx->host_status + 8, dcount, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "join probe");
+    std::memcpy(&cnt, ctx->host_status + 8, sizeof(cnt));
+    *out_count = cnt;
+    if (cnt > capacity) return fail(ctx, OLAP_E_OVERFLOW, "join probe: output capacity too small");
+    if (out_where != OLAP_MEM_DEVICE && cnt) {
+        st = copy_d2h(ctx, out, dout, cnt * 8, out_where);
+        if (st != OLAP_OK) return st;
+        e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "join result copy");
+    }
+    return OLAP_OK;
+}
+
+olap_status olap_join_table_info(const olap_join_table* t, uint64_t* n_build, uint64_t* n_buckets, uint64_t* n_side) {
+    if (!t || !t->slots) return OLAP_E_INVALID;
+    if (n_build) *n_build = t->n_build;
+    if (n_buckets) *n_buckets = t->n_buckets;
+    if (n_side) *n_side = t->n_side;
+    return OLAP_OK;
+}
+
+void olap_join_free(olap_join_table* t) {
+    if (!t) return;
+    if (t->owner) {
+        t->owner->table_bytes -= t->bytes;
+        t->owner->tables.erase(t);
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(t->device);
+    cudaDeviceSynchronize();
+    if (t->slots) cudaFree(t->slots);
+    if (t->side) cudaFree(t->side);
+    t->slots = nullptr;
+    t->side = nullptr;
+    cudaSetDevice(cur);
+    delete t;
+}
+
+}  // extern "C"
+
+void detach_tables(olap_ctx* ctx) {
+    for (olap_join_table* t : ctx->tables) t->owner = nullptr;
+    ctx->tables.clear();
+}

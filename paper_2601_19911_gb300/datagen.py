@@ -162,12 +162,14 @@ def identity_rowids(n: int) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 class JoinBuild:
-    """Build side: ``keys`` (int64) with row-ids ``0..n-1`` and the distinct keys."""
+    """Build side: ``keys`` (int64) with row-ids ``0..n-1``, the distinct keys
+    and how many rows carry each of them (``mult``, aligned with ``distinct``)."""
 
-    def __init__(self, keys: np.ndarray, distinct: np.ndarray):
+    def __init__(self, keys: np.ndarray, distinct: np.ndarray, mult: np.ndarray):
         self.keys = keys
         self.rowids = identity_rowids(keys.shape[0])
         self.distinct = distinct
+        self.mult = mult
 
 
 def join_build(n: int, mult: str = "unique", seed: int = 2) -> JoinBuild:
@@ -177,7 +179,7 @@ def join_build(n: int, mult: str = "unique", seed: int = 2) -> JoinBuild:
     n = int(n)
     if mult == "unique":
         keys = _distinct_u64(stream_seed(seed, 1), n).view(np.int64)
-        return JoinBuild(keys, keys)
+        return JoinBuild(keys, keys, np.ones(n, dtype=np.int64))
     if mult != "mult14":
         raise ValueError(mult)
     m = (splitmix64(stream_seed(seed, 7), n) % _U64(4)).astype(np.int64) + 1
@@ -188,7 +190,7 @@ def join_build(n: int, mult: str = "unique", seed: int = 2) -> JoinBuild:
     distinct = _distinct_u64(stream_seed(seed, 1), d).view(np.int64)
     rows = np.repeat(distinct, m)
     perm = np.argsort(splitmix64(stream_seed(seed, 6), n), kind="stable")
-    return JoinBuild(rows[perm], distinct)
+    return JoinBuild(rows[perm], distinct, m)
 
 
 def _zipf_ranks(u: np.ndarray, d: int, s: float) -> np.ndarray:
@@ -201,10 +203,15 @@ def _zipf_ranks(u: np.ndarray, d: int, s: float) -> np.ndarray:
 
 
 class JoinProbe:
-    def __init__(self, keys: np.ndarray, hit: np.ndarray):
+    def __init__(self, keys: np.ndarray, hit: np.ndarray, pick: np.ndarray):
         self.keys = keys
         self.hit = hit                   # bool per probe row: drawn as a hit
+        self.pick = pick                 # index into the build's distinct keys (hits only)
         self.rowids = identity_rowids(keys.shape[0])
+
+    def expected_pairs(self, build: "JoinBuild") -> int:
+        """Pairs the join must return: the build multiplicity of every hit."""
+        return int(build.mult[self.pick[self.hit]].sum())
 
 
 def join_probe(n: int, build: JoinBuild, hit_rate: float = 0.9, dist: str = "uniform",
@@ -238,7 +245,7 @@ def join_probe(n: int, build: JoinBuild, hit_rate: float = 0.9, dist: str = "uni
         miss[bad] = splitmix64(stream_seed(seed, 5), bad.shape[0], start=nxt).view(np.int64)
         nxt += bad.shape[0]
     keys[~hit] = miss
-    return JoinProbe(keys, hit)
+    return JoinProbe(keys, hit, idx)
 
 
 # --------------------------------------------------------------------------

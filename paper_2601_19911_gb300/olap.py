@@ -28,6 +28,7 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
+    "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
 ]
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
 NOALLOC_MAX_N = 1 << 24
@@ -100,6 +101,16 @@ def load(path: str | None = None):
         lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         lib.olap_topk_info_last.restype = i32
         lib.olap_topk_info_last.argtypes = [vp, ctypes.POINTER(olap_topk_info)]
+        lib.olap_join_build.restype = i32
+        lib.olap_join_build.argtypes = [vp, vp, vp, i32, u64, ctypes.c_double, ctypes.POINTER(vp)]
+        lib.olap_join_probe.restype = i32
+        lib.olap_join_probe.argtypes = [vp, vp, vp, vp, i32, u64, vp, i32, u64, ctypes.POINTER(u64)]
+        lib.olap_join_probe_async.restype = i32
+        lib.olap_join_probe_async.argtypes = [vp, vp, vp, vp, u64, vp, u64, vp, vp]
+        lib.olap_join_table_info.restype = i32
+        lib.olap_join_table_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        lib.olap_join_free.restype = None
+        lib.olap_join_free.argtypes = [vp]
         lib.olap_topk_noalloc.restype = i32
         lib.olap_topk_noalloc.argtypes = [vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         _bind_more(lib)
@@ -240,6 +251,48 @@ class Context:
         assert got.value == cnt
         return out_keys[:cnt], out_rowids[:cnt]
 
+    # -- Join ----------------------------------------------------------------
+    def join_build(self, keys, rowids=None, load_factor: float = 0.0) -> "JoinTable":
+        """olap_join_build over int64 keys (numpy, pinned or CUDA tensor)."""
+        where = mem_kind(keys)
+        if rowids is not None:
+            assert mem_kind(rowids) == where and numel(rowids) == numel(keys)
+        h = ctypes.c_void_p()
+        self.check(self.lib.olap_join_build(self.h, ptr(keys), ptr(rowids), where, numel(keys),
+                                            float(load_factor), ctypes.byref(h)))
+        return JoinTable(self.lib, h)
+
+    def join_probe(self, table: "JoinTable", keys, rowids=None, out=None, capacity: int | None = None):
+        """olap_join_probe.  Returns the pairs as an (M, 2) uint32 array
+        [probe_rowid, build_rowid] (numpy by default, or the given buffer cut to
+        M rows).  With no buffer given, retries once with the exact size when
+        the first guess overflows."""
+        where = mem_kind(keys)
+        n = numel(keys)
+        if rowids is not None:
+            assert mem_kind(rowids) == where and numel(rowids) == n
+        own = out is None
+        if own:
+            capacity = capacity if capacity is not None else max(16, 2 * n)
+            out = np.empty((capacity, 2), dtype=np.uint32)
+        cap = (out.shape[0] if isinstance(out, np.ndarray) else out.numel() // 2) if capacity is None else capacity
+        got = ctypes.c_uint64()
+        st = self.lib.olap_join_probe(self.h, table.h, ptr(keys), ptr(rowids), where, n, ptr(out), mem_kind(out),
+                                      cap, ctypes.byref(got))
+        if st == E_OVERFLOW and own:
+            out = np.empty((max(1, got.value), 2), dtype=np.uint32)
+            st = self.lib.olap_join_probe(self.h, table.h, ptr(keys), ptr(rowids), where, n, ptr(out),
+                                          MEM_HOST, got.value, ctypes.byref(got))
+        if st == E_OVERFLOW:
+            raise OlapError(st, f"{self.last_error()} (need {got.value} pairs)")
+        self.check(st)
+        return out[: got.value]
+
+    def join_probe_async(self, table: "JoinTable", d_keys, d_out, capacity: int, d_count, d_rowids=None,
+                         stream: int | None = None):
+        self.check(self.lib.olap_join_probe_async(self.h, table.h, ptr(d_keys), ptr(d_rowids), numel(d_keys),
+                                                  ptr(d_out), int(capacity), ptr(d_count), stream))
+
     def topk_info(self) -> dict:
         """olap_topk_info_last as a dict (phase times in microseconds)."""
         info = olap_topk_info()
@@ -255,6 +308,32 @@ class Context:
                                       numel(d_keys), int(k), int(order), ptr(d_out_keys),
                                       ptr(d_out_rowids), ptr(dev_status), stream)
         self.check(st)
+
+
+class JoinTable:
+    """A resident key-only hash table (olap_join_table)."""
+
+    def __init__(self, lib, h):
+        self.lib = lib
+        self.h = h
+
+    def info(self) -> dict:
+        nb, nk, ns = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        st = self.lib.olap_join_table_info(self.h, ctypes.byref(nb), ctypes.byref(nk), ctypes.byref(ns))
+        if st != OK:
+            raise OlapError(st, "olap_join_table_info failed")
+        return {"n_build": nb.value, "n_buckets": nk.value, "n_side": ns.value}
+
+    def free(self):
+        if getattr(self, "h", None):
+            self.lib.olap_join_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def topk_noalloc(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=None, dev_status=None,

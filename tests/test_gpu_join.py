@@ -1,0 +1,171 @@
+"""GPU parity of the hash join (Sec. III-B: key-based join probe returning the
+set of matched (probe, build) row pointers) against the CPU oracle: the pair
+multiset, compared sorted, bit-exact.
+
+Small and medium sizes compare every pair.  The full-size workload (2^24
+build rows, 2^28 probes) checks the exact pair count the generator fixes
+(sum of build multiplicities over the hits), key equality of every pair, and
+the exact pairs of a sample of probe rows against the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_19911_gb300 import datagen, olap
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+I64_MIN, I64_MAX = -(1 << 63), (1 << 63) - 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0)
+    yield c
+    c.close()
+
+
+def packed(pairs):
+    p = np.asarray(pairs, dtype=np.uint32).reshape(-1, 2).astype(np.uint64)
+    return np.sort((p[:, 0] << np.uint64(32)) | p[:, 1])
+
+
+def _check(ctx, bk, pk, br=None, pr=None, load=0.0, device=True):
+    if device:
+        t = ctx.join_build(torch.from_numpy(bk).cuda(),
+                           None if br is None else torch.from_numpy(br.view(np.int32)).cuda(), load)
+        dk = torch.from_numpy(pk).cuda()
+        dr = None if pr is None else torch.from_numpy(pr.view(np.int32)).cuda()
+        want = oracle.join(bk, pk, br, pr)
+        out = torch.empty((max(1, want.shape[0]), 2), dtype=torch.int32, device="cuda")
+        got = ctx.join_probe(t, dk, dr, out=out)
+        got = got.cpu().numpy().view(np.uint32)
+    else:
+        t = ctx.join_build(bk, br, load)
+        got = ctx.join_probe(t, pk, pr)
+        want = oracle.join(bk, pk, br, pr)
+    np.testing.assert_array_equal(packed(got), want)
+    t.free()
+    return want.shape[0]
+
+
+@pytest.mark.parametrize("mult", ["unique", "mult14"])
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+@pytest.mark.parametrize("hit", [0.1, 0.9])
+def test_generated_medium(ctx, mult, dist, hit):
+    b = datagen.join_build(200_003, mult, seed=11)
+    p = datagen.join_probe(1_000_003, b, hit, dist, seed=11)
+    cnt = _check(ctx, b.keys, p.keys)
+    assert cnt == p.expected_pairs(b)
+
+
+@pytest.mark.parametrize("load", [0.25, 0.5, 0.7, 0.9])
+def test_load_factors(ctx, load):
+    b = datagen.join_build(50_000, "mult14", seed=3)
+    p = datagen.join_probe(300_000, b, 0.5, "uniform", seed=3)
+    _check(ctx, b.keys, p.keys, load=load)
+
+
+def test_small_and_empty(ctx):
+    for nb, npr in [(0, 10), (10, 0), (1, 1), (31, 33), (1000, 4097)]:
+        rng = np.random.default_rng(nb + npr)
+        bk = rng.integers(-50, 50, nb).astype(np.int64)
+        pk = rng.integers(-50, 50, npr).astype(np.int64)
+        _check(ctx, bk, pk)
+
+
+def test_extreme_keys_and_empty_marker(ctx):
+    # -1 is the table's empty marker: such build rows live in the side list.
+    rng = np.random.default_rng(4)
+    alphabet = np.array([I64_MIN, I64_MAX, 0, -1, 1, -2], dtype=np.int64)
+    bk = alphabet[rng.integers(0, len(alphabet), 3000)]
+    pk = alphabet[rng.integers(0, len(alphabet), 5000)]
+    _check(ctx, bk, pk)
+    # all build keys -1
+    _check(ctx, np.full(100, -1, dtype=np.int64), np.array([-1, 0, -1], dtype=np.int64))
+
+
+def test_explicit_rowids(ctx):
+    b = datagen.join_build(100_000, "mult14", seed=6)
+    p = datagen.join_probe(400_000, b, 0.7, "zipf", seed=6)
+    br = (datagen.splitmix64(1, b.keys.shape[0]) >> np.uint64(33)).astype(np.uint32)
+    pr = (datagen.splitmix64(2, p.keys.shape[0]) >> np.uint64(33)).astype(np.uint32)
+    _check(ctx, b.keys, p.keys, br, pr)
+
+
+def test_heavy_build_duplicates(ctx):
+    # long chains: 5000 copies of a few keys
+    bk = np.repeat(np.array([7, -7, 123456789], dtype=np.int64), 5000)
+    pk = np.array([7, 8, -7, 123456789, 7], dtype=np.int64)
+    _check(ctx, bk, pk)
+
+
+@pytest.mark.parametrize("where", ["pinned", "pageable"])
+def test_host_memory(ctx, where):
+    b = datagen.join_build(100_000, "unique", seed=9)
+    p = datagen.join_probe(300_000, b, 0.5, "uniform", seed=9)
+    if where == "pinned":
+        t = ctx.join_build(torch.from_numpy(b.keys).pin_memory())
+        out = torch.empty((200_000, 2), dtype=torch.int32).pin_memory()
+        got = ctx.join_probe(t, torch.from_numpy(p.keys).pin_memory(), out=out).numpy().view(np.uint32)
+        t.free()
+        np.testing.assert_array_equal(packed(got), oracle.join(b.keys, p.keys))
+    else:
+        _check(ctx, b.keys, p.keys, device=False)
+
+
+def test_overflow_reports_required_count(ctx):
+    b = datagen.join_build(10_000, "mult14", seed=12)
+    p = datagen.join_probe(50_000, b, 0.9, "uniform", seed=12)
+    need = p.expected_pairs(b)
+    t = ctx.join_build(b.keys)
+    out = np.empty((need // 2, 2), dtype=np.uint32)
+    with pytest.raises(olap.OlapError) as ei:
+        ctx.join_probe(t, p.keys, out=out)
+    assert ei.value.status == olap.E_OVERFLOW and str(need) in str(ei.value)
+    got = ctx.join_probe(t, p.keys)            # own buffer: retried at the exact size
+    assert got.shape[0] == need
+    t.free()
+
+
+def test_golden_fixtures(ctx):
+    from tests.golden import make_golden
+    for case in make_golden.JOIN_CASES:
+        b, p = make_golden.join_input(case)
+        t = ctx.join_build(b.keys)
+        got = packed(ctx.join_probe(t, p.keys))
+        assert got.tolist() == make_golden.read_join(case["name"])
+        t.free()
+
+
+@pytest.mark.parametrize("mult,dist,hit", [("mult14", "zipf", 0.9), ("unique", "uniform", 0.1)])
+def test_full_size(ctx, mult, dist, hit):
+    """2^24 build rows, 2^28 probe keys, device resident (the benchmark's call)."""
+    b = datagen.join_build(1 << 24, mult, seed=2)
+    p = datagen.join_probe(1 << 28, b, hit, dist, seed=2)
+    need = p.expected_pairs(b)
+    t = ctx.join_build(torch.from_numpy(b.keys).cuda())
+    dk = torch.from_numpy(p.keys).cuda()
+    out = torch.empty((need, 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ctx.join_probe_async(t, dk, out, need, cnt)
+    ctx.sync()
+    assert int(cnt.item()) == need
+    pairs = out.view(torch.int64) if False else out
+    pr = pairs[:, 0].to(torch.int64) & 0xFFFFFFFF
+    br = pairs[:, 1].to(torch.int64) & 0xFFFFFFFF
+    bkd = torch.from_numpy(b.keys).cuda()
+    assert torch.equal(dk[pr], bkd[br])                       # every pair joins equal keys
+    # exact pairs of a sample of probe rows against the oracle
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(1 << 28, 4096, replace=False))
+    sel = torch.isin(pr, torch.from_numpy(rows).cuda())
+    got = packed(pairs[sel].cpu().numpy().view(np.uint32))
+    want = oracle.join(b.keys, p.keys[rows], None, rows.astype(np.uint32))
+    np.testing.assert_array_equal(got, want)
+    t.free()
+    del dk, out, bkd
+    torch.cuda.empty_cache()
