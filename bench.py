@@ -174,6 +174,82 @@ def run_reference(args):
     return 0
 
 
+def join_leg(args, ctx, torch, world):
+    """Probe of 2^log2p int64 keys against a resident table of 2^log2b build
+    rows; one probe launch per step.  Returns the join sub-object."""
+    from paper_2601_19911_gb300 import datagen, olap
+    mult, dist, hit = args.join_cell.split(",")
+    hit = float(hit)
+    nb, npr = 1 << args.join_log2b, 1 << args.join_log2p
+    b = datagen.join_build(nb, mult, seed=2)
+    p = datagen.join_probe(npr, b, hit, dist, seed=2)
+    need = p.expected_pairs(b)
+    dbk = torch.from_numpy(b.keys).cuda()
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    # build (timed once, after one warm build)
+    ctx.join_build(dbk).free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    table = ctx.join_build(dbk)
+    build_s = time.perf_counter() - t0
+    dk = torch.from_numpy(p.keys).cuda()
+    out = torch.empty((need, 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(max(3, args.warmup)):
+        ctx.join_probe_async(table, dk, out, need, cnt)
+    ctx.sync()
+    assert int(cnt.item()) == need, (int(cnt.item()), need)
+    steps = args.join_steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    _barrier(world)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        for i in range(steps):
+            evs[i][0].record(stream)
+            ctx.join_probe_async(table, dk, out, need, cnt)
+            evs[i][1].record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+    per = [a.elapsed_time(b_) for a, b_ in evs]
+    ms = _max_over_ranks(float(np.mean(per)), world)
+    # end to end: pinned host probe keys in, pairs out to pinned host memory
+    hk = torch.from_numpy(p.keys).pin_memory()
+    hout = torch.empty((need, 2), dtype=torch.int32).pin_memory()
+    ctx.join_probe(table, hk, out=hout)
+    e2e_steps = max(2, min(5, args.e2e_steps))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.join_probe(table, hk, out=hout)
+    e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    peak, peak_kind = _peaks()
+    m = need / npr
+    honest = npr * (8 + 32) + need * 8
+    stream_only = npr * 8 + need * 8
+    info = table.info()
+    table.free()
+    return {
+        "metric": "join probes/s", "unit": "Gprobes/s", "value": world * npr / (ms * 1e-3) / 1e9,
+        "ms_per_step": ms, "steps": steps,
+        "cell": {"build_rows": nb, "build": mult, "probe_rows": npr, "dist": dist, "hit_rate": hit,
+                 "pairs": need, "pairs_per_probe": m, "buckets": info["n_buckets"], "load": 0.5,
+                 "rowids": "implicit"},
+        "build": {"ms": build_s * 1e3, "Grows_per_s": nb / build_s / 1e9},
+        "roofline": {"bound": "hbm", "kernel": "olap::join_probe_kernel", "peak": peak, "peak_kind": peak_kind,
+                     "unit": "GB/s",
+                     "honest": {"bytes_per_launch": honest, "achieved": honest / (ms * 1e-3) / 1e9,
+                                "frac": honest / (ms * 1e-3) / 1e9 / peak,
+                                "bytes_per_probe": "8 key + 32 table sector + 8 per pair"},
+                     "streaming_only": {"bytes_per_launch": stream_only,
+                                        "achieved": stream_only / (ms * 1e-3) / 1e9,
+                                        "frac": stream_only / (ms * 1e-3) / 1e9 / peak},
+                     "traffic": args.join_traffic},
+        "e2e": {"value": world * npr / e2e_s / 1e9, "unit": "Gprobes/s", "ms_per_step": e2e_s * 1e3,
+                "h2d_bytes_per_step": npr * 8, "d2h_bytes_per_step": need * 8 + 8},
+        "gpu_launches": steps,
+        "clocks": clk.summary(),
+    }
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -186,6 +262,7 @@ def run_ours(args):
     from paper_2601_19911_gb300 import datagen, olap
 
     n, k = 1 << args.log2n, args.k
+    workloads = args.workload.split(",")
     filt = {"bulk": olap.FILTER_BULK, "regs": olap.FILTER_REGS}[args.filter]
     ctx = olap.Context(torch.cuda.current_device(), topk_filter=filt, topk_tile_bytes=args.tile,
                        topk_stages=args.stages, topk_ctas_per_sm=args.ctas_per_sm)
@@ -255,9 +332,14 @@ def run_ours(args):
                      "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w,
                 "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (3 if (n > (1 << 21) and k <= n // 256) else 2),
         "clocks": clk.summary(),
     }
+    if "join" in workloads:
+        del dk, hk
+        torch.cuda.empty_cache()
+        line["join"] = join_leg(args, ctx, torch, world)
+        line["gpu_launches"] += line["join"]["gpu_launches"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, k)
     if rank == 0:
@@ -283,6 +365,14 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="topk,join",
+                    help="comma list: topk (the headline value), join (probe sub-object)")
+    ap.add_argument("--join-cell", default="unique,uniform,0.9",
+                    help="build multiplicity (unique|mult14), probe distribution (uniform|zipf), hit rate")
+    ap.add_argument("--join-log2b", type=int, default=24)
+    ap.add_argument("--join-log2p", type=int, default=28)
+    ap.add_argument("--join-steps", type=int, default=50)
+    ap.add_argument("--join-traffic", type=float, default=None)
     ap.add_argument("--tile", type=int, default=0, help="bulk-copy bytes (0 = library default)")
     ap.add_argument("--stages", type=int, default=0, help="copies in flight per CTA (0 = default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM (0 = default)")
