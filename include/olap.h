@@ -195,6 +195,76 @@ olap_status olap_join_table_info(const olap_join_table* table, uint64_t* n_build
 void olap_join_free(olap_join_table* table);
 
 /* ------------------------------------------------------------------------
+ * Risky Gate (Sec. II-B; fitted constants and break-even N*, Sec. V-D).
+ *
+ * The gate offloads only when the estimated CPU cost exceeds the estimated
+ * GPU cost by more than a margin (ms):
+ *   C_cpu  = a * x + b, x = N * log2(N) or N * K (Top-K; the form with the
+ *            smaller residual on the calibration samples is kept, N log2 N on
+ *            a tie) or N * M (probe; M = expected candidates per probe)
+ *   C_gpu  = C_tx + C_ker + C_post, C_tx = c * bytes + d (key-only transfer),
+ *            C_ker = e * N + f, C_post = g * rows returned + h
+ *            (result return and late materialization)
+ *   offload  <=>  C_cpu - C_gpu > margin  (strict)
+ * Every fit is ordinary least squares in the centred closed form of the 2x2
+ * normal equations.  N* is the smallest integer N in [1, 2^34] where
+ * C_cpu(N) - C_gpu(N) > margin for the query's K (or M), with transfer bytes
+ * and returned rows scaled with N as the query says; 1 if that already holds
+ * at N = 1 and 0 ("never") if it fails at 2^34.  Pure host arithmetic: these
+ * calls touch no device.  The gate only advises; it runs no CPU path.
+ * ------------------------------------------------------------------------ */
+typedef enum { OLAP_OP_TOPK = 0, OLAP_OP_PROBE = 1 } olap_op;
+typedef enum { OLAP_CPU_NLOGN = 0, OLAP_CPU_NK = 1, OLAP_CPU_NM = 2 } olap_cpu_form;
+
+typedef struct {
+    olap_op op;
+    uint64_t count;               /* number of samples (>= 2) */
+    const double* n;              /* input rows N */
+    const double* k_or_m;         /* Top-K: K; probe: M */
+    const double* tx_bytes;       /* bytes moved to the device */
+    const double* out_rows;       /* rows returned (K, or pairs) */
+    const double* t_cpu_ms;       /* measured CPU engine time */
+    const double* t_tx_ms;        /* measured transfer time */
+    const double* t_ker_ms;       /* measured kernel time */
+    const double* t_post_ms;      /* measured result return + materialization time */
+} olap_gate_samples;
+
+typedef struct {
+    olap_op op;
+    olap_cpu_form cpu_form;
+    double a, b;                  /* CPU: a * x + b */
+    double c, d;                  /* transfer: c * bytes + d */
+    double e, f;                  /* kernel: e * N + f */
+    double g, h;                  /* post-processing: g * rows + h */
+    double margin_ms;
+    double rss_nlogn, rss_nk;     /* Top-K: residual sums of squares of both CPU forms */
+} olap_gate_model;
+
+typedef struct {
+    olap_op op;
+    uint64_t n;                   /* input rows */
+    double k_or_m;                /* K (Top-K) or M (probe) */
+    double tx_bytes;              /* bytes this query moves to the device */
+    double out_rows;              /* rows this query returns */
+    double bytes_per_row;         /* for N*: transfer bytes per input row */
+    double out_per_row;           /* for N* of a probe: returned rows per input row */
+} olap_gate_query;
+
+typedef struct {
+    int offload;                  /* 1 => run on the GPU */
+    double c_cpu, c_tx, c_ker, c_post, c_gpu;
+    double gain_ms;               /* c_cpu - c_gpu */
+    double margin_ms;
+    uint64_t n_star;              /* break-even N for this query's shape */
+} olap_gate_decision;
+
+/* Fit the model from measured samples; margin_ms is stored in it. */
+olap_status olap_gate_calibrate(const olap_gate_samples* samples, double margin_ms, olap_gate_model* out);
+/* Decide one query and report its costs and break-even N*. */
+olap_status olap_gate_estimate(const olap_gate_model* model, const olap_gate_query* query,
+                               olap_gate_decision* out);
+
+/* ------------------------------------------------------------------------
  * Top-K that allocates nothing (no counterpart in the paper: a deployment
  * entry point for callers that cannot let a library allocate GPU memory --
  * engines whose device memory is wholly reserved by their own pool, plug-in

@@ -29,7 +29,10 @@ EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
+    "olap_gate_calibrate", "olap_gate_estimate",
 ]
+OP_TOPK, OP_PROBE = 0, 1
+CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
 NOALLOC_MAX_N = 1 << 24
 NOALLOC_MAX_K = 4096
@@ -55,6 +58,33 @@ class olap_opts(ctypes.Structure):
         ("topk_stages", ctypes.c_int),
         ("topk_ctas_per_sm", ctypes.c_int),
     ]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class olap_gate_samples(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("count", ctypes.c_uint64), ("n", _dp), ("k_or_m", _dp),
+                ("tx_bytes", _dp), ("out_rows", _dp), ("t_cpu_ms", _dp), ("t_tx_ms", _dp),
+                ("t_ker_ms", _dp), ("t_post_ms", _dp)]
+
+
+class olap_gate_model(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("cpu_form", ctypes.c_int)] + \
+        [(nm, ctypes.c_double) for nm in ("a", "b", "c", "d", "e", "f", "g", "h", "margin_ms", "rss_nlogn",
+                                          "rss_nk")]
+
+
+class olap_gate_query(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("n", ctypes.c_uint64), ("k_or_m", ctypes.c_double),
+                ("tx_bytes", ctypes.c_double), ("out_rows", ctypes.c_double),
+                ("bytes_per_row", ctypes.c_double), ("out_per_row", ctypes.c_double)]
+
+
+class olap_gate_decision(ctypes.Structure):
+    _fields_ = [("offload", ctypes.c_int)] + \
+        [(nm, ctypes.c_double) for nm in ("c_cpu", "c_tx", "c_ker", "c_post", "c_gpu", "gain_ms", "margin_ms")] + \
+        [("n_star", ctypes.c_uint64)]
 
 
 class olap_topk_info(ctypes.Structure):
@@ -111,6 +141,12 @@ def load(path: str | None = None):
         lib.olap_join_table_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
         lib.olap_join_free.restype = None
         lib.olap_join_free.argtypes = [vp]
+        lib.olap_gate_calibrate.restype = i32
+        lib.olap_gate_calibrate.argtypes = [ctypes.POINTER(olap_gate_samples), ctypes.c_double,
+                                            ctypes.POINTER(olap_gate_model)]
+        lib.olap_gate_estimate.restype = i32
+        lib.olap_gate_estimate.argtypes = [ctypes.POINTER(olap_gate_model), ctypes.POINTER(olap_gate_query),
+                                           ctypes.POINTER(olap_gate_decision)]
         lib.olap_topk_noalloc.restype = i32
         lib.olap_topk_noalloc.argtypes = [vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         _bind_more(lib)
@@ -350,3 +386,36 @@ def topk_noalloc(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=
                                ptr(d_out_keys), ptr(d_out_rowids), ptr(dev_status), stream)
     if st != OK:
         raise OlapError(st, "olap_topk_noalloc failed")
+
+
+# ---------------------------------------------------------------------------
+# Risky Gate (host arithmetic in the library; no device needed)
+# ---------------------------------------------------------------------------
+
+def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_ker_ms, t_post_ms,
+                   margin_ms: float = 0.0) -> olap_gate_model:
+    """olap_gate_calibrate over equal-length sample sequences (times in ms)."""
+    lib = load()
+    cols = [np.ascontiguousarray(np.asarray(c, dtype=np.float64)) for c in
+            (n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_ker_ms, t_post_ms)]
+    cnt = cols[0].shape[0]
+    assert all(c.shape[0] == cnt for c in cols)
+    ptrs = [c.ctypes.data_as(_dp) for c in cols]
+    smp = olap_gate_samples(op, cnt, *ptrs)
+    m = olap_gate_model()
+    st = lib.olap_gate_calibrate(ctypes.byref(smp), float(margin_ms), ctypes.byref(m))
+    if st != OK:
+        raise OlapError(st, "olap_gate_calibrate rejected the samples")
+    return m
+
+
+def gate_estimate(model: olap_gate_model, op: int, n: int, k_or_m: float, tx_bytes: float, out_rows: float,
+                  bytes_per_row: float = 0.0, out_per_row: float = 0.0) -> olap_gate_decision:
+    lib = load()
+    q = olap_gate_query(op, int(n), float(k_or_m), float(tx_bytes), float(out_rows), float(bytes_per_row),
+                        float(out_per_row))
+    d = olap_gate_decision()
+    st = lib.olap_gate_estimate(ctypes.byref(model), ctypes.byref(q), ctypes.byref(d))
+    if st != OK:
+        raise OlapError(st, "olap_gate_estimate rejected the query")
+    return d

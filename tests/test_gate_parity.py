@@ -1,0 +1,84 @@
+"""Parity of the library's Risky Gate (host arithmetic inside libolap.so, so
+this runs without a GPU) with the gate oracle (Sec. II-B decision; Sec. V-D
+fits and break-even N*): fitted coefficients within 1e-9 relative (fp64 with
+a different summation order), the same CPU form, and the same decisions and
+N* away from knife-edge ties."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import gate
+from paper_2601_19911_gb300 import build, olap
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    return olap.load()
+
+
+def _noisy_samples(rng, op, form, count=24):
+    n = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(1e8), count)))
+    if op == gate.TOPK:
+        km = np.floor(np.exp(rng.uniform(0, np.log(1e5), count)))
+        km = np.minimum(km, n)
+        x = n * np.log2(n) if form == gate.CPU_NLOGN else n * km
+        out = km
+        bpr = 8.0
+    else:
+        km = rng.uniform(1.0, 3.5, count)
+        x = n * km
+        out = n * (km - 1.0)
+        bpr = 8.0
+    noise = lambda: 1.0 + rng.normal(0.0, 0.03, count)
+    t_cpu = (2e-6 * x + 0.05) * noise()
+    tx = bpr * n
+    t_tx = (1.0 / 2.0e8 * tx + 0.02) * noise()
+    t_ker = (2e-8 * n + 0.01) * noise()
+    t_post = (5e-7 * out + 0.005) * noise()
+    return n, km, tx, out, t_cpu, t_tx, t_ker, t_post
+
+
+@pytest.mark.parametrize("op,form", [(gate.TOPK, gate.CPU_NLOGN), (gate.TOPK, gate.CPU_NK),
+                                     (gate.PROBE, gate.CPU_NM)])
+@pytest.mark.parametrize("seed", range(4))
+def test_calibrate_and_decide_match_oracle(op, form, seed):
+    rng = np.random.default_rng(seed)
+    smp = _noisy_samples(rng, op, form)
+    for margin in (0.0, 5.0, 10.0):
+        want = gate.calibrate(op, *smp, margin_ms=margin)
+        got = olap.gate_calibrate(op, *smp, margin_ms=margin)
+        assert got.cpu_form == want.cpu_form
+        for nm in "abcdefgh":
+            assert math.isclose(getattr(got, nm), getattr(want, nm), rel_tol=1e-9, abs_tol=1e-15), nm
+        qn = np.floor(np.exp(rng.uniform(np.log(1e2), np.log(1e9), 50))).astype(np.int64)
+        for nq in qn:
+            km = 100.0 if op == gate.TOPK else 1.9
+            out = min(km, nq) if op == gate.TOPK else nq * (km - 1.0)
+            d = olap.gate_estimate(got, op, nq, km, 8.0 * nq, out, 8.0, km - 1.0)
+            c = gate.costs(want, nq, km, 8.0 * nq, out)
+            gain = c[0] - (c[1] + c[2] + c[3])
+            if abs(gain - margin) > 1e-9 * max(1.0, abs(gain)):
+                assert bool(d.offload) == (gain > margin)
+            assert math.isclose(d.c_cpu, c[0], rel_tol=1e-9, abs_tol=1e-12)
+            ns = gate.n_star(want, km, 8.0, km - 1.0, km if op == gate.TOPK else None)
+            assert abs(int(d.n_star) - ns) <= max(1, ns * 1e-9)
+
+
+def test_exact_knife_edge_is_not_offloaded():
+    # dyadic constants: C_cpu - C_gpu equals the margin exactly (the paper's
+    # "exceeds" is strict).  n=8, M=2: C_cpu = 0.5*16 + 1 = 9; C_tx = 0.25*8 +
+    # 0.5 = 2.5; C_ker = 0.125*8 = 1; C_post = 0 -> gain 5.5.
+    model = olap.olap_gate_model(gate.PROBE, gate.CPU_NM, 0.5, 1.0, 0.25, 0.5, 0.125, 0.0, 0.0, 0.0, 5.5, 0.0, 0.0)
+    d = olap.gate_estimate(model, gate.PROBE, 8, 2.0, 8.0, 0.0)
+    assert d.gain_ms == 5.5 and d.offload == 0
+    model.margin_ms = 5.25
+    assert olap.gate_estimate(model, gate.PROBE, 8, 2.0, 8.0, 0.0).offload == 1
+    o = gate.Model(gate.PROBE, gate.CPU_NM, 0.5, 1.0, 0.25, 0.5, 0.125, 0.0, 0.0, 0.0, 5.5)
+    assert not gate.decide(o, 8, 2.0, 8.0, 0.0)
+
+
+def test_rejects_bad_input():
+    with pytest.raises(olap.OlapError):
+        olap.gate_calibrate(gate.TOPK, [1.0], [1.0], [1.0], [1.0], [1.0], [1.0], [1.0], [1.0])
