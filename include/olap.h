@@ -195,6 +195,50 @@ olap_status olap_join_table_info(const olap_join_table* table, uint64_t* n_build
 void olap_join_free(olap_join_table* table);
 
 /* ------------------------------------------------------------------------
+ * Batched execution: many Top-K queries and probe batches in one persistent
+ * launch fed by a device work queue and captured in a CUDA graph, against
+ * one launch per query (the small-N overhead of Sec. IV, small-N interval).
+ *
+ * Every item is one Top-K (keys, n, k <= 4096, order; outputs as olap_topk,
+ * count receives min(k, n)) or one probe (keys, n, against a resident table;
+ * pairs as olap_join_probe, count receives the pair count, which may exceed
+ * capacity).  All pointers are device pointers; count is a device uint64;
+ * status (device int32, may be NULL) receives OLAP_OK or OLAP_E_DEVICE when
+ * the device-side check of the descriptor rejects it.  The items' buffers
+ * must outlive the batch; their contents may change between runs.
+ * ------------------------------------------------------------------------ */
+typedef struct olap_batch olap_batch;
+
+typedef struct {
+    int op;                          /* olap_op */
+    int key_type;                    /* Top-K: olap_key_type */
+    int order;                       /* Top-K: olap_order */
+    const void* keys;
+    const uint32_t* rowids;          /* NULL => index */
+    uint64_t n;
+    uint64_t k;                      /* Top-K */
+    void* out_keys;                  /* Top-K */
+    uint32_t* out_rowids;            /* Top-K */
+    const olap_join_table* table;    /* probe */
+    olap_pair* out_pairs;            /* probe */
+    uint64_t capacity;               /* probe */
+    uint64_t* count;                 /* device: rows (Top-K) or pairs (probe) written */
+    int32_t* status;                 /* device, optional */
+} olap_batch_item;
+
+/* Check the items, upload the work queue (largest items first) and capture
+ * the persistent launch in a CUDA graph.  Blocking. */
+olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint64_t n_items, olap_batch** out);
+/* Run every item once: one graph launch on `stream` (NULL => context stream). */
+olap_status olap_batch_run(olap_batch* batch, void* stream);
+/* The same work as one library call per item (olap_topk_async /
+ * olap_join_probe_async) on `stream`: the per-query baseline. */
+olap_status olap_batch_run_per_query(olap_batch* batch, void* stream);
+/* Number of descriptors the device rejected in the last run (waits for it). */
+olap_status olap_batch_errors(olap_batch* batch, int* errors);
+void olap_batch_free(olap_batch* batch);
+
+/* ------------------------------------------------------------------------
  * Risky Gate (Sec. II-B; fitted constants and break-even N*, Sec. V-D).
  *
  * The gate offloads only when the estimated CPU cost exceeds the estimated

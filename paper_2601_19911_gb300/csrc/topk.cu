@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "block.cuh"
 #include "topk.cuh"
 
 namespace olap {
@@ -37,10 +38,6 @@ struct Elem {
     uint64_t r;
     uint32_t rid;
 };
-
-__device__ __forceinline__ bool elem_less(uint64_t ar, uint32_t arid, uint64_t br, uint32_t brid) {
-    return ar < br || (ar == br && arid < brid);
-}
 
 __device__ __forceinline__ Elem load_input(const TopkArgs& a, uint64_t i) {
     Elem e;
@@ -55,117 +52,6 @@ __device__ __forceinline__ Elem load_input(const TopkArgs& a, uint64_t i) {
 __device__ __forceinline__ Elem load_src(const TopkArgs& a, bool cand, uint64_t i) {
     if (cand) return Elem{__ldcg(a.cand_r + i), __ldcg(a.cand_rid + i)};
     return load_input(a, i);
-}
-
-__device__ __forceinline__ uint4 ld_stream_v4(const void* p) {
-    uint4 v;
-    asm volatile("ld.global.cs.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-
-// Block-wide exclusive scan helper over one value per thread (TK_TPB threads).
-__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long v,
-                                                              unsigned long long* warp_sums,
-                                                              unsigned long long* total) {
-    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    unsigned long long incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= static_cast<unsigned>(o)) incl += t;
-    }
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        constexpr int NW = TK_TPB / 32;
-        unsigned long long w = lane < NW ? warp_sums[lane] : 0ull;
-        unsigned long long wi = w;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long t = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            if (lane >= static_cast<unsigned>(o)) wi += t;
-        }
-        if (lane < NW) warp_sums[lane] = wi - w;
-        if (lane == NW - 1) *total = wi;
-    }
-    __syncthreads();
-    const unsigned long long r = warp_sums[warp] + incl - v;
-    __syncthreads();
-    return r;
-}
-
-// Find the bucket b of a TK_BINS histogram where the running count first
-// reaches `need` (1 <= need <= total).  Every thread gets b, the count below b
-// and the count in b.
-struct Pick {
-    unsigned b;
-    unsigned long long below;
-    unsigned long long in_b;
-};
-
-__device__ Pick pick_bucket(const unsigned* hist, unsigned long long need, unsigned long long* sc) {
-    constexpr int PER = TK_BINS / TK_TPB;   // 8 bins per thread
-    unsigned v[PER];
-    unsigned long long local = 0;
-    const volatile unsigned* h = hist;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        v[j] = h[threadIdx.x * PER + j];
-        local += v[j];
-    }
-    unsigned long long* warp_sums = sc;        // 16 entries
-    unsigned long long* total = sc + 16;
-    unsigned long long* res = sc + 17;         // b, below, in_b
-    const unsigned long long before = block_excl_scan(local, warp_sums, total);
-    if (before < need && need <= before + local) {
-        unsigned long long run = before;
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            if (run < need && need <= run + v[j]) {
-                res[0] = threadIdx.x * PER + j;
-                res[1] = run;
-                res[2] = v[j];
-            }
-            run += v[j];
-        }
-    }
-    __syncthreads();
-    Pick p{static_cast<unsigned>(res[0]), res[1], res[2]};
-    __syncthreads();
-    return p;
-}
-
-// Bitonic sort of `count` (<= TK_SMALL) entries in shared memory, ascending
-// by (r, rid); padded to a power of two with all-ones entries.
-__device__ void block_sort(uint64_t* sr, uint32_t* srid, int count) {
-    int m = 1;
-    while (m < count) m <<= 1;
-    for (int i = count + threadIdx.x; i < m; i += TK_TPB) {
-        sr[i] = ~0ull;
-        srid[i] = ~0u;
-    }
-    __syncthreads();
-    for (int size = 2; size <= m; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < (m >> 1); t += TK_TPB) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = ((lo & size) == 0);
-                const uint64_t a = sr[lo], b = sr[hi];
-                const uint32_t ar = srid[lo], br = srid[hi];
-                const bool swap = up ? elem_less(b, br, a, ar) : elem_less(a, ar, b, br);
-                if (swap) {
-                    sr[lo] = b;
-                    sr[hi] = a;
-                    srid[lo] = br;
-                    srid[hi] = ar;
-                }
-            }
-            __syncthreads();
-        }
-    }
 }
 
 __device__ __forceinline__ void write_result(const TopkArgs& a, uint64_t i, uint64_t r, uint32_t rid) {
@@ -204,7 +90,7 @@ __device__ uint64_t sample_threshold(const TopkArgs& a, unsigned* sh, unsigned l
             if (match) atomicAdd(&sh[static_cast<unsigned>((s[j] << L) >> (64 - d))], 1u);
         }
         __syncthreads();
-        const Pick pk = pick_bucket(sh, rem, sc);
+        const Pick pk = pick_bucket<TK_TPB>(sh, rem, sc);
         prefix |= static_cast<uint64_t>(pk.b) << (64 - L - d);
         rem -= pk.below;
         cum += pk.below;
@@ -212,46 +98,6 @@ __device__ uint64_t sample_threshold(const TopkArgs& a, unsigned* sh, unsigned l
     }
     return prefix;
 }
-
-// The threshold of the streaming pass moved into the key domain, so that a
-// key is tested with one XOR and one unsigned comparison and no transform:
-// `rank <= t` holds exactly when `(key ^ m) >= c` for the (m, c) below.
-//   int64: rank = key ^ SIGN (ASC) or its complement (DESC); the signed key
-//     order is the unsigned order of key ^ SIGN, and "<=" becomes ">=" on
-//     the complement.
-//   float32: the rank's significant half u(x) is <= t32 = t >> 32 (its low
-//     half is zero).  With y = x ^ ((x >> 31) & 0x7FFFFFFF) the signed image of
-//     totalOrder and L the signed limit on y, each of the four cases (order x
-//     sign of L) is one unsigned comparison of x under a fixed XOR mask:
-//       DESC, L >= 0: y >= L  <=>  x ^ 0x80000000 >= L ^ 0x80000000
-//       DESC, L <  0: y >= L  <=>  ~x >= ~(L ^ 0x7FFFFFFF)
-//       ASC,  L >= 0: y <= L  <=>  x ^ 0x7FFFFFFF >= L ^ 0x7FFFFFFF
-//       ASC,  L <  0: y <= L  <=>  x >= L ^ 0x7FFFFFFF
-//     (XOR with 0x7FFFFFFF reverses the signed order among negative values.)
-struct KeyLimit {
-    uint64_t m64, c64;
-    uint32_t m32, c32;
-};
-__device__ __forceinline__ KeyLimit key_limit(uint64_t t, bool desc) {
-    KeyLimit k;
-    const uint64_t lim = (desc ? ~t : t) ^ SIGN64;              // signed limit on the int64 key
-    // DESC: key >= lim  <=> key ^ SIGN >= lim ^ SIGN;  ASC: key <= lim <=> key ^ ~SIGN >= lim ^ ~SIGN
-    k.m64 = desc ? SIGN64 : ~SIGN64;
-    k.c64 = lim ^ k.m64;
-    const uint32_t t32 = static_cast<uint32_t>(t >> 32);
-    const int32_t L = static_cast<int32_t>((desc ? ~t32 : t32) ^ 0x80000000u);
-    const uint32_t uL = static_cast<uint32_t>(L);
-    if (desc) {
-        if (L >= 0) { k.m32 = 0x80000000u; k.c32 = uL ^ 0x80000000u; }
-        else        { k.m32 = 0xFFFFFFFFu; k.c32 = ~(uL ^ 0x7FFFFFFFu); }
-    } else {
-        if (L >= 0) { k.m32 = 0x7FFFFFFFu; k.c32 = uL ^ 0x7FFFFFFFu; }
-        else        { k.m32 = 0u;          k.c32 = uL ^ 0x7FFFFFFFu; }
-    }
-    return k;
-}
-__device__ __forceinline__ bool pass_i64(uint64_t bits, const KeyLimit& k) { return (bits ^ k.m64) >= k.c64; }
-__device__ __forceinline__ bool pass_f32(uint32_t bits, const KeyLimit& k) { return (bits ^ k.m32) >= k.c32; }
 
 // Hits of the streaming pass are staged per warp in shared memory and
 // flushed to the global candidate buffer WS_CAP at a time: one atomic on the
@@ -711,7 +557,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
         unsigned* gz = a.ghist + ((pass + 1) % 3) * TK_BINS;
         hist_pass(a, cand, src_n, p0, p1, L, d, kb, gh, gz, sh);
         if (!grid_sync(a.bar, &ctl->err)) return report(a);
-        const Pick pk = pick_bucket(gh, krem, sc);
+        const Pick pk = pick_bucket<TK_TPB>(gh, krem, sc);
         krem -= pk.below;
         bcnt = pk.in_b;
         prefix_set(p0, p1, L, d, pk.b);
@@ -853,7 +699,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
             local += v[j];
             mx = max(mx, v[j]);
         }
-        const unsigned long long before = block_excl_scan(local, reinterpret_cast<unsigned long long*>(sc),
+        const unsigned long long before = block_excl_scan<TK_TPB>(local, reinterpret_cast<unsigned long long*>(sc),
                                                           reinterpret_cast<unsigned long long*>(sc) + 16);
         unsigned* off = sh;                                      // exclusive offsets per bucket
         {
@@ -925,7 +771,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
                 srid[i] = __ldcg(a.small_rid + i);
             }
             __syncthreads();
-            block_sort(sr, srid, cnt);
+            block_sort<TK_TPB>(sr, srid, cnt);
             const uint64_t base = a.k - krem;
             for (uint64_t i = threadIdx.x; i < krem; i += TK_TPB) {
                 a.out_r0[base + i] = sr[i];
@@ -941,7 +787,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
                 srid[i] = __ldcg(a.out_rid0 + i);
             }
             __syncthreads();
-            block_sort(sr, srid, cnt);
+            block_sort<TK_TPB>(sr, srid, cnt);
             if (stamp) ctl->ts[8] = gtimer();
             for (int i = threadIdx.x; i < cnt; i += TK_TPB) write_result(a, i, sr[i], srid[i]);
             if (threadIdx.x == 0 && a.dev_status) *a.dev_status = ld_volatile_i32(&ctl->err);
@@ -962,7 +808,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
             srid[i] = __ldcg(a.out_rid0 + lo + i);
         }
         __syncthreads();
-        block_sort(sr, srid, cnt);
+        block_sort<TK_TPB>(sr, srid, cnt);
         for (int i = threadIdx.x; i < cnt; i += TK_TPB) {
             a.out_r0[lo + i] = sr[i];
             a.out_rid0[lo + i] = srid[i];

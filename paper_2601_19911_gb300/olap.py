@@ -30,6 +30,7 @@ EXPORTS = [
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
+    "olap_batch_create", "olap_batch_run", "olap_batch_run_per_query", "olap_batch_errors", "olap_batch_free",
 ]
 OP_TOPK, OP_PROBE = 0, 1
 CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
@@ -85,6 +86,14 @@ class olap_gate_decision(ctypes.Structure):
     _fields_ = [("offload", ctypes.c_int)] + \
         [(nm, ctypes.c_double) for nm in ("c_cpu", "c_tx", "c_ker", "c_post", "c_gpu", "gain_ms", "margin_ms")] + \
         [("n_star", ctypes.c_uint64)]
+
+
+class olap_batch_item(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("key_type", ctypes.c_int), ("order", ctypes.c_int),
+                ("keys", ctypes.c_void_p), ("rowids", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("k", ctypes.c_uint64), ("out_keys", ctypes.c_void_p), ("out_rowids", ctypes.c_void_p),
+                ("table", ctypes.c_void_p), ("out_pairs", ctypes.c_void_p), ("capacity", ctypes.c_uint64),
+                ("count", ctypes.c_void_p), ("status", ctypes.c_void_p)]
 
 
 class olap_topk_info(ctypes.Structure):
@@ -147,6 +156,16 @@ def load(path: str | None = None):
         lib.olap_gate_estimate.restype = i32
         lib.olap_gate_estimate.argtypes = [ctypes.POINTER(olap_gate_model), ctypes.POINTER(olap_gate_query),
                                            ctypes.POINTER(olap_gate_decision)]
+        lib.olap_batch_create.restype = i32
+        lib.olap_batch_create.argtypes = [vp, ctypes.POINTER(olap_batch_item), u64, ctypes.POINTER(vp)]
+        lib.olap_batch_run.restype = i32
+        lib.olap_batch_run.argtypes = [vp, vp]
+        lib.olap_batch_run_per_query.restype = i32
+        lib.olap_batch_run_per_query.argtypes = [vp, vp]
+        lib.olap_batch_errors.restype = i32
+        lib.olap_batch_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        lib.olap_batch_free.restype = None
+        lib.olap_batch_free.argtypes = [vp]
         lib.olap_topk_noalloc.restype = i32
         lib.olap_topk_noalloc.argtypes = [vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         _bind_more(lib)
@@ -329,6 +348,14 @@ class Context:
         self.check(self.lib.olap_join_probe_async(self.h, table.h, ptr(d_keys), ptr(d_rowids), numel(d_keys),
                                                   ptr(d_out), int(capacity), ptr(d_count), stream))
 
+    # -- Batched executor ----------------------------------------------------
+    def batch(self, items) -> "Batch":
+        """olap_batch_create from a list of olap_batch_item."""
+        arr = (olap_batch_item * max(1, len(items)))(*items)
+        h = ctypes.c_void_p()
+        self.check(self.lib.olap_batch_create(self.h, arr, len(items), ctypes.byref(h)))
+        return Batch(self, h)
+
     def topk_info(self) -> dict:
         """olap_topk_info_last as a dict (phase times in microseconds)."""
         info = olap_topk_info()
@@ -344,6 +371,47 @@ class Context:
                                       numel(d_keys), int(k), int(order), ptr(d_out_keys),
                                       ptr(d_out_rowids), ptr(dev_status), stream)
         self.check(st)
+
+
+class Batch:
+    """A captured batch (olap_batch): run() replays its CUDA graph."""
+
+    def __init__(self, ctx: "Context", h):
+        self.ctx = ctx
+        self.h = h
+
+    def run(self, stream: int | None = None):
+        self.ctx.check(self.ctx.lib.olap_batch_run(self.h, stream))
+
+    def run_per_query(self, stream: int | None = None):
+        self.ctx.check(self.ctx.lib.olap_batch_run_per_query(self.h, stream))
+
+    def errors(self) -> int:
+        e = ctypes.c_int()
+        self.ctx.check(self.ctx.lib.olap_batch_errors(self.h, ctypes.byref(e)))
+        return e.value
+
+    def free(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.olap_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def topk_item(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_count, d_rowids=None, d_status=None):
+    return olap_batch_item(OP_TOPK, key_type_of(d_keys), order, ptr(d_keys), ptr(d_rowids), numel(d_keys), k,
+                           ptr(d_out_keys), ptr(d_out_rowids), None, None, 0, ptr(d_count), ptr(d_status))
+
+
+def probe_item(table: "JoinTable", d_keys, d_out_pairs, capacity: int, d_count, d_rowids=None, d_status=None):
+    return olap_batch_item(OP_PROBE, KEY_I64, 0, ptr(d_keys), ptr(d_rowids), numel(d_keys), 0, None, None,
+                           table.h.value if isinstance(table.h, ctypes.c_void_p) else table.h, ptr(d_out_pairs),
+                           capacity, ptr(d_count), ptr(d_status))
 
 
 class JoinTable:
