@@ -250,6 +250,77 @@ def join_leg(args, ctx, torch, world):
     }
 
 
+def batched_leg(args, ctx, torch):
+    """4096 Top-K queries (N ~ logU[1e3, 4e6) int64 uniform, K ~ U{1..1000},
+    implicit row-ids) and 1024 probe batches (n ~ logU[1e3, 1e6)) against one
+    resident 2^22-key unique table (hit rate 0.5), all device resident: one
+    graph launch of the persistent executor against one library call per
+    query on one stream."""
+    from paper_2601_19911_gb300 import datagen, olap
+    ns, ks = datagen.batched_topk_queries(args.batch_topk, 1e3, 4e6, 1000, seed=3)
+    offs = np.concatenate([[0], np.cumsum(ns)])
+    keys = datagen.splitmix64_torch(datagen.stream_seed(3, 0), int(offs[-1]), device="cuda")
+    koffs = np.concatenate([[0], np.cumsum(ks)])
+    out_k = torch.empty(int(koffs[-1]), dtype=torch.int64, device="cuda")
+    out_r = torch.empty(int(koffs[-1]), dtype=torch.int32, device="cuda")
+    nitems = args.batch_topk + args.batch_probe
+    counts = torch.zeros(nitems, dtype=torch.int64, device="cuda")
+    status = torch.zeros(nitems, dtype=torch.int32, device="cuda")
+    items = []
+    for i in range(args.batch_topk):
+        items.append(olap.topk_item(keys[int(offs[i]):int(offs[i + 1])], int(ks[i]), olap.DESC,
+                                    out_k[int(koffs[i]):int(koffs[i + 1])], out_r[int(koffs[i]):int(koffs[i + 1])],
+                                    counts[i:i + 1], d_status=status[i:i + 1]))
+    b = datagen.join_build(1 << 22, "unique", seed=3)
+    table = ctx.join_build(torch.from_numpy(b.keys).cuda())
+    pns = datagen.batched_probe_sizes(args.batch_probe, 1e3, 1e6, seed=3)
+    poffs = np.concatenate([[0], np.cumsum(pns)])
+    p = datagen.join_probe(int(poffs[-1]), b, 0.5, "uniform", seed=3)
+    hits = np.concatenate([[0], np.cumsum(p.hit)])
+    pk = torch.from_numpy(p.keys).cuda()
+    pairs = torch.empty((int(hits[-1]) + 1, 2), dtype=torch.int32, device="cuda")
+    for j in range(args.batch_probe):
+        a, e = int(poffs[j]), int(poffs[j + 1])
+        h0, h1 = int(hits[a]), int(hits[e])
+        items.append(olap.probe_item(table, pk[a:e], pairs[h0:h1 + 1], h1 - h0,
+                                     counts[args.batch_topk + j:args.batch_topk + j + 1],
+                                     d_status=status[args.batch_topk + j:args.batch_topk + j + 1]))
+    batch = ctx.batch(items)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        ctx.sync()
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        for _ in range(reps):
+            fn()
+        b_.record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+        return a_.elapsed_time(b_) / reps
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms_graph = timed(batch.run, args.batch_reps)
+    errors = batch.errors()
+    ok = int((status != olap.OK).sum().item()) == 0
+    ms_per_query = timed(batch.run_per_query, max(1, args.batch_reps // 5))
+    peak, peak_kind = _peaks()
+    algo = float(offs[-1]) * 8 + float(ks.sum()) * 24 + float(poffs[-1]) * 40 + float(hits[-1]) * 8
+    batch.free()
+    table.free()
+    return {"metric": "batched vs per-query speedup", "value": ms_per_query / ms_graph, "unit": "x",
+            "graph_ms": ms_graph, "per_query_ms": ms_per_query, "device_errors": errors, "all_ok": ok,
+            "items": {"topk": args.batch_topk, "probe": args.batch_probe, "topk_keys": int(offs[-1]),
+                      "probes": int(poffs[-1]), "pairs": int(hits[-1])},
+            "roofline": {"bound": "hbm", "algorithmic_bytes": algo, "achieved": algo / (ms_graph * 1e-3) / 1e9,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": algo / (ms_graph * 1e-3) / 1e9 / peak,
+                         "bytes": "8 per Top-K key + 24 per selected row + 40 per probe + 8 per pair"},
+            "gpu_launches_graph": 2, "clocks": clk.summary()}
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -340,6 +411,10 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["join"] = join_leg(args, ctx, torch, world)
         line["gpu_launches"] += line["join"]["gpu_launches"]
+    if "batched" in workloads:
+        torch.cuda.empty_cache()
+        line["batched"] = batched_leg(args, ctx, torch)
+        line["gpu_launches"] += 2 * args.batch_reps
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, k)
     if rank == 0:
@@ -365,14 +440,17 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,join",
-                    help="comma list: topk (the headline value), join (probe sub-object)")
+    ap.add_argument("--workload", default="topk,join,batched",
+                    help="comma list: topk (the headline value), join (probe sub-object), batched (executor)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",
                     help="build multiplicity (unique|mult14), probe distribution (uniform|zipf), hit rate")
     ap.add_argument("--join-log2b", type=int, default=24)
     ap.add_argument("--join-log2p", type=int, default=28)
     ap.add_argument("--join-steps", type=int, default=50)
     ap.add_argument("--join-traffic", type=float, default=None)
+    ap.add_argument("--batch-topk", type=int, default=4096)
+    ap.add_argument("--batch-probe", type=int, default=1024)
+    ap.add_argument("--batch-reps", type=int, default=10)
     ap.add_argument("--tile", type=int, default=0, help="bulk-copy bytes (0 = library default)")
     ap.add_argument("--stages", type=int, default=0, help="copies in flight per CTA (0 = default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM (0 = default)")

@@ -66,6 +66,33 @@ def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
     return out
 
 
+def _i64(v: int) -> int:
+    v &= 0xFFFFFFFFFFFFFFFF
+    return v - (1 << 64) if v >> 63 else v
+
+
+def splitmix64_torch(seed: int, count: int, start: int = 0, device="cuda", chunk: int = 1 << 26):
+    """The same draws as ``splitmix64`` as a torch int64 tensor (bit-identical),
+    computed on ``device`` with wrapping int64 arithmetic (logical shifts are
+    an arithmetic shift and a mask)."""
+    import torch
+    out = torch.empty(int(count), dtype=torch.int64, device=device)
+    g, m1, m2 = _i64(GAMMA), _i64(0xBF58476D1CE4E5B9), _i64(0x94D049BB133111EB)
+    s0 = _i64(seed)
+
+    def lsr(x, k):
+        return (x >> k) & ((1 << (64 - k)) - 1)
+
+    for a in range(0, int(count), chunk):
+        b = min(int(count), a + chunk)
+        i = torch.arange(start + a + 1, start + b + 1, dtype=torch.int64, device=device)
+        z = i * g + s0
+        z = (z ^ lsr(z, 30)) * m1
+        z = (z ^ lsr(z, 27)) * m2
+        out[a:b] = z ^ lsr(z, 31)
+    return out
+
+
 def unit_f64(seed: int, count: int, start: int = 0) -> np.ndarray:
     """Uniform doubles in [0, 1) from the top 53 bits of each draw."""
     return (splitmix64(seed, count, start) >> _U64(11)).astype(np.float64) * (1.0 / (1 << 53))

@@ -50,3 +50,10 @@ def test_join_shapes():
 def test_log_uniform_range():
     ns, ks = datagen.batched_topk_queries(4096)
     assert ns.min() >= 1000 and ns.max() < 4e6 and ks.min() >= 1 and ks.max() <= 1000
+
+
+def test_torch_stream_equals_numpy_stream():
+    torch = __import__("pytest").importorskip("torch")
+    a = datagen.splitmix64(stream_seed := datagen.stream_seed(3, 0), 5000, start=17)
+    b = datagen.splitmix64_torch(stream_seed, 5000, start=17, device="cpu", chunk=777).numpy().view(np.uint64)
+    assert np.array_equal(a, b)
