@@ -309,6 +309,77 @@ olap_status olap_gate_estimate(const olap_gate_model* model, const olap_gate_que
                                olap_gate_decision* out);
 
 /* ------------------------------------------------------------------------
+ * Serving loop (gated against always-on offload, Sec. II-B and Sec. IV).
+ *
+ * Requests arrive at given times (or all at once in closed loop).  Each is
+ * decided on arrival -- by the gate, or always GPU, or always host -- and then
+ * queued.  GPU requests are admitted first-come first-served into one of
+ * gpu_slots slots, each with its own context (stream, device scratch and
+ * pinned double buffers), as soon as a slot is free and the request's device
+ * memory fits the budget next to the requests already running (a request is
+ * always admitted when nothing else runs).  Requests in different slots
+ * overlap on the device: this is continuous batching, not a queue in front of
+ * one stream.  Host requests run on cpu_workers threads through the caller's
+ * engine callback: the library has no CPU implementation of the primitives.
+ * Latency = completion time - arrival time.  Keys and outputs are host
+ * memory (key-only H2D through pinned staging, results D2H).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int op;                          /* olap_op */
+    int key_type;                    /* Top-K: olap_key_type */
+    int order;                       /* Top-K: olap_order */
+    int table_id;                    /* probe: index of the table in the caller's engine */
+    const void* keys;                /* host */
+    const uint32_t* rowids;          /* host or NULL */
+    uint64_t n;
+    uint64_t k;                      /* Top-K */
+    const olap_join_table* table;    /* probe (device table) */
+    double expected_pairs;           /* probe: the caller's estimate, for the gate */
+    double arrival_ms;               /* from the start of the run */
+    void* out_keys;                  /* Top-K host outputs (>= min(k, n)) */
+    uint32_t* out_rowids;
+    olap_pair* out_pairs;            /* probe host output */
+    uint64_t capacity;
+    /* filled in by olap_serve */
+    uint64_t out_count;
+    int status;                      /* olap_status of the request */
+    int on_gpu;
+    double start_ms, done_ms;
+} olap_serve_request;
+
+/* The caller's host engine: run `req` on the CPU, write its outputs and
+ * out_count; return an olap_status. */
+typedef int (*olap_host_engine_fn)(void* user, olap_serve_request* req);
+
+typedef enum { OLAP_SERVE_GATED = 0, OLAP_SERVE_ALWAYS_GPU = 1, OLAP_SERVE_ALWAYS_HOST = 2 } olap_serve_policy;
+
+typedef struct {
+    int policy;                      /* olap_serve_policy */
+    int gpu_slots;                   /* concurrent GPU requests (default 4) */
+    int cpu_workers;                 /* host engine threads (default 8) */
+    uint64_t mem_budget_bytes;       /* device memory for in-flight requests (0 = unlimited) */
+    const olap_gate_model* topk_model;
+    const olap_gate_model* probe_model;
+    olap_host_engine_fn host_engine;
+    void* host_user;
+    int closed_loop;                 /* 1: ignore arrival times, all arrive at 0 */
+    const olap_opts* ctx_opts;       /* options of the slot contexts (device, staging) */
+} olap_serve_opts;
+
+typedef struct {
+    double wall_ms;
+    double throughput_rps;
+    double p50_ms, p95_ms, p99_ms, mean_ms, max_ms;
+    uint64_t n_gpu, n_host, n_failed;
+    double offload_fraction;
+    uint64_t peak_reserved_bytes;
+} olap_serve_stats;
+
+/* Serve n requests (sorted by arrival or not; served in arrival order) and
+ * report latency percentiles and throughput.  Blocking. */
+olap_status olap_serve(olap_serve_request* reqs, uint64_t n, const olap_serve_opts* opts, olap_serve_stats* out);
+
+/* ------------------------------------------------------------------------
  * Top-K that allocates nothing (no counterpart in the paper: a deployment
  * entry point for callers that cannot let a library allocate GPU memory --
  * engines whose device memory is wholly reserved by their own pool, plug-in

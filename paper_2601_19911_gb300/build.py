@@ -16,6 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libolap.so")
+HOST_LIB = os.path.join(OUT_DIR, "libolap_host.so")
+HOST_SRC = os.path.join(HERE, "host", "host_engine.cpp")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -69,7 +71,23 @@ def build(force: bool = False, verbose: bool = False) -> str:
         tmp = LIB + f".{os.getpid()}.tmp"
         run([cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"])
         os.replace(tmp, LIB)
+    build_host(force)
     return LIB
+
+
+def build_host(force: bool = False) -> str:
+    """The serving harness's host engine (plain C++, no CUDA): a library of
+    its own, so the GPU library carries no CPU path."""
+    hdr = os.path.join(ROOT, "include", "olap.h")
+    if force or not os.path.exists(HOST_LIB) or os.path.getmtime(HOST_LIB) < max(
+            os.path.getmtime(HOST_SRC), os.path.getmtime(hdr)):
+        tmp = HOST_LIB + f".{os.getpid()}.tmp"
+        r = subprocess.run(["g++", "-O3", "-std=c++17", "-shared", "-fPIC", "-pthread", "-I",
+                            os.path.join(ROOT, "include"), "-o", tmp, HOST_SRC], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"host engine build failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, HOST_LIB)
+    return HOST_LIB
 
 
 if __name__ == "__main__":

@@ -1,0 +1,208 @@
+// Host engine used by the serving harness for the requests the gate keeps on
+// the CPU: the "existing execution engine" of the paper's hybrid design
+// (Sec. II-A) that the GPU augments.  It is a separate library on purpose:
+// the GPU library has no CPU implementation of the primitives.
+//
+//   Top-K: each thread keeps a bounded max-heap of the K smallest composites
+//   (order-preserving key word, row-id) of its chunk; the heaps are merged and
+//   sorted.  Same ordering as the GPU: key in the requested order, row-id
+//   ascending on ties, float32 by IEEE totalOrder.
+//   Probe: per table, rows sorted by key plus an open-addressing index from
+//   key to its run; threads probe chunks and the pairs are concatenated.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <queue>
+#include <thread>
+#include <vector>
+
+#include "olap.h"
+
+namespace {
+
+struct Comp {
+    uint64_t r;
+    uint32_t rid;
+    bool operator<(const Comp& o) const { return r < o.r || (r == o.r && rid < o.rid); }
+};
+
+inline uint64_t word_i64(uint64_t bits, bool desc) {
+    const uint64_t u = bits ^ 0x8000000000000000ull;
+    return desc ? ~u : u;
+}
+inline uint64_t word_f32(uint32_t bits, bool desc) {
+    uint32_t u = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+    if (desc) u = ~u;
+    return u;
+}
+inline uint64_t unword_i64(uint64_t r, bool desc) { return (desc ? ~r : r) ^ 0x8000000000000000ull; }
+inline uint32_t unword_f32(uint64_t r, bool desc) {
+    uint32_t u = static_cast<uint32_t>(r);
+    if (desc) u = ~u;
+    return (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+}
+
+struct Table {
+    std::vector<int64_t> keys;      // sorted
+    std::vector<uint32_t> rids;     // in key order
+    std::vector<uint64_t> slot_key; // index: key -> first position, count
+    std::vector<uint32_t> slot_pos, slot_cnt;
+    uint64_t mask = 0;
+};
+
+inline uint64_t mix(uint64_t h) {
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    return h;
+}
+
+struct Engine {
+    int threads = 8;
+    std::vector<Table> tables;
+};
+
+template <typename F>
+void parallel(int t, uint64_t n, F&& f) {
+    if (t <= 1 || n < 65536) {
+        f(0, 0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    const uint64_t per = (n + t - 1) / t;
+    for (int i = 0; i < t; ++i) {
+        const uint64_t a = std::min(n, i * per), b = std::min(n, a + per);
+        th.emplace_back([&, i, a, b] { f(i, a, b); });
+    }
+    for (auto& x : th) x.join();
+}
+
+int run_topk(Engine* E, olap_serve_request* r) {
+    const bool f32 = r->key_type == OLAP_KEY_F32, desc = r->order == OLAP_DESC;
+    const uint64_t n = r->n, kk = std::min(r->k, n);
+    if (kk == 0) {
+        r->out_count = 0;
+        return OLAP_OK;
+    }
+    const int t = n < 65536 ? 1 : E->threads;
+    std::vector<std::vector<Comp>> part(t);
+    parallel(t, n, [&](int ti, uint64_t a, uint64_t b) {
+        std::priority_queue<Comp> heap;
+        for (uint64_t i = a; i < b; ++i) {
+            Comp c;
+            c.r = f32 ? word_f32(static_cast<const uint32_t*>(r->keys)[i], desc)
+                      : word_i64(static_cast<const uint64_t*>(r->keys)[i], desc);
+            c.rid = r->rowids ? r->rowids[i] : static_cast<uint32_t>(i);
+            if (heap.size() < kk) heap.push(c);
+            else if (c < heap.top()) {
+                heap.pop();
+                heap.push(c);
+            }
+        }
+        auto& v = part[ti];
+        v.reserve(heap.size());
+        while (!heap.empty()) {
+            v.push_back(heap.top());
+            heap.pop();
+        }
+    });
+    std::vector<Comp> all;
+    for (auto& v : part) all.insert(all.end(), v.begin(), v.end());
+    std::partial_sort(all.begin(), all.begin() + static_cast<long>(kk), all.end());
+    for (uint64_t i = 0; i < kk; ++i) {
+        if (f32) static_cast<uint32_t*>(r->out_keys)[i] = unword_f32(all[i].r, desc);
+        else static_cast<uint64_t*>(r->out_keys)[i] = unword_i64(all[i].r, desc);
+        r->out_rowids[i] = all[i].rid;
+    }
+    r->out_count = kk;
+    return OLAP_OK;
+}
+
+int run_probe(Engine* E, olap_serve_request* r) {
+    if (r->table_id < 0 || r->table_id >= static_cast<int>(E->tables.size())) return OLAP_E_INVALID;
+    const Table& T = E->tables[r->table_id];
+    const int64_t* keys = static_cast<const int64_t*>(r->keys);
+    const int t = r->n < 65536 ? 1 : E->threads;
+    std::vector<std::vector<olap_pair>> part(t);
+    parallel(t, r->n, [&](int ti, uint64_t a, uint64_t b) {
+        auto& v = part[ti];
+        for (uint64_t i = a; i < b; ++i) {
+            const uint64_t key = static_cast<uint64_t>(keys[i]);
+            uint64_t s = mix(key) & T.mask;
+            while (T.slot_cnt[s]) {
+                if (T.slot_key[s] == key) {
+                    const uint32_t prid = r->rowids ? r->rowids[i] : static_cast<uint32_t>(i);
+                    for (uint32_t j = 0; j < T.slot_cnt[s]; ++j) v.push_back(olap_pair{prid, T.rids[T.slot_pos[s] + j]});
+                    break;
+                }
+                s = (s + 1) & T.mask;
+            }
+        }
+    });
+    uint64_t total = 0;
+    for (auto& v : part) total += v.size();
+    r->out_count = total;
+    if (total > r->capacity) return OLAP_E_OVERFLOW;
+    uint64_t off = 0;
+    for (auto& v : part) {
+        if (!v.empty()) std::memcpy(r->out_pairs + off, v.data(), v.size() * sizeof(olap_pair));
+        off += v.size();
+    }
+    return OLAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void* olap_host_engine_create(int threads) {
+    Engine* e = new Engine();
+    e->threads = threads > 0 ? threads : 8;
+    return e;
+}
+
+int olap_host_engine_add_table(void* eng, const int64_t* keys, const uint32_t* rowids, uint64_t n) {
+    Engine* E = static_cast<Engine*>(eng);
+    Table T;
+    std::vector<uint64_t> idx(n);
+    for (uint64_t i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](uint64_t a, uint64_t b) { return keys[a] < keys[b]; });
+    T.keys.resize(n);
+    T.rids.resize(n);
+    for (uint64_t i = 0; i < n; ++i) {
+        T.keys[i] = keys[idx[i]];
+        T.rids[i] = rowids ? rowids[idx[i]] : static_cast<uint32_t>(idx[i]);
+    }
+    uint64_t cap = 1;
+    while (cap < 2 * n + 2) cap <<= 1;
+    T.mask = cap - 1;
+    T.slot_key.assign(cap, 0);
+    T.slot_pos.assign(cap, 0);
+    T.slot_cnt.assign(cap, 0);
+    for (uint64_t i = 0; i < n;) {
+        uint64_t j = i;
+        while (j < n && T.keys[j] == T.keys[i]) ++j;
+        const uint64_t key = static_cast<uint64_t>(T.keys[i]);
+        uint64_t s = mix(key) & T.mask;
+        while (T.slot_cnt[s]) s = (s + 1) & T.mask;
+        T.slot_key[s] = key;
+        T.slot_pos[s] = static_cast<uint32_t>(i);
+        T.slot_cnt[s] = static_cast<uint32_t>(j - i);
+        i = j;
+    }
+    E->tables.push_back(std::move(T));
+    return static_cast<int>(E->tables.size()) - 1;
+}
+
+int olap_host_engine_run(void* eng, olap_serve_request* r) {
+    Engine* E = static_cast<Engine*>(eng);
+    if (r->op == OLAP_OP_TOPK) return run_topk(E, r);
+    if (r->op == OLAP_OP_PROBE) return run_probe(E, r);
+    return OLAP_E_INVALID;
+}
+
+void olap_host_engine_free(void* eng) { delete static_cast<Engine*>(eng); }
+
+}  // extern "C"

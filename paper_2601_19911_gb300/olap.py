@@ -31,7 +31,9 @@ EXPORTS = [
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
     "olap_batch_create", "olap_batch_run", "olap_batch_run_per_query", "olap_batch_errors", "olap_batch_free",
+    "olap_serve",
 ]
+SERVE_GATED, SERVE_ALWAYS_GPU, SERVE_ALWAYS_HOST = 0, 1, 2
 OP_TOPK, OP_PROBE = 0, 1
 CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
@@ -94,6 +96,32 @@ class olap_batch_item(ctypes.Structure):
                 ("k", ctypes.c_uint64), ("out_keys", ctypes.c_void_p), ("out_rowids", ctypes.c_void_p),
                 ("table", ctypes.c_void_p), ("out_pairs", ctypes.c_void_p), ("capacity", ctypes.c_uint64),
                 ("count", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+class olap_serve_request(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("key_type", ctypes.c_int), ("order", ctypes.c_int), ("table_id", ctypes.c_int),
+                ("keys", ctypes.c_void_p), ("rowids", ctypes.c_void_p), ("n", ctypes.c_uint64), ("k", ctypes.c_uint64),
+                ("table", ctypes.c_void_p), ("expected_pairs", ctypes.c_double), ("arrival_ms", ctypes.c_double),
+                ("out_keys", ctypes.c_void_p), ("out_rowids", ctypes.c_void_p), ("out_pairs", ctypes.c_void_p),
+                ("capacity", ctypes.c_uint64), ("out_count", ctypes.c_uint64), ("status", ctypes.c_int),
+                ("on_gpu", ctypes.c_int), ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
+HOST_ENGINE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(olap_serve_request))
+
+
+class olap_serve_opts(ctypes.Structure):
+    _fields_ = [("policy", ctypes.c_int), ("gpu_slots", ctypes.c_int), ("cpu_workers", ctypes.c_int),
+                ("mem_budget_bytes", ctypes.c_uint64), ("topk_model", ctypes.c_void_p),
+                ("probe_model", ctypes.c_void_p), ("host_engine", ctypes.c_void_p), ("host_user", ctypes.c_void_p),
+                ("closed_loop", ctypes.c_int), ("ctx_opts", ctypes.c_void_p)]
+
+
+class olap_serve_stats(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_double) for nm in ("wall_ms", "throughput_rps", "p50_ms", "p95_ms", "p99_ms",
+                                                  "mean_ms", "max_ms")] + \
+        [("n_gpu", ctypes.c_uint64), ("n_host", ctypes.c_uint64), ("n_failed", ctypes.c_uint64),
+         ("offload_fraction", ctypes.c_double), ("peak_reserved_bytes", ctypes.c_uint64)]
 
 
 class olap_topk_info(ctypes.Structure):
@@ -166,6 +194,9 @@ def load(path: str | None = None):
         lib.olap_batch_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         lib.olap_batch_free.restype = None
         lib.olap_batch_free.argtypes = [vp]
+        lib.olap_serve.restype = i32
+        lib.olap_serve.argtypes = [ctypes.POINTER(olap_serve_request), u64, ctypes.POINTER(olap_serve_opts),
+                                   ctypes.POINTER(olap_serve_stats)]
         lib.olap_topk_noalloc.restype = i32
         lib.olap_topk_noalloc.argtypes = [vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         _bind_more(lib)
@@ -487,3 +518,68 @@ def gate_estimate(model: olap_gate_model, op: int, n: int, k_or_m: float, tx_byt
     if st != OK:
         raise OlapError(st, "olap_gate_estimate rejected the query")
     return d
+
+
+# ---------------------------------------------------------------------------
+# Serving loop and the host engine of the serving harness
+# ---------------------------------------------------------------------------
+
+class HostEngine:
+    """The serving harness's CPU engine (libolap_host.so): the existing
+    engine the GPU augments, used for requests the gate keeps on the host."""
+
+    def __init__(self, threads: int = 8):
+        p = _build.HOST_LIB
+        if not os.path.exists(p):
+            raise ImportError(f"host engine not built: {p} is missing")
+        self.lib = ctypes.CDLL(p)
+        self.lib.olap_host_engine_create.restype = ctypes.c_void_p
+        self.lib.olap_host_engine_create.argtypes = [ctypes.c_int]
+        self.lib.olap_host_engine_add_table.restype = ctypes.c_int
+        self.lib.olap_host_engine_add_table.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                        ctypes.c_uint64]
+        self.lib.olap_host_engine_free.argtypes = [ctypes.c_void_p]
+        self.h = self.lib.olap_host_engine_create(threads)
+        self._keep = []
+
+    def add_table(self, keys: np.ndarray, rowids: np.ndarray | None = None) -> int:
+        keys = np.ascontiguousarray(keys, dtype=np.int64)
+        return self.lib.olap_host_engine_add_table(self.h, keys.ctypes.data, ptr(rowids), keys.shape[0])
+
+    @property
+    def fn(self) -> int:
+        return ctypes.cast(self.lib.olap_host_engine_run, ctypes.c_void_p).value
+
+    def run(self, req: olap_serve_request) -> int:
+        f = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(olap_serve_request))(self.fn)
+        return f(self.h, ctypes.byref(req))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.olap_host_engine_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def serve(requests, policy: int, topk_model=None, probe_model=None, host: HostEngine | None = None,
+          gpu_slots: int = 4, cpu_workers: int = 8, mem_budget_bytes: int = 0, closed_loop: bool = False,
+          device: int = 0) -> olap_serve_stats:
+    """olap_serve over a ctypes array (or list) of olap_serve_request."""
+    lib = load()
+    arr = requests if isinstance(requests, ctypes.Array) else (olap_serve_request * len(requests))(*requests)
+    co = olap_opts(device, None, 0, 0.0, 0, 0.0, 0, 0, 0, 0, 0)
+    o = olap_serve_opts(policy, gpu_slots, cpu_workers, mem_budget_bytes,
+                        ctypes.addressof(topk_model) if topk_model is not None else None,
+                        ctypes.addressof(probe_model) if probe_model is not None else None,
+                        host.fn if host else None, host.h if host else None, 1 if closed_loop else 0,
+                        ctypes.addressof(co))
+    st = olap_serve_stats()
+    rc = lib.olap_serve(arr, len(arr), ctypes.byref(o), ctypes.byref(st))
+    if rc != OK:
+        raise OlapError(rc, "olap_serve failed")
+    return st

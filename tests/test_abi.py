@@ -48,3 +48,31 @@ def test_null_context_is_rejected(lib):
     assert lib.olap_topk(None, None, 0, None, 0, 0, 0, 0, None, None, 0, ctypes.byref(got)) == olap.E_INVALID
     assert lib.olap_ctx_sync(None) == olap.E_INVALID
     assert lib.olap_last_error(None) == b"no context"
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror of an include/olap.h struct has the C layout
+    (size and field offsets, from a C program compiled against the header)."""
+    import subprocess
+    structs = {
+        "olap_opts": olap.olap_opts, "olap_topk_info": olap.olap_topk_info,
+        "olap_gate_samples": olap.olap_gate_samples, "olap_gate_model": olap.olap_gate_model,
+        "olap_gate_query": olap.olap_gate_query, "olap_gate_decision": olap.olap_gate_decision,
+        "olap_batch_item": olap.olap_batch_item, "olap_serve_request": olap.olap_serve_request,
+        "olap_serve_opts": olap.olap_serve_opts, "olap_serve_stats": olap.olap_serve_stats,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "olap.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert int(got[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])
