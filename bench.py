@@ -321,6 +321,151 @@ def batched_leg(args, ctx, torch):
             "gpu_launches_graph": 2, "clocks": clk.summary()}
 
 
+def _median_ms(fn, reps=3):
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return float(np.median(ts))
+
+
+def serving_leg(args, ctx, torch):
+    """The serving stream: Poisson arrivals, half Top-K (N ~ logU[1e3, 1e8),
+    K ~ logU[1, 1e5) clipped to N), half probes (n ~ logU[1e3, 1e8)) against
+    8 resident tables of logU[1M, 16M) unique keys with hit rate 10% or 90%,
+    keys sliced at seeded offsets from host column arenas and staged through
+    pinned double buffers.  The gate is calibrated from measured host-engine,
+    transfer, kernel and result times; the arrival rate is 0.7 x the
+    always-on closed-loop throughput; gated and always-on serve the same
+    trace."""
+    from paper_2601_19911_gb300 import datagen, olap
+    A = args.serve_arena
+    rng = np.random.default_rng(4)
+    topk_arena = datagen.topk_keys(A, "uniform", "i64", seed=4)
+    D = datagen.join_build(1 << 24, "unique", seed=4)
+    host = olap.HostEngine(threads=args.serve_cpu_workers)
+    sizes = np.sort(datagen.log_uniform(1 << 20, 1 << 24, datagen.stream_seed(4, 12), 8))
+    tables, tbytes = [], 0
+    for t in range(8):
+        keys_t = D.keys[: int(sizes[t])]
+        tables.append(ctx.join_build(keys_t))
+        host.add_table(keys_t)
+        tbytes += int(sizes[t]) * 32 // 1
+    common = datagen.JoinBuild(D.keys[: 1 << 20], D.keys[: 1 << 20], np.ones(1 << 20, dtype=np.int64))
+    arenas = []
+    for j, hit in enumerate((0.1, 0.9)):
+        p = datagen.join_probe(A, common, hit, "uniform", seed=40 + j)
+        arenas.append((hit, p.keys, np.concatenate([[0], np.cumsum(p.hit)])))
+
+    def make_requests(count, seed):
+        r_ = np.random.default_rng(seed)
+        reqs, keep = [], []
+        for i in range(count):
+            n = int(min(A, np.floor(1e3 * (1e8 / 1e3) ** r_.random())))
+            off = int(r_.integers(0, A - n + 1))
+            if i % 2 == 0:
+                k = int(min(n, np.floor(1e5 ** r_.random())))
+                ok = np.empty(max(1, k), dtype=np.int64)
+                orow = np.empty(max(1, k), dtype=np.uint32)
+                keys = topk_arena[off:off + n]
+                keep.append((ok, orow))
+                reqs.append(olap.olap_serve_request(olap.OP_TOPK, olap.KEY_I64, olap.DESC, 0, keys.ctypes.data, None,
+                                                    n, k, None, 0.0, 0.0, ok.ctypes.data, orow.ctypes.data, None, 0))
+            else:
+                t = int(r_.integers(0, 8))
+                hit, pk, cum = arenas[int(r_.integers(0, 2))]
+                need = int(cum[off + n] - cum[off])
+                out = np.empty((need + 64, 2), dtype=np.uint32)
+                keep.append((out,))
+                reqs.append(olap.olap_serve_request(olap.OP_PROBE, olap.KEY_I64, 0, t, pk[off:off + n].ctypes.data,
+                                                    None, n, 0, tables[t].h.value, float(need), 0.0, None, None,
+                                                    out.ctypes.data, need + 64))
+        return (olap.olap_serve_request * count)(*reqs), keep
+
+    # -- gate calibration from measured times (one request at a time) ----------
+    cal_n = np.unique(np.floor(np.logspace(3, 8, args.serve_cal_points)).astype(np.int64))
+    cal_n = cal_n[cal_n <= A]
+    samples = {olap.OP_TOPK: [], olap.OP_PROBE: []}
+    kcal = 100
+    dev_keys = torch.from_numpy(topk_arena).cuda()
+    for n in cal_n:
+        n = int(n)
+        keys = topk_arena[:n]
+        ok = np.empty(kcal, dtype=np.int64)
+        orow = np.empty(kcal, dtype=np.uint32)
+        req = olap.olap_serve_request(olap.OP_TOPK, olap.KEY_I64, olap.DESC, 0, keys.ctypes.data, None, n, kcal,
+                                      None, 0.0, 0.0, ok.ctypes.data, orow.ctypes.data, None, 0)
+        t_cpu = _median_ms(lambda: host.run(req))
+        dok = torch.empty(kcal, dtype=torch.int64, device="cuda")
+        dor = torch.empty(kcal, dtype=torch.int32, device="cuda")
+        t_in = _median_ms(lambda: ctx.topk(keys, kcal, olap.DESC, out_keys=dok, out_rowids=dor))
+        t_all = _median_ms(lambda: ctx.topk(keys, kcal, olap.DESC))
+        def kern():
+            ctx.topk_async(dev_keys[:n], kcal, olap.DESC, dok, dor)
+            ctx.sync()
+        t_ker = _median_ms(kern)
+        samples[olap.OP_TOPK].append((n, kcal, 8.0 * n, min(kcal, n), t_cpu, max(t_in - t_ker, 0.0), t_ker,
+                                      max(t_all - t_in, 0.0)))
+        hit, pk, cum = arenas[1]
+        pkeys = pk[:n]
+        need = int(cum[n])
+        out = np.empty((need + 64, 2), dtype=np.uint32)
+        preq = olap.olap_serve_request(olap.OP_PROBE, olap.KEY_I64, 0, 0, pkeys.ctypes.data, None, n, 0,
+                                       tables[0].h.value, float(need), 0.0, None, None, out.ctypes.data, need + 64)
+        t_cpu = _median_ms(lambda: host.run(preq))
+        dpk = dev_keys  # reuse the device buffer for the probe keys
+        dpk[:n].copy_(torch.from_numpy(pkeys))
+        dout = torch.empty((need + 64, 2), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        t_in = _median_ms(lambda: ctx.join_probe(tables[0], pkeys, out=dout))
+        t_all = _median_ms(lambda: ctx.join_probe(tables[0], pkeys, out=out))
+        def pkern():
+            ctx.join_probe_async(tables[0], dpk[:n], dout, need + 64, cnt)
+            ctx.sync()
+        t_ker = _median_ms(pkern)
+        samples[olap.OP_PROBE].append((n, 1.0 + need / n, 8.0 * n, need, t_cpu, max(t_in - t_ker, 0.0), t_ker,
+                                       max(t_all - t_in, 0.0)))
+        dev_keys[:n].copy_(torch.from_numpy(keys))
+    del dev_keys
+    torch.cuda.empty_cache()
+    models = {}
+    for op, rows in samples.items():
+        cols = list(zip(*rows))
+        models[op] = olap.gate_calibrate(op, *cols, margin_ms=args.serve_margin, weighting=olap.FIT_RELATIVE)
+    # -- arrival rate from the closed-loop always-on throughput -----------------
+    reqs, keep = make_requests(args.serve_requests, seed=4)
+    budget = max(1, args.serve_budget_gb * (1 << 30) - tbytes)
+    closed = olap.serve(reqs, olap.SERVE_ALWAYS_GPU, gpu_slots=args.serve_slots, mem_budget_bytes=budget,
+                        closed_loop=True)
+    lam = 0.7 * closed.throughput_rps
+    arrivals = datagen.poisson_arrivals(args.serve_requests, lam, seed=4) * 1e3
+    out = {}
+    for name, policy in (("always_on", olap.SERVE_ALWAYS_GPU), ("gated", olap.SERVE_GATED)):
+        for i in range(args.serve_requests):
+            reqs[i].arrival_ms = float(arrivals[i])
+        st = olap.serve(reqs, policy, models[olap.OP_TOPK], models[olap.OP_PROBE], host,
+                        gpu_slots=args.serve_slots, cpu_workers=args.serve_cpu_workers, mem_budget_bytes=budget)
+        out[name] = {"p50_ms": st.p50_ms, "p95_ms": st.p95_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
+                     "max_ms": st.max_ms, "throughput_rps": st.throughput_rps, "wall_ms": st.wall_ms,
+                     "offload_fraction": st.offload_fraction, "n_gpu": st.n_gpu, "n_host": st.n_host,
+                     "failed": st.n_failed, "peak_reserved_gb": st.peak_reserved_bytes / 2**30}
+    def mdict(m):
+        return {"cpu_form": ["n_log2_n", "n_k", "n_m"][m.cpu_form], "a": m.a, "b": m.b, "c_ms_per_byte": m.c,
+                "d": m.d, "e": m.e, "f": m.f, "g": m.g, "h": m.h, "margin_ms": m.margin_ms}
+    nstar = olap.gate_estimate(models[olap.OP_TOPK], olap.OP_TOPK, 1 << 20, 100, 8.0 * (1 << 20), 100, 8.0).n_star
+    for t in tables:
+        t.free()
+    host.close()
+    return {"metric": "gated vs always-on P99 latency (ms)", "value": out["gated"]["p99_ms"], "unit": "ms",
+            "higher_is_better": False, "requests": args.serve_requests, "arrival_rate_rps": lam,
+            "closed_loop_always_on_rps": closed.throughput_rps, "gpu_slots": args.serve_slots,
+            "budget_gb": args.serve_budget_gb, "arena_keys": A, "tables": [int(x) for x in sizes],
+            "gated": out["gated"], "always_on": out["always_on"],
+            "gate": {"topk": mdict(models[olap.OP_TOPK]), "probe": mdict(models[olap.OP_PROBE]),
+                     "topk_n_star_k100": int(nstar), "calibration_points": len(cal_n)}}
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
@@ -415,6 +560,9 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["batched"] = batched_leg(args, ctx, torch)
         line["gpu_launches"] += 2 * args.batch_reps
+    if "serving" in workloads:
+        torch.cuda.empty_cache()
+        line["serving"] = serving_leg(args, ctx, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, k)
     if rank == 0:
@@ -440,8 +588,9 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,join,batched",
-                    help="comma list: topk (the headline value), join (probe sub-object), batched (executor)")
+    ap.add_argument("--workload", default="topk,join,batched,serving",
+                    help="comma list: topk (the headline value), join (probe sub-object), batched (executor), "
+                         "serving (gated vs always-on stream)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",
                     help="build multiplicity (unique|mult14), probe distribution (uniform|zipf), hit rate")
     ap.add_argument("--join-log2b", type=int, default=24)
@@ -451,6 +600,13 @@ def main():
     ap.add_argument("--batch-topk", type=int, default=4096)
     ap.add_argument("--batch-probe", type=int, default=1024)
     ap.add_argument("--batch-reps", type=int, default=10)
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-arena", type=int, default=100_000_000)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-cpu-workers", type=int, default=12)
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--serve-margin", type=float, default=0.0)
+    ap.add_argument("--serve-cal-points", type=int, default=12)
     ap.add_argument("--tile", type=int, default=0, help="bulk-copy bytes (0 = library default)")
     ap.add_argument("--stages", type=int, default=0, help="copies in flight per CTA (0 = default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM (0 = default)")

@@ -250,8 +250,10 @@ void olap_batch_free(olap_batch* batch);
  *            C_ker = e * N + f, C_post = g * rows returned + h
  *            (result return and late materialization)
  *   offload  <=>  C_cpu - C_gpu > margin  (strict)
- * Every fit is ordinary least squares in the centred closed form of the 2x2
- * normal equations.  N* is the smallest integer N in [1, 2^34] where
+ * Every fit is least squares in the centred closed form of the 2x2 normal
+ * equations, ordinary or weighted by 1/y^2 (relative error; the measured
+ * times span decades of N and unweighted the largest sizes decide the small-N
+ * costs the gate exists for).  N* is the smallest integer N in [1, 2^34] where
  * C_cpu(N) - C_gpu(N) > margin for the query's K (or M), with transfer bytes
  * and returned rows scaled with N as the query says; 1 if that already holds
  * at N = 1 and 0 ("never") if it fails at 2^34.  Pure host arithmetic: these
@@ -259,9 +261,11 @@ void olap_batch_free(olap_batch* batch);
  * ------------------------------------------------------------------------ */
 typedef enum { OLAP_OP_TOPK = 0, OLAP_OP_PROBE = 1 } olap_op;
 typedef enum { OLAP_CPU_NLOGN = 0, OLAP_CPU_NK = 1, OLAP_CPU_NM = 2 } olap_cpu_form;
+typedef enum { OLAP_FIT_ORDINARY = 0, OLAP_FIT_RELATIVE = 1 } olap_fit;
 
 typedef struct {
     olap_op op;
+    int weighting;                /* olap_fit */
     uint64_t count;               /* number of samples (>= 2) */
     const double* n;              /* input rows N */
     const double* k_or_m;         /* Top-K: K; probe: M */

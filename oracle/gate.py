@@ -15,8 +15,11 @@ What the paper fixes:
   * the break-even N* solves T_cpu(N*) = T_tx(N*) + T_gpu(N*) (Sec. V-D).
 
 Readings where it is open (kept identical in the library's contract):
-  * fits are ordinary least squares y = slope*x + intercept on the given
-    points, in the centred closed form of the normal equations;
+  * fits are least squares y = slope*x + intercept on the given points, in
+    the centred closed form of the normal equations, either ordinary or
+    weighted by 1/y^2 (relative error: measured times span decades of N, and
+    unweighted the largest sizes decide the small-N costs the gate exists
+    for);
   * Top-K fits both CPU forms, x = N*log2(N) and x = N*K, and keeps the one
     with the smaller residual sum of squares (N*log2 N on a tie);
   * probe CPU cost uses x = N*M, M the expected candidates per probe;
@@ -38,23 +41,40 @@ CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
 N_STAR_HI = 1 << 34
 
 
-def ols(x, y):
-    """Least-squares slope and intercept of y = slope*x + intercept."""
+ORDINARY, RELATIVE = 0, 1
+
+
+def weights(y, weighting):
+    """Least-squares weights: 1 (ordinary) or 1 / y^2 (relative error; a
+    non-positive y gets the weight of the smallest positive y)."""
+    y = np.asarray(y, dtype=np.float64)
+    if weighting == ORDINARY:
+        return np.ones_like(y)
+    pos = y[y > 0.0]
+    floor = pos.min() if pos.shape[0] else 1.0
+    return 1.0 / np.square(np.where(y > 0.0, y, floor))
+
+
+def ols(x, y, weighting=ORDINARY):
+    """(Weighted) least-squares slope and intercept of y = slope*x + intercept,
+    from the centred normal equations."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
-    xm = x.mean()
-    ym = y.mean()
-    sxx = float(np.sum((x - xm) * (x - xm)))
-    sxy = float(np.sum((x - xm) * (y - ym)))
+    w = weights(y, weighting)
+    sw = w.sum()
+    xm = float(np.sum(w * x) / sw)
+    ym = float(np.sum(w * y) / sw)
+    sxx = float(np.sum(w * (x - xm) * (x - xm)))
+    sxy = float(np.sum(w * (x - xm) * (y - ym)))
     slope = sxy / sxx if sxx > 0.0 else 0.0
     return slope, float(ym - slope * xm)
 
 
-def rss(x, y, slope, intercept):
+def rss(x, y, slope, intercept, weighting=ORDINARY):
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     r = y - (slope * x + intercept)
-    return float(np.sum(r * r))
+    return float(np.sum(weights(y, weighting) * r * r))
 
 
 def cpu_x(form, n, k_or_m):
@@ -72,20 +92,22 @@ class Model:
         self.margin_ms = margin_ms
 
 
-def calibrate(op, n, k_or_m, tx_bytes, out_rows, t_cpu, t_tx, t_ker, t_post, margin_ms=0.0):
+def calibrate(op, n, k_or_m, tx_bytes, out_rows, t_cpu, t_tx, t_ker, t_post, margin_ms=0.0,
+              weighting=ORDINARY):
     """Fit every cost term from measured samples (all times in ms)."""
+    wt = weighting
     if op == TOPK:
         xs = {f: [cpu_x(f, ni, ki) for ni, ki in zip(n, k_or_m)] for f in (CPU_NLOGN, CPU_NK)}
-        fits = {f: ols(xs[f], t_cpu) for f in xs}
-        res = {f: rss(xs[f], t_cpu, *fits[f]) for f in xs}
+        fits = {f: ols(xs[f], t_cpu, wt) for f in xs}
+        res = {f: rss(xs[f], t_cpu, *fits[f], wt) for f in xs}
         form = CPU_NLOGN if res[CPU_NLOGN] <= res[CPU_NK] else CPU_NK
     else:
         form = CPU_NM
-        fits = {form: ols([cpu_x(form, ni, mi) for ni, mi in zip(n, k_or_m)], t_cpu)}
+        fits = {form: ols([cpu_x(form, ni, mi) for ni, mi in zip(n, k_or_m)], t_cpu, wt)}
     a, b = fits[form]
-    c, d = ols(tx_bytes, t_tx)
-    e, f = ols(n, t_ker)
-    g, h = ols(out_rows, t_post)
+    c, d = ols(tx_bytes, t_tx, wt)
+    e, f = ols(n, t_ker, wt)
+    g, h = ols(out_rows, t_post, wt)
     return Model(op, form, a, b, c, d, e, f, g, h, margin_ms)
 
 

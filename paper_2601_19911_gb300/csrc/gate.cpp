@@ -9,29 +9,53 @@ namespace {
 
 constexpr uint64_t N_STAR_HI = 1ull << 34;
 
-// Ordinary least squares y = slope * x + intercept, centred normal equations.
-void ols(const double* x, const double* y, uint64_t n, double* slope, double* intercept) {
-    double xm = 0.0, ym = 0.0;
-    for (uint64_t i = 0; i < n; ++i) {
-        xm += x[i];
-        ym += y[i];
+// Weight of a sample: 1 (ordinary) or 1 / y^2 (relative error); a
+// non-positive y takes the weight of the smallest positive y.
+struct Weights {
+    int mode;
+    double floor;
+    double operator()(double y) const {
+        if (mode == OLAP_FIT_ORDINARY) return 1.0;
+        const double v = y > 0.0 ? y : floor;
+        return 1.0 / (v * v);
     }
-    xm /= static_cast<double>(n);
-    ym /= static_cast<double>(n);
+};
+
+Weights make_weights(const double* y, uint64_t n, int mode) {
+    double fl = 0.0;
+    for (uint64_t i = 0; i < n; ++i)
+        if (y[i] > 0.0 && (fl == 0.0 || y[i] < fl)) fl = y[i];
+    return Weights{mode, fl > 0.0 ? fl : 1.0};
+}
+
+// (Weighted) least squares y = slope * x + intercept, centred normal equations.
+void ols(const double* x, const double* y, uint64_t n, int mode, double* slope, double* intercept) {
+    const Weights w = make_weights(y, n, mode);
+    double sw = 0.0, xm = 0.0, ym = 0.0;
+    for (uint64_t i = 0; i < n; ++i) {
+        const double wi = w(y[i]);
+        sw += wi;
+        xm += wi * x[i];
+        ym += wi * y[i];
+    }
+    xm /= sw;
+    ym /= sw;
     double sxx = 0.0, sxy = 0.0;
     for (uint64_t i = 0; i < n; ++i) {
-        sxx += (x[i] - xm) * (x[i] - xm);
-        sxy += (x[i] - xm) * (y[i] - ym);
+        const double wi = w(y[i]);
+        sxx += wi * (x[i] - xm) * (x[i] - xm);
+        sxy += wi * (x[i] - xm) * (y[i] - ym);
     }
     *slope = sxx > 0.0 ? sxy / sxx : 0.0;
     *intercept = ym - *slope * xm;
 }
 
-double rss(const double* x, const double* y, uint64_t n, double slope, double intercept) {
+double rss(const double* x, const double* y, uint64_t n, int mode, double slope, double intercept) {
+    const Weights w = make_weights(y, n, mode);
     double r = 0.0;
     for (uint64_t i = 0; i < n; ++i) {
         const double e = y[i] - (slope * x[i] + intercept);
-        r += e * e;
+        r += w(y[i]) * e * e;
     }
     return r;
 }
@@ -85,6 +109,7 @@ olap_status olap_gate_calibrate(const olap_gate_samples* s, double margin_ms, ol
         !s->t_tx_ms || !s->t_ker_ms || !s->t_post_ms)
         return OLAP_E_INVALID;
     if (s->op != OLAP_OP_TOPK && s->op != OLAP_OP_PROBE) return OLAP_E_INVALID;
+    if (s->weighting != OLAP_FIT_ORDINARY && s->weighting != OLAP_FIT_RELATIVE) return OLAP_E_INVALID;
     const uint64_t n = s->count;
     olap_gate_model m;
     std::memset(&m, 0, sizeof(m));
@@ -94,11 +119,11 @@ olap_status olap_gate_calibrate(const olap_gate_samples* s, double margin_ms, ol
     if (s->op == OLAP_OP_TOPK) {
         double a1, b1, a2, b2;
         for (uint64_t i = 0; i < n; ++i) x[i] = cpu_x(OLAP_CPU_NLOGN, s->n[i], s->k_or_m[i]);
-        ols(x, s->t_cpu_ms, n, &a1, &b1);
-        m.rss_nlogn = rss(x, s->t_cpu_ms, n, a1, b1);
+        ols(x, s->t_cpu_ms, n, s->weighting, &a1, &b1);
+        m.rss_nlogn = rss(x, s->t_cpu_ms, n, s->weighting, a1, b1);
         for (uint64_t i = 0; i < n; ++i) x[i] = cpu_x(OLAP_CPU_NK, s->n[i], s->k_or_m[i]);
-        ols(x, s->t_cpu_ms, n, &a2, &b2);
-        m.rss_nk = rss(x, s->t_cpu_ms, n, a2, b2);
+        ols(x, s->t_cpu_ms, n, s->weighting, &a2, &b2);
+        m.rss_nk = rss(x, s->t_cpu_ms, n, s->weighting, a2, b2);
         if (m.rss_nlogn <= m.rss_nk) {
             m.cpu_form = OLAP_CPU_NLOGN;
             m.a = a1;
@@ -111,12 +136,12 @@ olap_status olap_gate_calibrate(const olap_gate_samples* s, double margin_ms, ol
     } else {
         m.cpu_form = OLAP_CPU_NM;
         for (uint64_t i = 0; i < n; ++i) x[i] = cpu_x(OLAP_CPU_NM, s->n[i], s->k_or_m[i]);
-        ols(x, s->t_cpu_ms, n, &m.a, &m.b);
+        ols(x, s->t_cpu_ms, n, s->weighting, &m.a, &m.b);
     }
     delete[] x;
-    ols(s->tx_bytes, s->t_tx_ms, n, &m.c, &m.d);
-    ols(s->n, s->t_ker_ms, n, &m.e, &m.f);
-    ols(s->out_rows, s->t_post_ms, n, &m.g, &m.h);
+    ols(s->tx_bytes, s->t_tx_ms, n, s->weighting, &m.c, &m.d);
+    ols(s->n, s->t_ker_ms, n, s->weighting, &m.e, &m.f);
+    ols(s->out_rows, s->t_post_ms, n, s->weighting, &m.g, &m.h);
     *out = m;
     return OLAP_OK;
 }

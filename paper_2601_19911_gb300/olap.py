@@ -36,6 +36,7 @@ EXPORTS = [
 SERVE_GATED, SERVE_ALWAYS_GPU, SERVE_ALWAYS_HOST = 0, 1, 2
 OP_TOPK, OP_PROBE = 0, 1
 CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
+FIT_ORDINARY, FIT_RELATIVE = 0, 1
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
 NOALLOC_MAX_N = 1 << 24
 NOALLOC_MAX_K = 4096
@@ -67,7 +68,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 
 class olap_gate_samples(ctypes.Structure):
-    _fields_ = [("op", ctypes.c_int), ("count", ctypes.c_uint64), ("n", _dp), ("k_or_m", _dp),
+    _fields_ = [("op", ctypes.c_int), ("weighting", ctypes.c_int), ("count", ctypes.c_uint64), ("n", _dp),
+                ("k_or_m", _dp),
                 ("tx_bytes", _dp), ("out_rows", _dp), ("t_cpu_ms", _dp), ("t_tx_ms", _dp),
                 ("t_ker_ms", _dp), ("t_post_ms", _dp)]
 
@@ -492,7 +494,7 @@ def topk_noalloc(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=
 # ---------------------------------------------------------------------------
 
 def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_ker_ms, t_post_ms,
-                   margin_ms: float = 0.0) -> olap_gate_model:
+                   margin_ms: float = 0.0, weighting: int = FIT_ORDINARY) -> olap_gate_model:
     """olap_gate_calibrate over equal-length sample sequences (times in ms)."""
     lib = load()
     cols = [np.ascontiguousarray(np.asarray(c, dtype=np.float64)) for c in
@@ -500,7 +502,7 @@ def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_
     cnt = cols[0].shape[0]
     assert all(c.shape[0] == cnt for c in cols)
     ptrs = [c.ctypes.data_as(_dp) for c in cols]
-    smp = olap_gate_samples(op, cnt, *ptrs)
+    smp = olap_gate_samples(op, weighting, cnt, *ptrs)
     m = olap_gate_model()
     st = lib.olap_gate_calibrate(ctypes.byref(smp), float(margin_ms), ctypes.byref(m))
     if st != OK:

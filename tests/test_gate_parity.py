@@ -43,12 +43,13 @@ def _noisy_samples(rng, op, form, count=24):
 @pytest.mark.parametrize("op,form", [(gate.TOPK, gate.CPU_NLOGN), (gate.TOPK, gate.CPU_NK),
                                      (gate.PROBE, gate.CPU_NM)])
 @pytest.mark.parametrize("seed", range(4))
-def test_calibrate_and_decide_match_oracle(op, form, seed):
+@pytest.mark.parametrize("weighting", [gate.ORDINARY, gate.RELATIVE])
+def test_calibrate_and_decide_match_oracle(op, form, seed, weighting):
     rng = np.random.default_rng(seed)
     smp = _noisy_samples(rng, op, form)
     for margin in (0.0, 5.0, 10.0):
-        want = gate.calibrate(op, *smp, margin_ms=margin)
-        got = olap.gate_calibrate(op, *smp, margin_ms=margin)
+        want = gate.calibrate(op, *smp, margin_ms=margin, weighting=weighting)
+        got = olap.gate_calibrate(op, *smp, margin_ms=margin, weighting=weighting)
         assert got.cpu_form == want.cpu_form
         for nm in "abcdefgh":
             assert math.isclose(getattr(got, nm), getattr(want, nm), rel_tol=1e-9, abs_tol=1e-15), nm

@@ -86,3 +86,22 @@ def test_probe_fit():
     m = gate.calibrate(gate.PROBE, n, mm, 8 * n, n, t_cpu, 1e-9 * 8 * n + 0.01, 1e-8 * n, 1e-9 * n)
     assert m.cpu_form == gate.CPU_NM
     assert math.isclose(m.a, 4e-6, rel_tol=1e-9) and math.isclose(m.b, 0.3, rel_tol=1e-9)
+
+
+def test_relative_weighting_recovers_exact_data_and_favours_small_points():
+    # exact data: both weightings recover the coefficients
+    co = dict(a=3.1e-6, b=0.25, c=2.5e-9, d=0.04, e=1.5e-7, f=0.01, g=3e-6, h=0.002)
+    smp = _samples(**co, form=gate.CPU_NLOGN)
+    m = gate.calibrate(gate.TOPK, *smp, weighting=gate.RELATIVE)
+    for name, want in co.items():
+        assert math.isclose(getattr(m, name), want, rel_tol=1e-9, abs_tol=1e-12), name
+    # a fixed cost at small x and a different slope at large x: the relative
+    # fit keeps the small-x intercept, the ordinary fit does not
+    x = np.array([1e3, 1e4, 1e5, 1e6, 1e7, 1e8])
+    y = np.array([0.05, 0.05, 0.06, 0.15, 1.0, 10.0])
+    s_o, i_o = gate.ols(x, y, gate.ORDINARY)
+    s_r, i_r = gate.ols(x, y, gate.RELATIVE)
+    assert abs(i_r - 0.05) < abs(i_o - 0.05)
+    # weights 1/y^2 by hand on two points reduce to the line through them
+    s2, i2 = gate.ols([1.0, 3.0], [2.0, 4.0], gate.RELATIVE)
+    assert math.isclose(s2, 1.0) and math.isclose(i2, 1.0)
