@@ -318,7 +318,7 @@ def batched_leg(args, ctx, torch):
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": algo / (ms_graph * 1e-3) / 1e9 / peak,
                          "bytes": "8 per Top-K key + 24 per selected row + 40 per probe + 8 per pair"},
-            "gpu_launches_graph": 2, "clocks": clk.summary()}
+            "gpu_launches_graph": (1 if args.batch_topk else 0) + (2 if args.batch_probe else 0), "clocks": clk.summary()}
 
 
 def _median_ms(fn, reps=3):

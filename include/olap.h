@@ -226,8 +226,10 @@ typedef struct {
     int32_t* status;                 /* device, optional */
 } olap_batch_item;
 
-/* Check the items, upload the work queue (largest items first) and capture
- * the persistent launch in a CUDA graph.  Blocking. */
+/* Check the items, upload the work queues (Top-K items largest first, one CTA
+ * each; probe items largest first, cut into chunks of 32768 probe rows that
+ * any CTA may take) and capture the persistent launches in a CUDA graph.
+ * Blocking. */
 olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint64_t n_items, olap_batch** out);
 /* Run every item once: one graph launch on `stream` (NULL => context stream). */
 olap_status olap_batch_run(olap_batch* batch, void* stream);

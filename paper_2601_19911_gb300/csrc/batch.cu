@@ -13,8 +13,10 @@
 //     the selected entries in shared memory, where they are sorted.  Small
 //     items (n <= 4096) are sorted whole; a misjudged sample falls back to
 //     radix passes over the item's keys.
-//   * probe: the probe rounds of the join kernel, run by this CTA alone over
-//     the item's keys, pairs counted in the item's own count word.
+//   * probe: the probe rounds of the join kernel over one chunk of at most
+//     BP_CHUNK probe rows of an item; a large item is many chunks taken by
+//     many CTAs, all appending to the item's own count word, which a reset
+//     kernel zeroes before the probe queue starts.
 // Descriptors are checked on the device; a bad one gets OLAP_E_DEVICE in its
 // status word and is skipped.
 #include <algorithm>
@@ -39,6 +41,8 @@ constexpr uint32_t BT_CAND = 65536;       // candidate capacity per CTA
 constexpr int BT_WS = 128;                // staged hits per warp
 constexpr int BT_BINS = 4096;
 constexpr int BT_SMEM = 2 * BT_SMALL * 12; // two sort areas; also the histogram, stages, probe stage
+constexpr uint64_t BP_ROUNDS = 32;         // probe rounds (JP_TPB * JP_U rows each) per chunk
+constexpr uint64_t BP_CHUNK = BP_ROUNDS * JP_TPB * JP_U;
 static_assert(JP_STAGE * 8 <= BT_SMEM, "probe stage must fit");
 static_assert((BT_TPB / 32) * BT_WS * 12 <= BT_SMEM, "warp stages must fit");
 
@@ -61,6 +65,13 @@ struct __align__(8) Item {
     uint64_t cap;
     unsigned long long* count;   // rows (Top-K) or pairs (probe) written
     int32_t* status;
+};
+
+// One probe work unit: rounds [r0, r1) of probe item `item`.
+struct ProbeChunk {
+    uint32_t item;
+    uint32_t r0, r1;
+    uint32_t pad;
 };
 
 __device__ __forceinline__ uint64_t item_rank(const Item& it, uint64_t i, uint32_t* rid) {
@@ -393,29 +404,40 @@ __global__ void __launch_bounds__(BT_TPB, 2) batch_topk_kernel(const Item* items
     }
 }
 
-// Persistent probe executor: each CTA takes the next probe item and runs
-// all its rounds.
-__global__ void __launch_bounds__(JP_TPB, 3) batch_probe_kernel(const Item* items, uint64_t n_items,
-                                                                unsigned long long* next, int* errors) {
+// Before the probe queue starts: check each probe item, zero its pair count
+// and record its status (one thread per item).
+__global__ void batch_probe_reset_kernel(const Item* items, uint64_t n_items, int* errors) {
+    const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    const Item& it = items[i];
+    const int st = it.op == OLAP_OP_PROBE ? item_check(it) : static_cast<int>(OLAP_E_DEVICE);
+    if (st == OLAP_OK) *it.count = 0;
+    if (it.status) *it.status = st;
+    if (st != OLAP_OK) atomicAdd(errors, 1);
+}
+
+// Persistent probe executor: each CTA takes the next chunk off the queue and
+// runs its rounds; chunks of items that failed the check are skipped.
+__global__ void __launch_bounds__(JP_TPB, 3) batch_probe_kernel(const Item* items, const ProbeChunk* chunks,
+                                                                uint64_t n_chunks, unsigned long long* next) {
     extern __shared__ __align__(16) uint2 stage[];
     __shared__ unsigned long long s_item;
     __shared__ unsigned scount;
     __shared__ unsigned long long sbase;
-    __shared__ Item s_it;
+    __shared__ ProbeChunk s_ch;
+    __shared__ int s_ok;
     __shared__ ProbeArgs s_args;       // kept in shared memory, read as needed
+    uint32_t cur = 0xFFFFFFFFu;        // item whose arguments s_args holds
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(next, 1ull);
         __syncthreads();
         const uint64_t idx = s_item;
-        if (idx >= n_items) break;
-        if (threadIdx.x < sizeof(Item) / 8)
-            reinterpret_cast<uint64_t*>(&s_it)[threadIdx.x] = reinterpret_cast<const uint64_t*>(items + idx)[threadIdx.x];
-        __syncthreads();
-        const Item& it = s_it;
-        const int st = it.op == OLAP_OP_PROBE ? item_check(it) : static_cast<int>(OLAP_E_DEVICE);
-        if (st == OLAP_OK) {
-            if (threadIdx.x == 0) {
-                *it.count = 0;
+        if (idx >= n_chunks) break;
+        if (threadIdx.x == 0) {
+            s_ch = chunks[idx];
+            if (s_ch.item != cur) {
+                const Item& it = items[s_ch.item];
+                s_ok = it.op == OLAP_OP_PROBE && item_check(it) == OLAP_OK;
                 s_args.keys = static_cast<const int64_t*>(it.keys);
                 s_args.rowids = it.rowids;
                 s_args.n = it.n;
@@ -427,13 +449,12 @@ __global__ void __launch_bounds__(JP_TPB, 3) batch_probe_kernel(const Item* item
                 s_args.cap = it.cap;
                 s_args.count = it.count;
             }
-            __syncthreads();
-            probe_rounds(s_args, 0, 1, stage, &scount, &sbase);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            if (it.status) *it.status = st;
-            if (st != OLAP_OK) atomicAdd(errors, 1);
+        cur = s_ch.item;
+        if (s_ok) {
+            const uint64_t end = min(s_args.n, static_cast<uint64_t>(s_ch.r1) * JP_TPB * JP_U);
+            probe_rounds(s_args, s_ch.r0, 1, end, stage, &scount, &sbase);
         }
         __syncthreads();
     }
@@ -450,6 +471,8 @@ struct olap_batch {
     std::vector<olap_batch_item> items;   // caller's order (per-query baseline)
     Item* d_items = nullptr;              // Top-K items then probe items, each largest first
     uint64_t n_topk = 0, n_probe = 0;
+    ProbeChunk* d_chunks = nullptr;       // probe work units, largest items first
+    uint64_t n_chunks = 0;
     unsigned long long* d_next = nullptr; // [0] Top-K queue head, [8] probe queue head
     int* d_errors = nullptr;
     uint64_t* cand_r = nullptr;
@@ -468,9 +491,14 @@ olap_status enqueue_batch(olap_batch* b, cudaStream_t s) {
     if (b->n_topk)
         batch_topk_kernel<<<b->grid_topk, BT_TPB, BT_SMEM, s>>>(b->d_items, b->n_topk, b->d_next, b->cand_r,
                                                                 b->cand_rid, b->d_errors);
-    if (b->n_probe)
-        batch_probe_kernel<<<b->grid_probe, JP_TPB, JP_SMEM, s>>>(b->d_items + b->n_topk, b->n_probe,
-                                                                  b->d_next + 1, b->d_errors);
+    if (b->n_probe) {
+        const Item* probe_items = b->d_items + b->n_topk;
+        batch_probe_reset_kernel<<<static_cast<unsigned>((b->n_probe + 255) / 256), 256, 0, s>>>(
+            probe_items, b->n_probe, b->d_errors);
+        if (b->n_chunks)
+            batch_probe_kernel<<<b->grid_probe, JP_TPB, JP_SMEM, s>>>(probe_items, b->d_chunks, b->n_chunks,
+                                                                      b->d_next + 1);
+    }
     e = cudaGetLastError();
     return e == cudaSuccess ? OLAP_OK : cuda_fail(b->ctx, e, "batch launch");
 }
@@ -480,6 +508,7 @@ void batch_release(olap_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_chunks) cudaFree(b->d_chunks);
     if (b->d_next) cudaFree(b->d_next);
     if (b->cand_r) cudaFree(b->cand_r);
     if (b->cand_rid) cudaFree(b->cand_rid);
@@ -550,8 +579,20 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
         if (sorted[i].op == OLAP_OP_TOPK) ++n_topk;
     }
 
+    // Probe work units: each item cut into chunks of BP_ROUNDS rounds, in the
+    // items' (largest first) order.
+    std::vector<ProbeChunk> chunks;
+    const uint64_t per_round = static_cast<uint64_t>(JP_TPB) * JP_U;
+    for (uint64_t i = n_topk; i < n_items; ++i) {
+        const uint64_t rounds = (sorted[i].n + per_round - 1) / per_round;
+        for (uint64_t r = 0; r < rounds; r += BP_ROUNDS)
+            chunks.push_back({static_cast<uint32_t>(i - n_topk), static_cast<uint32_t>(r),
+                              static_cast<uint32_t>(std::min(rounds, r + BP_ROUNDS)), 0u});
+    }
+
     olap_batch* b = new olap_batch();
     b->ctx = ctx;
+    b->n_chunks = chunks.size();
     b->items.assign(items, items + n_items);
     b->n_topk = n_topk;
     b->n_probe = n_items - n_topk;
@@ -570,9 +611,8 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
     }
     b->grid_topk = ctx->sm_count * std::max(1, std::min(per_t, 2));
     b->grid_probe = ctx->sm_count * std::max(1, per_p);
-    const size_t nb = std::max<uint64_t>(1, n_items) * sizeof(Item);
-    (void)nb;
     if ((e = cudaMalloc(&b->d_items, std::max<uint64_t>(1, n_items) * sizeof(Item))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_chunks, std::max<size_t>(1, chunks.size()) * sizeof(ProbeChunk))) != cudaSuccess ||
         (e = cudaMalloc(reinterpret_cast<void**>(&b->d_next), 256)) != cudaSuccess ||
         (e = cudaMalloc(&b->cand_r, static_cast<size_t>(b->grid_topk) * BT_CAND * 8)) != cudaSuccess ||
         (e = cudaMalloc(&b->cand_rid, static_cast<size_t>(b->grid_topk) * BT_CAND * 4)) != cudaSuccess) {
@@ -586,6 +626,11 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
                        cudaSuccess) {
         batch_release(b);
         return cuda_fail(ctx, e, "batch descriptor upload");
+    }
+    if (!chunks.empty() && (e = cudaMemcpy(b->d_chunks, chunks.data(), chunks.size() * sizeof(ProbeChunk),
+                                           cudaMemcpyHostToDevice)) != cudaSuccess) {
+        batch_release(b);
+        return cuda_fail(ctx, e, "batch chunk upload");
     }
     // Capture the reset and the persistent launch in a CUDA graph.
     cudaStream_t cap;

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs a) {
     extern __shared__ __align__(16) uint2 stage[];
     __shared__ unsigned scount;
     __shared__ unsigned long long sbase;
-    probe_rounds(a, blockIdx.x, gridDim.x, stage, &scount, &sbase);
+    probe_rounds(a, blockIdx.x, gridDim.x, a.n, stage, &scount, &sbase);
 }
 
 uint64_t next_pow2(uint64_t x) {

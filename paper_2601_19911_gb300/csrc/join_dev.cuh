@@ -110,15 +110,16 @@ __device__ __forceinline__ void flush_stage(const ProbeArgs& a, uint2* stage, un
 }
 
 // Probe rounds first, first + step, ... of JP_TPB * JP_U keys each by one CTA
-// (whole CTA calls), staging pairs in `stage` (JP_STAGE entries) and flushing
-// them to the output; everything staged is flushed before returning.
-__device__ __forceinline__ void probe_rounds(const ProbeArgs& a, uint64_t first, uint64_t step, uint2* stage,
-                                             unsigned* scount_p, unsigned long long* sbase_p) {
+// (whole CTA calls), over probe rows below `end` (at most a.n), staging pairs
+// in `stage` (JP_STAGE entries) and flushing them to the output; everything
+// staged is flushed before returning.
+__device__ __forceinline__ void probe_rounds(const ProbeArgs& a, uint64_t first, uint64_t step, uint64_t end,
+                                             uint2* stage, unsigned* scount_p, unsigned long long* sbase_p) {
     unsigned& scount = *scount_p;
     if (threadIdx.x == 0) scount = 0;
     __syncthreads();
     const uint64_t per = static_cast<uint64_t>(JP_TPB) * JP_U;
-    for (uint64_t base = first * per; base < a.n; base += step * per) {
+    for (uint64_t base = first * per; base < end; base += step * per) {
         uint64_t k[JP_U], bk[JP_U];
         uint32_t prid[JP_U];
         bool act[JP_U];
@@ -126,7 +127,7 @@ __device__ __forceinline__ void probe_rounds(const ProbeArgs& a, uint64_t first,
 #pragma unroll
         for (int j = 0; j < JP_U; ++j) {
             const uint64_t idx = base + static_cast<uint64_t>(j) * JP_TPB + threadIdx.x;
-            const bool v = idx < a.n;
+            const bool v = idx < end;
             k[j] = v ? ld_stream_u64(a.keys + idx) : JN_EMPTY;
             prid[j] = v ? (a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx)) : 0u;
             act[j] = v && k[j] != JN_EMPTY;

@@ -55,6 +55,7 @@ def _make(ctx, n_topk=300, n_probe=40, seed=5):
     b = datagen.join_build(1 << 18, "mult14", seed=seed)
     table = ctx.join_build(torch.from_numpy(b.keys).cuda())
     pns = datagen.log_uniform(1e3, 2e5, datagen.stream_seed(seed, 10), n_probe)
+    pns[:5] = [0, 1, 32768, 32769, 700_000]       # empty, one chunk exactly, one row over, 22 chunks
     for i in range(n_probe):
         p = datagen.join_probe(int(pns[i]), b, 0.5, "uniform", seed=seed * 100 + i)
         need = p.expected_pairs(b)
@@ -128,6 +129,29 @@ def test_corrupted_descriptor_is_rejected_on_device(ctx):
     wk, wr = oracle.topk(keys.cpu().numpy(), 10, olap.DESC)
     np.testing.assert_array_equal(orow.cpu().numpy().view(np.uint32), wr)
     batch.free()
+
+
+def test_corrupted_probe_descriptor_skips_only_its_chunks(ctx):
+    b = datagen.join_build(50_000, "mult14", seed=8)
+    table = ctx.join_build(torch.from_numpy(b.keys).cuda())
+    p = datagen.join_probe(200_000, b, 0.7, "uniform", seed=8)      # 7 chunks
+    need = p.expected_pairs(b)
+    dk = torch.from_numpy(p.keys).cuda()
+    out = torch.empty((need, 2), dtype=torch.int32, device="cuda")
+    c = torch.full((2,), 77, dtype=torch.int64, device="cuda")
+    st = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    good = olap.probe_item(table, dk, out, need, c[0:1], d_status=st[0:1])
+    bad = olap.probe_item(table, dk, out, need, c[1:2], d_status=st[1:2])
+    bad.keys = None                         # n > 0 with no keys
+    batch = ctx.batch([bad, good])
+    batch.run()
+    ctx.sync()
+    assert batch.errors() == 1
+    assert st.cpu().tolist() == [olap.OK, olap.E_DEVICE]
+    assert c.cpu().tolist() == [need, 77]   # the rejected item's count is left alone
+    np.testing.assert_array_equal(_packed(out.cpu().numpy().view(np.uint32)), oracle.join(b.keys, p.keys))
+    batch.free()
+    table.free()
 
 
 def test_host_rejects_k_above_limit(ctx):
