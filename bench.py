@@ -33,6 +33,28 @@ sys.path.insert(0, ROOT)
 METRIC = "Top-K Gkeys/s & join probes/s (% HBM peak); batched vs per-query; gated P99"
 
 
+# DRAM bytes (read + write) per input key of the Top-K filter kernel, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of that kernel at
+# 2^26 uniform keys, K = 1000, register filter; the traffic of a full launch
+# is this figure times n (the reads are the keys, the writes the candidates,
+# both in proportion to n).  Valid only for that configuration.
+FILTER_DRAM_BYTES_PER_KEY = {"i64": 540_177_408 / 2**26, "f32": 271_681_792 / 2**26}
+
+
+def _kernel_pass(ctx, steps, launch):
+    """Run `launch` `steps` more times with per-kernel CUDA events on the
+    library's stream; the mean device time of each kernel (ms)."""
+    ctx.time_kernels(True)
+    acc = {}
+    for _ in range(steps):
+        launch()
+        for nm, v in ctx.kernel_ms().items():
+            if v >= 0:
+                acc.setdefault(nm, []).append(v)
+    ctx.time_kernels(False)
+    return {nm: float(np.mean(v)) for nm, v in acc.items()}
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -221,6 +243,8 @@ def join_leg(args, ctx, torch, world):
     for _ in range(e2e_steps):
         ctx.join_probe(table, hk, out=hout)
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    kms = _kernel_pass(ctx, min(steps, 10), lambda: ctx.join_probe_async(table, dk, out, need, cnt))
+    kern_ms = kms["join_probe_ms"]
     peak, peak_kind = _peaks()
     m = need / npr
     honest = npr * (8 + 32) + need * 8
@@ -236,12 +260,13 @@ def join_leg(args, ctx, torch, world):
         "build": {"ms": build_s * 1e3, "Grows_per_s": nb / build_s / 1e9},
         "roofline": {"bound": "hbm", "kernel": "olap::join_probe_kernel", "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s",
-                     "honest": {"bytes_per_launch": honest, "achieved": honest / (ms * 1e-3) / 1e9,
-                                "frac": honest / (ms * 1e-3) / 1e9 / peak,
+                     "kernel_ms": kern_ms,
+                     "honest": {"bytes_per_launch": honest, "achieved": honest / (kern_ms * 1e-3) / 1e9,
+                                "frac": honest / (kern_ms * 1e-3) / 1e9 / peak,
                                 "bytes_per_probe": "8 key + 32 table sector + 8 per pair"},
                      "streaming_only": {"bytes_per_launch": stream_only,
-                                        "achieved": stream_only / (ms * 1e-3) / 1e9,
-                                        "frac": stream_only / (ms * 1e-3) / 1e9 / peak},
+                                        "achieved": stream_only / (kern_ms * 1e-3) / 1e9,
+                                        "frac": stream_only / (kern_ms * 1e-3) / 1e9 / peak},
                      "traffic": args.join_traffic},
         "e2e": {"value": world * npr / e2e_s / 1e9, "unit": "Gprobes/s", "ms_per_step": e2e_s * 1e3,
                 "h2d_bytes_per_step": npr * 8, "d2h_bytes_per_step": need * 8 + 8},
@@ -529,10 +554,20 @@ def run_ours(args):
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     e2e_value = world * n / e2e_s / 1e9
 
+    # -- per-kernel device time (events around each kernel), same workload ----
+    kms = _kernel_pass(ctx, args.steps, lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow))
     peak, peak_kind = _peaks()
-    algo_bytes = n * w + 24 * k
-    kern_ms = float(np.mean(per_launch))
+    call_ms = float(np.mean(per_launch))
+    # the dominant kernel: the streaming filter when the plan has one (it
+    # reads every key once), else the select kernel (which then does)
+    top = "topk_filter_ms" if "topk_filter_ms" in kms else "topk_select_ms"
+    kern_ms = kms[top]
+    algo_bytes = n * w
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
+    traffic = args.traffic
+    if traffic is None and top == "topk_filter_ms" and k == 1000 and args.dist == "uniform" \
+            and args.filter == "regs":
+        traffic = FILTER_DRAM_BYTES_PER_KEY[args.key_type] * n
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -542,9 +577,17 @@ def run_ours(args):
                    "l2": f"inputs larger than L2 ({n * w / 2**30:.2f} GiB keys)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": args.traffic, "peak_kind": peak_kind,
-                     "kernel": "olap::topk_kernel", "algorithmic_bytes_per_launch": algo_bytes,
-                     "kernel_ms": kern_ms, "filter": args.filter, "last_launch": phases,
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": {"topk_filter_ms": "olap::topk_filter_regs_kernel" if args.filter == "regs"
+                                else "olap::topk_filter_bulk_kernel",
+                                "topk_select_ms": "olap::topk_select_kernel"}[top],
+                     "algorithmic_bytes_per_launch": algo_bytes,
+                     "bytes_per_unit": f"{w} per key read once", "kernel_ms": kern_ms,
+                     "kernel_ms_all": kms, "call_ms": call_ms,
+                     "call_frac": algo_bytes / (call_ms * 1e-3) / 1e9 / peak,
+                     "timing": "CUDA events around each kernel on the library stream, "
+                               f"{args.steps} further steps after the timed region",
+                     "filter": args.filter, "last_launch": phases,
                      "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w,
                 "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
@@ -559,7 +602,7 @@ def run_ours(args):
     if "batched" in workloads:
         torch.cuda.empty_cache()
         line["batched"] = batched_leg(args, ctx, torch)
-        line["gpu_launches"] += 2 * args.batch_reps
+        line["gpu_launches"] += line["batched"]["gpu_launches_graph"] * args.batch_reps
     if "serving" in workloads:
         torch.cuda.empty_cache()
         line["serving"] = serving_leg(args, ctx, torch)

@@ -140,6 +140,20 @@ typedef struct {
 } olap_topk_info;
 olap_status olap_topk_info_last(olap_ctx* ctx, olap_topk_info* out);
 
+/* Per-kernel device time, from CUDA events recorded on the launching stream
+ * around each kernel of the Top-K and join probe calls made while timing is
+ * on (off by default; each timed call records up to four events more). */
+olap_status olap_ctx_time_kernels(olap_ctx* ctx, int on);
+typedef struct {
+    float topk_prepare_ms;           /* sample threshold kernel */
+    float topk_filter_ms;            /* streaming filter (-1: the plan had none) */
+    float topk_select_ms;            /* cooperative select kernel */
+    float join_probe_ms;             /* probe kernel */
+} olap_kernel_ms;
+/* Times of the last timed Top-K and join probe on this context (waits for
+ * them); -1 for a kernel that was not timed. */
+olap_status olap_kernel_ms_last(olap_ctx* ctx, olap_kernel_ms* out);
+
 /* ------------------------------------------------------------------------
  * Key-based hash join, build and probe (Sec. III-B: "parallel probing using a
  * key-only hash table", pointers returned for late materialization, Sec. II-C).

@@ -196,7 +196,9 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
     a.dev_status = dev_status;
     a.filter = ctx->opts.topk_filter == OLAP_FILTER_BULK ? TK_FILTER_BULK : TK_FILTER_REGS;
     ctx->last_topk_ctl = a.ctl;
-    cudaError_t e = topk_launch(a, ctx->topk_geom, stream);
+    ctx->topk_timed = ctx->time_kernels;
+    ctx->topk_filtered = plan.use_sample;
+    cudaError_t e = topk_launch(a, ctx->topk_geom, stream, ctx->time_kernels ? ctx->kev : nullptr);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return cuda_fail(ctx, e, "Top-K launch");
@@ -282,6 +284,8 @@ void olap_ctx_destroy(olap_ctx* ctx) {
         if (ctx->pinned[i]) cudaFreeHost(ctx->pinned[i]);
         if (ctx->pinned_ev[i]) cudaEventDestroy(ctx->pinned_ev[i]);
     }
+    for (cudaEvent_t ev : ctx->kev)
+        if (ev) cudaEventDestroy(ev);
     if (ctx->host_status) cudaFreeHost(ctx->host_status);
     if (ctx->aux) cudaFree(ctx->aux);
     detach_tables(ctx);
@@ -384,6 +388,36 @@ olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type typ
 }
 
 }  // extern "C"
+
+extern "C" olap_status olap_ctx_time_kernels(olap_ctx* ctx, int on) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (on && !ctx->kev[0]) {
+        cudaError_t e = cudaSetDevice(ctx->device);
+        for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->kev[i]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "timing events");
+    }
+    ctx->time_kernels = on != 0;
+    return OLAP_OK;
+}
+
+extern "C" olap_status olap_kernel_ms_last(olap_ctx* ctx, olap_kernel_ms* out) {
+    if (!ctx || !out) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    out->topk_prepare_ms = out->topk_filter_ms = out->topk_select_ms = out->join_probe_ms = -1.0f;
+    cudaError_t e = cudaSuccess;
+    auto span = [&](int a, int b, float* ms) {
+        if (e == cudaSuccess) e = cudaEventSynchronize(ctx->kev[b]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, ctx->kev[a], ctx->kev[b]);
+    };
+    if (ctx->topk_timed) {
+        span(0, 1, &out->topk_prepare_ms);
+        if (ctx->topk_filtered) span(1, 2, &out->topk_filter_ms);
+        span(2, 3, &out->topk_select_ms);
+    }
+    if (ctx->probe_timed) span(4, 5, &out->join_probe_ms);
+    return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "kernel timing read-back");
+}
 
 extern "C" olap_status olap_topk_info_last(olap_ctx* ctx, olap_topk_info* out) {
     if (!ctx || !out) return OLAP_E_INVALID;

@@ -44,6 +44,12 @@ struct olap_ctx {
     // Control block of the last Top-K launched (diagnostics).
     void* last_topk_ctl = nullptr;
 
+    // Optional per-kernel timing: events around the kernels of the last Top-K
+    // (4) and of the last join probe (2) launched while timing is on.
+    bool time_kernels = false;
+    cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool topk_timed = false, probe_timed = false, topk_filtered = false;
+
     // Device memory held by live join tables built through this context.
     uint64_t table_bytes = 0;
     std::set<olap_join_table*> tables;

@@ -119,8 +119,12 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     a.out = reinterpret_cast<uint2*>(d_out);
     a.cap = capacity;
     a.count = reinterpret_cast<unsigned long long*>(d_count);
+    ctx->probe_timed = ctx->time_kernels;
+    if (ctx->time_kernels && (e = cudaEventRecord(ctx->kev[4], s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "timing event");
     join_probe_kernel<<<grid, JP_TPB, JP_SMEM, s>>>(a);
     e = cudaGetLastError();
+    if (e == cudaSuccess && ctx->time_kernels) e = cudaEventRecord(ctx->kev[5], s);
     return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "probe launch");
 }
 

@@ -985,13 +985,16 @@ bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, Topk
     return true;
 }
 
-cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t stream) {
+cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t stream, cudaEvent_t* ev) {
     TopkArgs a = args;
     a.tile_bytes = geom.tile_bytes;
     a.stages = geom.stages;
+    cudaError_t e;
+    if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
     topk_prepare_kernel<<<1, TK_TPB, 0, stream>>>(a);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
     if (a.use_sample) {
         if (a.filter == TK_FILTER_REGS) {
             if (a.f32) topk_filter_regs_kernel<true><<<geom.regs_grid, TKR_TPB, 0, stream>>>(a);
@@ -1005,9 +1008,12 @@ cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (ev && (e = cudaEventRecord(ev[2], stream)) != cudaSuccess) return e;
     void* params[] = {&a};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(topk_select_kernel), dim3(geom.grid),
-                                       dim3(TK_TPB), params, TK_SORT_SMEM, stream);
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void*>(topk_select_kernel), dim3(geom.grid), dim3(TK_TPB),
+                                    params, TK_SORT_SMEM, stream);
+    if (e != cudaSuccess || !ev) return e;
+    return cudaEventRecord(ev[3], stream);
 }
 
 }  // namespace olap

@@ -111,6 +111,10 @@ bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, Topk
 // Enqueue one Top-K: prepare (1 CTA), the streaming filter when the sampled
 // path is taken, then the cooperative select kernel.  Returns the first CUDA
 // launch error.
-cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t stream);
+// ev (optional, 4 events): recorded before the prepare kernel and after the
+// prepare, filter and select kernels (the filter pair is empty when the plan
+// has no sample filter).
+cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t stream,
+                        cudaEvent_t* ev = nullptr);
 
 }  // namespace olap

@@ -28,6 +28,7 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
+    "olap_ctx_time_kernels", "olap_kernel_ms_last",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
     "olap_batch_create", "olap_batch_run", "olap_batch_run_per_query", "olap_batch_errors", "olap_batch_free",
@@ -135,6 +136,11 @@ class olap_topk_info(ctypes.Structure):
     ]
 
 
+class olap_kernel_ms(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_float) for nm in
+                ("topk_prepare_ms", "topk_filter_ms", "topk_select_ms", "join_probe_ms")]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -170,6 +176,10 @@ def load(path: str | None = None):
         lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         lib.olap_topk_info_last.restype = i32
         lib.olap_topk_info_last.argtypes = [vp, ctypes.POINTER(olap_topk_info)]
+        lib.olap_ctx_time_kernels.restype = i32
+        lib.olap_ctx_time_kernels.argtypes = [vp, i32]
+        lib.olap_kernel_ms_last.restype = i32
+        lib.olap_kernel_ms_last.argtypes = [vp, ctypes.POINTER(olap_kernel_ms)]
         lib.olap_join_build.restype = i32
         lib.olap_join_build.argtypes = [vp, vp, vp, i32, u64, ctypes.c_double, ctypes.POINTER(vp)]
         lib.olap_join_probe.restype = i32
@@ -396,6 +406,16 @@ class Context:
         names = ["sample", "filter", "refine", "split", "finish", "total", "finish_small", "finish_sort"]
         return {"path": info.path, "refine_passes": info.refine_passes, "candidates": info.candidates,
                 "phase_us": {nm: info.phase_ns[i] / 1e3 for i, nm in enumerate(names)}}
+
+    def time_kernels(self, on: bool = True):
+        """olap_ctx_time_kernels: record CUDA events around each kernel."""
+        self.check(self.lib.olap_ctx_time_kernels(self.h, 1 if on else 0))
+
+    def kernel_ms(self) -> dict:
+        """olap_kernel_ms_last as a dict (milliseconds; -1 = not timed)."""
+        t = olap_kernel_ms()
+        self.check(self.lib.olap_kernel_ms_last(self.h, ctypes.byref(t)))
+        return {nm: getattr(t, nm) for nm, _ in olap_kernel_ms._fields_}
 
     def topk_async(self, d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=None,
                    dev_status=None, stream: int | None = None):

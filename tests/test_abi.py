@@ -55,7 +55,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     (size and field offsets, from a C program compiled against the header)."""
     import subprocess
     structs = {
-        "olap_opts": olap.olap_opts, "olap_topk_info": olap.olap_topk_info,
+        "olap_opts": olap.olap_opts, "olap_topk_info": olap.olap_topk_info, "olap_kernel_ms": olap.olap_kernel_ms,
         "olap_gate_samples": olap.olap_gate_samples, "olap_gate_model": olap.olap_gate_model,
         "olap_gate_query": olap.olap_gate_query, "olap_gate_decision": olap.olap_gate_decision,
         "olap_batch_item": olap.olap_batch_item, "olap_serve_request": olap.olap_serve_request,

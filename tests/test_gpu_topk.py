@@ -217,6 +217,29 @@ def _total_order_i32(bits_u32):
     return x ^ ((x >> 31) & np.int32(0x7FFFFFFF))
 
 
+def test_kernel_timing_events(ctx):
+    # per-kernel CUDA events: each kernel of the sampled path is timed, the
+    # results are unchanged, and the direct path reports no filter kernel
+    keys = datagen.topk_keys(1 << 24, "uniform", "i64", seed=31)
+    dk = torch.from_numpy(keys).cuda()
+    ok = torch.empty(100, dtype=dk.dtype, device="cuda")
+    orow = torch.empty(100, dtype=torch.int32, device="cuda")
+    ctx.time_kernels(True)
+    try:
+        ctx.topk_async(dk, 100, olap.DESC, ok, orow)
+        t = ctx.kernel_ms()
+        assert t["topk_prepare_ms"] > 0 and t["topk_filter_ms"] > 0 and t["topk_select_ms"] > 0
+        assert t["join_probe_ms"] == -1.0
+        wk, wr = oracle.topk(keys, 100, olap.DESC)
+        np.testing.assert_array_equal(orow.cpu().numpy().view(np.uint32), wr)
+        small = dk[:100_000]
+        ctx.topk_async(small, 100, olap.DESC, ok, orow)
+        t = ctx.kernel_ms()
+        assert t["topk_filter_ms"] == -1.0 and t["topk_select_ms"] > 0
+    finally:
+        ctx.time_kernels(False)
+
+
 def test_total_order_key_matches_fixture():
     from tests.test_oracle_topk import f32_specials
     bits, _ = f32_specials()
