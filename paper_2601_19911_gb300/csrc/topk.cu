@@ -2,18 +2,22 @@
 // (Sec. III-A, "partial selection (or radix-based selection)", returning the
 // row pointers of the Top-K rows in order).
 //
-// One cooperative launch runs the whole selection; CTAs meet at bounded grid
-// barriers between phases:
-//   0. (N > 2^21, K small against N) CTA 0 reads a stratified sample of 8192
-//      keys and finds the rank word of the sample's r-th best entry by an
-//      in-register radix select; r is chosen so that, with high probability,
-//      at least K keys but not many more fall at or below it.
-//   1. Filter: the only full pass over the keys.  16-byte streaming loads,
-//      order-preserving transform in registers, and every rank word at or
-//      below the threshold is appended (warp-aggregated) to a candidate
-//      buffer with its row-id.  If the sample misjudged (fewer than K
-//      candidates, or more than the buffer holds) the later phases run on
-//      the full input instead.
+// Three launches on one stream:
+//   0. topk_prepare_kernel (one CTA) zeroes the control block and, when
+//      N > 2^21 and K is small against N, reads a stratified sample of 8192
+//      keys and finds the rank word of the sample's r-th best entry by a
+//      radix select; r is chosen so that, with high probability, at least K
+//      keys but not many more fall at or below it.
+//   1. topk_filter_regs_kernel (default) or topk_filter_bulk_kernel (TMA
+//      bulk copies into a shared-memory ring): the only full pass over the
+//      keys, run only when there is a sample.  16-byte streaming loads, one
+//      compare per key against the threshold in the key's own bit domain,
+//      and every key that passes is appended (per-warp staging, one global
+//      atomic per flush) to a candidate buffer with its row-id.
+//   Phases 2-4 are one cooperative launch (topk_select_kernel) whose CTAs
+//   meet at bounded grid barriers.  Its source is the candidate buffer when
+//   the sample worked (at least K candidates, no overflow) and the full
+//   input otherwise (no sample, or a misjudged one).
 //   2. Refine: radix passes of 12-bit digits over the (key, row-id) composite
 //      of the candidates (or the input): a shared-memory histogram with
 //      __match_any_sync aggregation, merged into a global histogram; every
