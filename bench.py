@@ -506,7 +506,9 @@ def run_ours(args):
     workloads = args.workload.split(",")
     filt = {"bulk": olap.FILTER_BULK, "regs": olap.FILTER_REGS}[args.filter]
     ctx = olap.Context(torch.cuda.current_device(), topk_filter=filt, topk_tile_bytes=args.tile,
-                       topk_stages=args.stages, topk_ctas_per_sm=args.ctas_per_sm)
+                       topk_stages=args.stages, topk_ctas_per_sm=args.ctas_per_sm,
+                       join_partitions=args.join_partitions, join_bucket_loads=args.join_loads,
+                       l2_fetch_bytes=args.l2_fetch)
     keys = datagen.topk_keys(n, args.dist, args.key_type, seed=1)
     w = keys.dtype.itemsize
     dk = torch.from_numpy(keys).cuda()
@@ -640,6 +642,10 @@ def main():
     ap.add_argument("--join-log2p", type=int, default=28)
     ap.add_argument("--join-steps", type=int, default=50)
     ap.add_argument("--join-traffic", type=float, default=None)
+    ap.add_argument("--join-partitions", type=int, default=0,
+                    help="0 automatic, 1 direct probe, 2..256 forced partition count")
+    ap.add_argument("--join-loads", type=int, default=0, help="bucket reads: 0 auto, 1 via L1, 2 L2 only")
+    ap.add_argument("--l2-fetch", type=int, default=0, help="L2 fetch granularity to set (0 = leave)")
     ap.add_argument("--batch-topk", type=int, default=4096)
     ap.add_argument("--batch-probe", type=int, default=1024)
     ap.add_argument("--batch-reps", type=int, default=10)

@@ -75,7 +75,21 @@ typedef struct {
     int topk_tile_bytes;        /* bulk-copy size of the streaming pass (multiple of 8 KiB) */
     int topk_stages;            /* bulk copies in flight per CTA (1..16) */
     int topk_ctas_per_sm;       /* resident CTAs per SM of the Top-K grid (1..4) */
+    int join_partitions;        /* join probe: 0 => automatic (partition the probe rows by
+                                   home bucket when the table is well above L2), 1 => direct
+                                   probe, a power of two 2..256 => that many partitions */
+    int join_bucket_loads;      /* olap_loads: cache path of the probe's bucket reads */
+    int l2_fetch_bytes;         /* 0 => leave the device's L2 fetch granularity; 32, 64 or 128
+                                   => set it (cudaLimitMaxL2FetchGranularity) when the context
+                                   is created; it applies to the whole process on that device */
 } olap_opts;
+
+/* Cache path of the join probe's random bucket reads. */
+typedef enum {
+    OLAP_LOADS_AUTO = 0,        /* the default: L2_ONLY */
+    OLAP_LOADS_L1 = 1,          /* read-only path through L1 (ld.global.nc) */
+    OLAP_LOADS_L2_ONLY = 2      /* bypass L1 (ld.global.cg): no L1 line fills for 32-byte reads */
+} olap_loads;
 
 /* Streaming-pass flavour of Top-K: 16-byte register loads (the default), or
  * bulk asynchronous copies (TMA engine) through a ring of shared-memory

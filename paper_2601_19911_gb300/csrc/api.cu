@@ -73,6 +73,10 @@ olap_status ensure_dev_out(olap_ctx* ctx, size_t bytes) {
     return grow(ctx, &ctx->dev_out, &ctx->dev_out_bytes, bytes, "output staging allocation");
 }
 
+olap_status ensure_part(olap_ctx* ctx, size_t bytes) {
+    return grow(ctx, &ctx->part, &ctx->part_bytes, bytes, "probe partition allocation");
+}
+
 olap_status ensure_pinned(olap_ctx* ctx) {
     if (ctx->pinned[0]) return OLAP_OK;
     const size_t b = ctx->opts.staging_bytes ? ctx->opts.staging_bytes : (64ull << 20);
@@ -231,8 +235,12 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     *out = nullptr;
     olap_ctx* ctx = new olap_ctx();
     if (opts) ctx->opts = *opts;
+    const int jp = ctx->opts.join_partitions;
     if (ctx->opts.load_factor < 0.0 || ctx->opts.load_factor > 0.9 || ctx->opts.topk_filter < 0 ||
-        ctx->opts.topk_filter > OLAP_FILTER_REGS) {
+        ctx->opts.topk_filter > OLAP_FILTER_REGS || jp < 0 || jp > 256 || (jp > 1 && (jp & (jp - 1))) ||
+        ctx->opts.join_bucket_loads < OLAP_LOADS_AUTO || ctx->opts.join_bucket_loads > OLAP_LOADS_L2_ONLY ||
+        (ctx->opts.l2_fetch_bytes != 0 && ctx->opts.l2_fetch_bytes != 32 && ctx->opts.l2_fetch_bytes != 64 &&
+         ctx->opts.l2_fetch_bytes != 128)) {
         delete ctx;
         return OLAP_E_INVALID;
     }
@@ -258,6 +266,13 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     }
     if ((e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device)) != cudaSuccess)
         return bail(e);
+    int l2 = 0;
+    if ((e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device)) != cudaSuccess) return bail(e);
+    ctx->l2_bytes = static_cast<uint64_t>(l2);
+    if (ctx->opts.l2_fetch_bytes &&
+        (e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, static_cast<size_t>(ctx->opts.l2_fetch_bytes))) !=
+            cudaSuccess)
+        return bail(e);
     TopkGeom g;
     if (!topk_geometry(ctx->device, ctx->opts.topk_tile_bytes, ctx->opts.topk_stages,
                        ctx->opts.topk_ctas_per_sm, &g)) {
@@ -280,6 +295,7 @@ void olap_ctx_destroy(olap_ctx* ctx) {
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->dev_in) cudaFree(ctx->dev_in);
     if (ctx->dev_out) cudaFree(ctx->dev_out);
+    if (ctx->part) cudaFree(ctx->part);
     for (int i = 0; i < 2; ++i) {
         if (ctx->pinned[i]) cudaFreeHost(ctx->pinned[i]);
         if (ctx->pinned_ev[i]) cudaEventDestroy(ctx->pinned_ev[i]);

@@ -41,8 +41,7 @@ constexpr uint32_t BT_CAND = 65536;       // candidate capacity per CTA
 constexpr int BT_WS = 128;                // staged hits per warp
 constexpr int BT_BINS = 4096;
 constexpr int BT_SMEM = 2 * BT_SMALL * 12; // two sort areas; also the histogram, stages, probe stage
-constexpr uint64_t BP_ROUNDS = 32;         // probe rounds (JP_TPB * JP_U rows each) per chunk
-constexpr uint64_t BP_CHUNK = BP_ROUNDS * JP_TPB * JP_U;
+constexpr uint64_t BP_CHUNK = 32768;       // probe rows per work unit
 static_assert(JP_STAGE * 8 <= BT_SMEM, "probe stage must fit");
 static_assert((BT_TPB / 32) * BT_WS * 12 <= BT_SMEM, "warp stages must fit");
 
@@ -67,11 +66,11 @@ struct __align__(8) Item {
     int32_t* status;
 };
 
-// One probe work unit: rounds [r0, r1) of probe item `item`.
+// One probe work unit: rows [chunk * BP_CHUNK, (chunk + 1) * BP_CHUNK) of probe
+// item `item` (the last chunk of an item is shorter).
 struct ProbeChunk {
     uint32_t item;
-    uint32_t r0, r1;
-    uint32_t pad;
+    uint32_t chunk;
 };
 
 __device__ __forceinline__ uint64_t item_rank(const Item& it, uint64_t i, uint32_t* rid) {
@@ -417,13 +416,12 @@ __global__ void batch_probe_reset_kernel(const Item* items, uint64_t n_items, in
 }
 
 // Persistent probe executor: each CTA takes the next chunk off the queue and
-// runs its rounds; chunks of items that failed the check are skipped.
+// splits its rows over its warps; chunks of items that failed the check are
+// skipped.
 __global__ void __launch_bounds__(JP_TPB, 3) batch_probe_kernel(const Item* items, const ProbeChunk* chunks,
                                                                 uint64_t n_chunks, unsigned long long* next) {
     extern __shared__ __align__(16) uint2 stage[];
     __shared__ unsigned long long s_item;
-    __shared__ unsigned scount;
-    __shared__ unsigned long long sbase;
     __shared__ ProbeChunk s_ch;
     __shared__ int s_ok;
     __shared__ ProbeArgs s_args;       // kept in shared memory, read as needed
@@ -453,8 +451,12 @@ __global__ void __launch_bounds__(JP_TPB, 3) batch_probe_kernel(const Item* item
         __syncthreads();
         cur = s_ch.item;
         if (s_ok) {
-            const uint64_t end = min(s_args.n, static_cast<uint64_t>(s_ch.r1) * JP_TPB * JP_U);
-            probe_rounds(s_args, s_ch.r0, 1, end, stage, &scount, &sbase);
+            const uint64_t r0 = static_cast<uint64_t>(s_ch.chunk) * BP_CHUNK;
+            const uint64_t r1 = min(s_args.n, r0 + BP_CHUNK);
+            const unsigned warp = threadIdx.x >> 5;
+            uint64_t b, e;
+            warp_share(r0, r1, warp, JP_WARPS, &b, &e);
+            probe_warp<true>(s_args, b, e, stage + warp * JP_WCAP);
         }
         __syncthreads();
     }
@@ -579,15 +581,13 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
         if (sorted[i].op == OLAP_OP_TOPK) ++n_topk;
     }
 
-    // Probe work units: each item cut into chunks of BP_ROUNDS rounds, in the
+    // Probe work units: each item cut into chunks of BP_CHUNK rows, in the
     // items' (largest first) order.
     std::vector<ProbeChunk> chunks;
-    const uint64_t per_round = static_cast<uint64_t>(JP_TPB) * JP_U;
     for (uint64_t i = n_topk; i < n_items; ++i) {
-        const uint64_t rounds = (sorted[i].n + per_round - 1) / per_round;
-        for (uint64_t r = 0; r < rounds; r += BP_ROUNDS)
-            chunks.push_back({static_cast<uint32_t>(i - n_topk), static_cast<uint32_t>(r),
-                              static_cast<uint32_t>(std::min(rounds, r + BP_ROUNDS)), 0u});
+        const uint64_t nch = (sorted[i].n + BP_CHUNK - 1) / BP_CHUNK;
+        for (uint64_t c = 0; c < nch; ++c)
+            chunks.push_back({static_cast<uint32_t>(i - n_topk), static_cast<uint32_t>(c)});
     }
 
     olap_batch* b = new olap_batch();

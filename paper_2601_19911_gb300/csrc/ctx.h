@@ -50,6 +50,12 @@ struct olap_ctx {
     cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool topk_timed = false, probe_timed = false, topk_filtered = false;
 
+    // Partitioned-probe scratch (grow-only): partitioned keys, row-ids and
+    // the per-CTA partition counts.
+    void* part = nullptr;
+    size_t part_bytes = 0;
+    uint64_t l2_bytes = 0;            // device L2 size
+
     // Device memory held by live join tables built through this context.
     uint64_t table_bytes = 0;
     std::set<olap_join_table*> tables;
@@ -69,6 +75,12 @@ olap_status ensure_scratch(olap_ctx* ctx, size_t bytes);
 olap_status ensure_dev_in(olap_ctx* ctx, size_t bytes);
 olap_status ensure_dev_out(olap_ctx* ctx, size_t bytes);
 olap_status ensure_pinned(olap_ctx* ctx);
+olap_status ensure_part(olap_ctx* ctx, size_t bytes);
+
+// Partitions a probe of n rows against table t uses (1 = direct probe), and
+// the partition scratch it needs (0 for a direct probe).
+int probe_parts(const olap_ctx* ctx, const olap_join_table* t, uint64_t n);
+size_t probe_scratch_bytes(const olap_ctx* ctx, const olap_join_table* t, uint64_t n);
 
 // Copy `bytes` from host memory of kind `where` to device `dst` on the
 // context stream; pageable memory goes through the pinned double buffers.

@@ -9,15 +9,27 @@
 // with all bits set; build rows carrying that key value live in a side list.
 // Hash: the 64-bit finalizer of MurmurHash3 (fmix64, A. Appleby).
 //
-// Probe: every thread takes JP_U probe keys per round (coalesced loads),
-// issues their first bucket loads together, then walks the chains in
-// warp-uniform steps.  Matches are appended per warp (one ballot per slot)
-// into a per-CTA shared-memory stage that is flushed to the output in blocks
-// of at least JP_FLUSH pairs with one atomic on the global count.
+// Probe: the rows are split evenly over all warps of the grid.  Each lane
+// runs two independent probe streams and walks their chains one bucket per
+// step; a stream whose chain ends starts its next row at once (its key is
+// already loaded), so lanes do not wait for the longest chain of the warp.
+// Matches are staged per warp in shared memory and appended to the output
+// with one atomic on the global count per flush.
+//
+// Partitioned probe (table much larger than L2, many probe rows): a table
+// larger than L2 turns every probe into a random DRAM sector read.  Instead
+// the probe rows are first radix-partitioned by the top bits of their home
+// bucket into P partitions (a counting pass and a scatter pass, both
+// streaming, with the same CTA-to-tile assignment so every CTA's output
+// ranges come from the count matrix without global atomics), then all CTAs
+// probe partition 0, then 1, ...: the buckets a partition can touch are one
+// 1/P slice of the table, sized to stay resident in L2, so the table is read
+// from DRAM about once.
 #include <algorithm>
 #include <cstring>
 #include <string>
 
+#include "block.cuh"
 #include "ctx.h"
 #include "join_dev.cuh"
 
@@ -64,11 +76,156 @@ __global__ void __launch_bounds__(JB_TPB) join_side_kernel(const int64_t* keys, 
     }
 }
 
+template <bool L2_ONLY>
 __global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs a) {
     extern __shared__ __align__(16) uint2 stage[];
-    __shared__ unsigned scount;
-    __shared__ unsigned long long sbase;
-    probe_rounds(a, blockIdx.x, gridDim.x, a.n, stage, &scount, &sbase);
+    const unsigned warp = threadIdx.x >> 5;
+    uint64_t b, e;
+    warp_share(0, a.n, static_cast<uint64_t>(blockIdx.x) * JP_WARPS + warp,
+               static_cast<uint64_t>(gridDim.x) * JP_WARPS, &b, &e);
+    probe_warp<L2_ONLY>(a, b, e, stage + warp * JP_WCAP);
+}
+
+// ---- partitioned probe ------------------------------------------------------
+
+constexpr int JQ_TPB = 256;
+constexpr int JQ_PER = 8;                      // probe rows per thread per tile
+constexpr int JQ_TILE = JQ_TPB * JQ_PER;       // rows per tile
+constexpr int JQ_PMAX = 256;                   // most partitions
+constexpr int JQ_CTAS_PER_SM = 4;              // grid of the two partition passes
+static_assert(JQ_PMAX <= JQ_TPB, "one scan slot per partition");
+
+struct PartArgs {
+    const int64_t* keys;
+    const uint32_t* rowids;                    // NULL => index
+    uint64_t n;
+    uint64_t mask;                             // buckets - 1
+    int shift;                                 // partition = home bucket >> shift
+    int parts;
+    unsigned long long* cnt;                   // [gridDim.x][parts] rows per CTA and partition
+    unsigned long long* pstart;                // [parts + 1] partition offsets (written by CTA 0)
+    int64_t* out_keys;
+    uint32_t* out_rowids;
+};
+
+__device__ __forceinline__ unsigned part_of(uint64_t key, const PartArgs& a) {
+    return static_cast<unsigned>((fmix64(key) & a.mask) >> a.shift);
+}
+
+// Pass 1: rows of each partition in the tiles of this CTA (tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...).
+__global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs a) {
+    __shared__ unsigned h[JQ_PMAX];
+    for (int p = threadIdx.x; p < a.parts; p += JQ_TPB) h[p] = 0;
+    __syncthreads();
+    for (uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * JQ_TILE; t0 < a.n;
+         t0 += static_cast<uint64_t>(gridDim.x) * JQ_TILE) {
+        uint64_t k[JQ_PER];
+#pragma unroll
+        for (int j = 0; j < JQ_PER; ++j) {
+            const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
+            k[j] = idx < a.n ? ld_stream_u64(a.keys + idx) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < JQ_PER; ++j) {
+            const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
+            if (idx < a.n) atomicAdd(&h[part_of(k[j], a)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < a.parts; p += JQ_TPB)
+        a.cnt[static_cast<uint64_t>(blockIdx.x) * a.parts + p] = h[p];
+}
+
+// Pass 2: the same tiles again; each row goes to its partition at this CTA's
+// running offset (partition start + rows of that partition in lower CTAs +
+// rows already placed), reordered in shared memory so the writes of a
+// partition's run are contiguous.
+__global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
+    __shared__ unsigned h[JQ_PMAX];
+    __shared__ unsigned off[JQ_PMAX];
+    __shared__ unsigned long long base[JQ_PMAX];
+    __shared__ unsigned long long wsum[JQ_TPB / 32];
+    __shared__ unsigned long long total;
+    __shared__ int64_t sk[JQ_TILE];
+    __shared__ uint32_t sr[JQ_TILE];
+    __shared__ uint8_t sp[JQ_TILE];
+    const int p = threadIdx.x;
+    {
+        unsigned long long below = 0, all = 0;
+        if (p < a.parts) {
+            for (unsigned c = 0; c < gridDim.x; ++c) {
+                const unsigned long long v = a.cnt[static_cast<uint64_t>(c) * a.parts + p];
+                all += v;
+                if (c < blockIdx.x) below += v;
+            }
+        }
+        const unsigned long long start = block_excl_scan<JQ_TPB>(all, wsum, &total);
+        if (p < a.parts) base[p] = start + below;
+        if (blockIdx.x == 0 && p < a.parts) a.pstart[p] = start;
+        if (blockIdx.x == 0 && p == 0) a.pstart[a.parts] = total;
+    }
+    for (uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * JQ_TILE; t0 < a.n;
+         t0 += static_cast<uint64_t>(gridDim.x) * JQ_TILE) {
+        if (p < a.parts) h[p] = 0;
+        __syncthreads();
+        uint64_t k[JQ_PER];
+        uint32_t r[JQ_PER];
+        unsigned pp[JQ_PER], rk[JQ_PER];
+#pragma unroll
+        for (int j = 0; j < JQ_PER; ++j) {
+            const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
+            k[j] = idx < a.n ? ld_stream_u64(a.keys + idx) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < JQ_PER; ++j) {
+            const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
+            r[j] = idx < a.n ? (a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx)) : 0u;
+            pp[j] = part_of(k[j], a);
+            rk[j] = idx < a.n ? atomicAdd(&h[pp[j]], 1u) : 0u;
+        }
+        __syncthreads();
+        const unsigned hv = p < a.parts ? h[p] : 0u;
+        const unsigned long long o = block_excl_scan<JQ_TPB>(hv, wsum, &total);
+        if (p < a.parts) off[p] = static_cast<unsigned>(o);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < JQ_PER; ++j) {
+            const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
+            if (idx < a.n) {
+                const unsigned pos = off[pp[j]] + rk[j];
+                sk[pos] = static_cast<int64_t>(k[j]);
+                sr[pos] = r[j];
+                sp[pos] = static_cast<uint8_t>(pp[j]);
+            }
+        }
+        __syncthreads();
+        const unsigned len = static_cast<unsigned>(min(static_cast<uint64_t>(JQ_TILE), a.n - t0));
+        for (unsigned i = threadIdx.x; i < len; i += JQ_TPB) {
+            const unsigned q = sp[i];
+            const unsigned long long dst = base[q] + (i - off[q]);
+            a.out_keys[dst] = sk[i];
+            a.out_rowids[dst] = sr[i];
+        }
+        __syncthreads();
+        if (p < a.parts) base[p] += hv;
+    }
+}
+
+// Pass 3: all CTAs probe partition 0, then 1, ...  `a` points at the
+// partitioned keys and row-ids; partition q is rows [pstart[q], pstart[q+1]).
+template <bool L2_ONLY>
+__global__ void __launch_bounds__(JP_TPB, 4) join_probe_part_kernel(ProbeArgs a, const unsigned long long* pstart,
+                                                                    int parts) {
+    extern __shared__ __align__(16) uint2 stage[];
+    const unsigned warp = threadIdx.x >> 5;
+    const uint64_t w = static_cast<uint64_t>(blockIdx.x) * JP_WARPS + warp;
+    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * JP_WARPS;
+    for (int q = 0; q < parts; ++q) {
+        uint64_t b, e;
+        warp_share(__ldcg(pstart + q), __ldcg(pstart + q + 1), w, warps, &b, &e);
+        probe_warp<L2_ONLY>(a, b, e, stage + warp * JP_WCAP);
+    }
 }
 
 uint64_t next_pow2(uint64_t x) {
@@ -77,22 +234,58 @@ uint64_t next_pow2(uint64_t x) {
     return p;
 }
 
+template <typename K>
+bool probe_kernel_setup(K kernel, int* per_sm) {
+    int per = 0;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, JP_SMEM) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, JP_TPB, JP_SMEM) != cudaSuccess)
+        return false;
+    *per_sm = std::min(*per_sm, per);
+    return true;
+}
+
 int probe_grid(int device) {
     static int cached[64] = {};
     if (device < 0 || device >= 64) return 0;
     if (cached[device]) return cached[device];
-    int sms = 0, per = 0;
+    int sms = 0, per = 1 << 20;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(join_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, JP_SMEM) !=
-        cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, join_probe_kernel, JP_TPB, JP_SMEM) != cudaSuccess)
+    if (!probe_kernel_setup(join_probe_kernel<false>, &per) || !probe_kernel_setup(join_probe_kernel<true>, &per) ||
+        !probe_kernel_setup(join_probe_part_kernel<false>, &per) ||
+        !probe_kernel_setup(join_probe_part_kernel<true>, &per))
         return 0;
     cached[device] = sms * std::max(1, per);
     return cached[device];
 }
 
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
 }  // namespace
+
+// Partitions the probe of `n` rows against `t` uses (1 = direct probe).
+int probe_parts(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
+    const int opt = ctx->opts.join_partitions;
+    uint64_t parts = 1;
+    if (opt >= 2) {
+        parts = static_cast<uint64_t>(opt);
+    } else if (opt == 0) {
+        const uint64_t tb = t->n_buckets * 32;
+        const uint64_t l2 = ctx->l2_bytes ? ctx->l2_bytes : (64ull << 20);
+        // worth it when the table is well above L2 and the probe side reads
+        // at least a quarter as many buckets as the table has
+        if (tb > l2 / 2 && n >= t->n_buckets / 4) parts = next_pow2((tb + l2 / 4 - 1) / (l2 / 4));
+    }
+    parts = std::min<uint64_t>(parts, static_cast<uint64_t>(JQ_PMAX));
+    parts = std::min<uint64_t>(parts, t->n_buckets);
+    return static_cast<int>(std::max<uint64_t>(parts, 1));
+}
+
+size_t probe_scratch_bytes(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
+    const int parts = probe_parts(ctx, t, n);
+    if (parts <= 1) return 0;
+    const uint64_t grid = static_cast<uint64_t>(ctx->sm_count) * JQ_CTAS_PER_SM;
+    return align256(n * 8) + align256(n * 4) + align256(grid * parts * 8) + align256((parts + 1) * 8);
+}
 
 }  // namespace olap
 
@@ -119,10 +312,47 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     a.out = reinterpret_cast<uint2*>(d_out);
     a.cap = capacity;
     a.count = reinterpret_cast<unsigned long long*>(d_count);
+    const int parts = probe_parts(ctx, t, n);
+    PartArgs q{};
+    if (parts > 1) {
+        olap_status st = ensure_part(ctx, probe_scratch_bytes(ctx, t, n));
+        if (st != OLAP_OK) return st;
+        unsigned char* m = static_cast<unsigned char*>(ctx->part);
+        const uint64_t qgrid = static_cast<uint64_t>(ctx->sm_count) * JQ_CTAS_PER_SM;
+        q.keys = d_keys;
+        q.rowids = d_rowids;
+        q.n = n;
+        q.mask = a.mask;
+        q.shift = 0;
+        while ((t->n_buckets >> q.shift) > static_cast<uint64_t>(parts)) ++q.shift;
+        q.parts = parts;
+        q.out_keys = reinterpret_cast<int64_t*>(m);
+        q.out_rowids = reinterpret_cast<uint32_t*>(m + align256(n * 8));
+        q.cnt = reinterpret_cast<unsigned long long*>(m + align256(n * 8) + align256(n * 4));
+        q.pstart = q.cnt + qgrid * parts;
+        if (q.pstart + parts + 1 > reinterpret_cast<unsigned long long*>(m + ctx->part_bytes))
+            return fail(ctx, OLAP_E_INVALID, "probe partition scratch too small");
+    }
     ctx->probe_timed = ctx->time_kernels;
     if (ctx->time_kernels && (e = cudaEventRecord(ctx->kev[4], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "timing event");
-    join_probe_kernel<<<grid, JP_TPB, JP_SMEM, s>>>(a);
+    if (parts > 1) {
+        const unsigned qgrid = static_cast<unsigned>(ctx->sm_count * JQ_CTAS_PER_SM);
+        join_part_count_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
+        join_part_scatter_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
+        ProbeArgs pa = a;
+        pa.keys = q.out_keys;
+        pa.rowids = q.out_rowids;
+        if (ctx->opts.join_bucket_loads == OLAP_LOADS_L1)
+            join_probe_part_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(pa, q.pstart, parts);
+        else
+            join_probe_part_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(pa, q.pstart, parts);
+    } else {
+        if (ctx->opts.join_bucket_loads == OLAP_LOADS_L1)
+            join_probe_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(a);
+        else
+            join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(a);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess && ctx->time_kernels) e = cudaEventRecord(ctx->kev[5], s);
     return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "probe launch");
@@ -155,6 +385,7 @@ olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* 
 
     const uint64_t want_slots = static_cast<uint64_t>(static_cast<double>(n) / load) + 2;
     const uint64_t buckets = next_pow2((want_slots + 1) / 2);
+    if (buckets > (1ull << 32)) return fail(ctx, OLAP_E_NOMEM, "join table: more than 2^32 buckets");
     const size_t slot_bytes = buckets * 32;
     const size_t bytes = slot_bytes + 256;
     if (!within_budget(ctx, bytes)) return fail(ctx, OLAP_E_NOMEM, "join table: device memory budget exceeded");

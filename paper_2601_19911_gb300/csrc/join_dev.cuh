@@ -24,11 +24,7 @@ namespace olap {
 constexpr uint64_t JN_EMPTY = ~0ull;
 constexpr int JB_TPB = 256;
 constexpr int JP_TPB = 256;
-constexpr int JP_U = 4;
-constexpr int JP_STAGE = 6144;    // pairs staged per CTA (48 KB)
-constexpr int JP_FLUSH = 2048;    // flush once this many are staged; a round adds at most
-                                  // JP_TPB * JP_U * 2 per chain step, and the stage spills
-                                  // to direct global appends if a round overfills it
+constexpr int JP_STAGE = 6144;    // pairs staged per CTA (48 KB), split evenly over its warps
 constexpr int JP_SMEM = JP_STAGE * 8;
 
 struct JoinCtl {
@@ -66,109 +62,153 @@ struct ProbeArgs {
     unsigned long long* count;
 };
 
-// Place one pair at stage position pos, or append it to the output directly
-// once the stage is full.
-__device__ __forceinline__ void put_pair(const ProbeArgs& a, uint2* stage, unsigned pos, uint2 p) {
-    if (pos < JP_STAGE) {
-        stage[pos] = p;
-    } else {
-        const unsigned long long g = atomicAdd(a.count, 1ull);
-        if (g < a.cap) a.out[g] = p;
-    }
+// One 32-byte bucket {key0, row-id0 | pad, key1, row-id1 | pad} in a single
+// 256-bit load; L2_ONLY bypasses L1 (ld.global.cg), else the read-only path
+// through L1 (ld.global.nc).
+struct Bucket {
+    uint64_t k0, w0, k1, w1;          // w: row-id in the low 32 bits
+};
+
+template <bool L2_ONLY>
+__device__ __forceinline__ Bucket ld_bucket(const ulonglong2* slots, uint32_t b) {
+    const ulonglong2* p = slots + static_cast<uint64_t>(b) * 2;
+    Bucket v;
+    if (L2_ONLY)
+        asm("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(v.k0), "=l"(v.w0), "=l"(v.k1), "=l"(v.w1) : "l"(p));
+    else
+        asm("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(v.k0), "=l"(v.w0), "=l"(v.k1), "=l"(v.w1) : "l"(p));
+    return v;
 }
 
-// Warp-aggregated append of up to two pairs per lane (all lanes call).
-__device__ __forceinline__ void warp_emit2(const ProbeArgs& a, uint2* stage, unsigned* scount, bool m0, uint2 p0,
-                                           bool m1, uint2 p1) {
-    const unsigned b0 = __ballot_sync(0xFFFFFFFFu, m0);
-    const unsigned b1 = __ballot_sync(0xFFFFFFFFu, m1);
-    const unsigned tot = __popc(b0) + __popc(b1);
-    if (tot == 0) return;
+constexpr int JP_S = 2;                                 // independent probe streams per lane
+constexpr int JP_WARPS = JP_TPB / 32;
+constexpr unsigned JP_WCAP = JP_STAGE / JP_WARPS;         // staged pairs per warp
+
+// Copy a warp's staged pairs to the output with one atomic on the global
+// count (whole warp calls; cnt is warp-uniform).
+__device__ __forceinline__ void warp_flush(const ProbeArgs& a, uint2* ws, unsigned& cnt) {
+    if (cnt == 0) return;
+    __syncwarp();
     const unsigned lane = threadIdx.x & 31u;
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(scount, tot);
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    const unsigned lt = (1u << lane) - 1u;
-    if (m0) put_pair(a, stage, base + __popc(b0 & lt), p0);
-    if (m1) put_pair(a, stage, base + __popc(b0) + __popc(b1 & lt), p1);
+    unsigned long long g = 0;
+    if (lane == 0) g = atomicAdd(a.count, static_cast<unsigned long long>(cnt));
+    g = __shfl_sync(0xFFFFFFFFu, g, 0);
+    for (unsigned i = lane; i < cnt; i += 32)
+        if (g + i < a.cap) a.out[g + i] = ws[i];
+    __syncwarp();
+    cnt = 0;
 }
 
-// Copy the staged pairs to the output (whole CTA; call between barriers).
-__device__ __forceinline__ void flush_stage(const ProbeArgs& a, uint2* stage, unsigned* scount,
-                                            unsigned long long* sbase) {
-    const unsigned c = min(*reinterpret_cast<volatile unsigned*>(scount), static_cast<unsigned>(JP_STAGE));
-    if (threadIdx.x == 0) *sbase = c ? atomicAdd(a.count, static_cast<unsigned long long>(c)) : 0ull;
-    __syncthreads();
-    const unsigned long long base = *sbase;
-    for (unsigned i = threadIdx.x; i < c; i += JP_TPB) {
-        const unsigned long long g = base + i;
-        if (g < a.cap) a.out[g] = stage[i];
+// Stage one pair for every lane where m is set (whole warp calls).
+__device__ __forceinline__ void warp_put(const ProbeArgs& a, uint2* ws, unsigned& cnt, bool m, uint2 p) {
+    const unsigned b = __ballot_sync(0xFFFFFFFFu, m);
+    if (b == 0) return;
+    if (cnt + 32 > JP_WCAP) warp_flush(a, ws, cnt);
+    const unsigned lane = threadIdx.x & 31u;
+    if (m) ws[cnt + __popc(b & ((1u << lane) - 1u))] = p;
+    cnt += __popc(b);
+}
+
+// One warp probes the rows [begin, end).  Each lane runs JP_S independent
+// streams; stream s of lane L takes rows begin + L + 32*s, then every
+// 32*JP_S-th row after it.  A stream walks its chain one bucket per step;
+// when the chain ends it starts its next row at once (the key and row-id of
+// that row are already loaded), so every lane keeps bucket loads in flight
+// however uneven the chain lengths are.  Matches go to the warp's own stage
+// `ws` (JP_WCAP pairs), flushed to the output whenever it could overflow and
+// before returning.
+template <bool L2_ONLY>
+__device__ __forceinline__ void probe_warp(const ProbeArgs& a, uint64_t begin, uint64_t end, uint2* ws) {
+    constexpr uint64_t STEP = 32ull * JP_S;
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t mask = static_cast<uint32_t>(a.mask);
+    unsigned cnt = 0;
+    uint64_t key[JP_S], pkey[JP_S], nxt[JP_S];
+    uint32_t rid[JP_S], prid[JP_S], bk[JP_S];
+    bool live[JP_S], plive[JP_S];
+    Bucket v[JP_S];
+#pragma unroll
+    for (int s = 0; s < JP_S; ++s) {
+        const uint64_t i = begin + lane + 32ull * s;
+        live[s] = i < end;
+        key[s] = live[s] ? ld_stream_u64(a.keys + i) : JN_EMPTY;
+        rid[s] = live[s] ? (a.rowids ? a.rowids[i] : static_cast<uint32_t>(i)) : 0u;
+        nxt[s] = i + STEP;
+        plive[s] = nxt[s] < end;
+        pkey[s] = plive[s] ? ld_stream_u64(a.keys + nxt[s]) : JN_EMPTY;
+        prid[s] = plive[s] ? (a.rowids ? a.rowids[nxt[s]] : static_cast<uint32_t>(nxt[s])) : 0u;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) *scount = 0;
-    __syncthreads();
-}
-
-// Probe rounds first, first + step, ... of JP_TPB * JP_U keys each by one CTA
-// (whole CTA calls), over probe rows below `end` (at most a.n), staging pairs
-// in `stage` (JP_STAGE entries) and flushing them to the output; everything
-// staged is flushed before returning.
-__device__ __forceinline__ void probe_rounds(const ProbeArgs& a, uint64_t first, uint64_t step, uint64_t end,
-                                             uint2* stage, unsigned* scount_p, unsigned long long* sbase_p) {
-    unsigned& scount = *scount_p;
-    if (threadIdx.x == 0) scount = 0;
-    __syncthreads();
-    const uint64_t per = static_cast<uint64_t>(JP_TPB) * JP_U;
-    for (uint64_t base = first * per; base < end; base += step * per) {
-        uint64_t k[JP_U], bk[JP_U];
-        uint32_t prid[JP_U];
-        bool act[JP_U];
-        ulonglong2 x0[JP_U], x1[JP_U];
 #pragma unroll
-        for (int j = 0; j < JP_U; ++j) {
-            const uint64_t idx = base + static_cast<uint64_t>(j) * JP_TPB + threadIdx.x;
-            const bool v = idx < end;
-            k[j] = v ? ld_stream_u64(a.keys + idx) : JN_EMPTY;
-            prid[j] = v ? (a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx)) : 0u;
-            act[j] = v && k[j] != JN_EMPTY;
-            // Probe keys equal to the empty marker pair with the side list.
-            if (v && k[j] == JN_EMPTY)
-                for (uint64_t o = 0; o < a.n_side; ++o)
-                    put_pair(a, stage, atomicAdd(&scount, 1u), make_uint2(prid[j], a.side[o]));
-        }
+    for (int s = 0; s < JP_S; ++s) {
+        bk[s] = static_cast<uint32_t>(fmix64(key[s])) & mask;
+        if (live[s] && key[s] != JN_EMPTY)
+            v[s] = ld_bucket<L2_ONLY>(a.slots, bk[s]);
+        else
+            v[s] = Bucket{JN_EMPTY, 0, JN_EMPTY, 0};
+    }
+    while (true) {
+        bool any = false;
 #pragma unroll
-        for (int j = 0; j < JP_U; ++j) {
-            bk[j] = act[j] ? (fmix64(k[j]) & a.mask) : 0;
-            if (act[j]) {
-                x0[j] = __ldg(a.slots + bk[j] * 2);
-                x1[j] = __ldg(a.slots + bk[j] * 2 + 1);
-            } else {
-                x0[j] = make_ulonglong2(JN_EMPTY, 0);
-                x1[j] = make_ulonglong2(JN_EMPTY, 0);
-            }
-        }
+        for (int s = 0; s < JP_S; ++s) any = any || live[s];
+        if (!__any_sync(0xFFFFFFFFu, any)) break;
+        // Probe keys equal to the empty marker pair with every side-list row;
+        // the warp emits them together, one such key at a time (rare).
 #pragma unroll
-        for (int j = 0; j < JP_U; ++j) {
-            bool on = act[j];
-            while (__any_sync(0xFFFFFFFFu, on)) {
-                const bool m0 = on && x0[j].x == k[j];
-                const bool m1 = on && x1[j].x == k[j];
-                warp_emit2(a, stage, &scount, m0, make_uint2(prid[j], static_cast<uint32_t>(x0[j].y)), m1,
-                           make_uint2(prid[j], static_cast<uint32_t>(x1[j].y)));
-                on = on && x0[j].x != JN_EMPTY && x1[j].x != JN_EMPTY;
-                if (on) {
-                    bk[j] = (bk[j] + 1) & a.mask;
-                    x0[j] = __ldg(a.slots + bk[j] * 2);
-                    x1[j] = __ldg(a.slots + bk[j] * 2 + 1);
+        for (int s = 0; s < JP_S; ++s) {
+            unsigned sb = __ballot_sync(0xFFFFFFFFu, live[s] && key[s] == JN_EMPTY);
+            while (sb) {
+                const int src = __ffs(sb) - 1;
+                sb &= sb - 1;
+                const uint32_t r = __shfl_sync(0xFFFFFFFFu, rid[s], src);
+                for (uint64_t o0 = 0; o0 < a.n_side; o0 += 32) {
+                    const bool m = o0 + lane < a.n_side;
+                    warp_put(a, ws, cnt, m, make_uint2(r, m ? a.side[o0 + lane] : 0u));
                 }
             }
         }
-        __syncthreads();
-        if (*reinterpret_cast<volatile unsigned*>(&scount) >= static_cast<unsigned>(JP_FLUSH))
-            flush_stage(a, stage, &scount, sbase_p);
+        // Matches in the current bucket of every stream.
+#pragma unroll
+        for (int s = 0; s < JP_S; ++s) {
+            const bool real = live[s] && key[s] != JN_EMPTY;
+            warp_put(a, ws, cnt, real && v[s].k0 == key[s], make_uint2(rid[s], static_cast<uint32_t>(v[s].w0)));
+            warp_put(a, ws, cnt, real && v[s].k1 == key[s], make_uint2(rid[s], static_cast<uint32_t>(v[s].w1)));
+        }
+        // Next bucket of the chain, or the stream's next row.
+#pragma unroll
+        for (int s = 0; s < JP_S; ++s) {
+            if (!live[s]) continue;
+            if (key[s] != JN_EMPTY && v[s].k0 != JN_EMPTY && v[s].k1 != JN_EMPTY) {
+                bk[s] = (bk[s] + 1u) & mask;
+            } else {
+                live[s] = plive[s];
+                key[s] = pkey[s];
+                rid[s] = prid[s];
+                if (!live[s]) continue;
+                bk[s] = static_cast<uint32_t>(fmix64(key[s])) & mask;
+                nxt[s] += STEP;
+                plive[s] = nxt[s] < end;
+                if (plive[s]) {
+                    pkey[s] = ld_stream_u64(a.keys + nxt[s]);
+                    prid[s] = a.rowids ? a.rowids[nxt[s]] : static_cast<uint32_t>(nxt[s]);
+                }
+                if (key[s] == JN_EMPTY) {
+                    v[s] = Bucket{JN_EMPTY, 0, JN_EMPTY, 0};
+                    continue;
+                }
+            }
+            v[s] = ld_bucket<L2_ONLY>(a.slots, bk[s]);
+        }
     }
-    __syncthreads();
-    flush_stage(a, stage, &scount, sbase_p);
+    warp_flush(a, ws, cnt);
+}
+
+// Rows [begin, end) split evenly over `warps` warps; this warp's share.
+__device__ __forceinline__ void warp_share(uint64_t begin, uint64_t end, uint64_t w, uint64_t warps, uint64_t* b,
+                                           uint64_t* e) {
+    const uint64_t len = end - begin;
+    const uint64_t per = (len + warps - 1) / warps;
+    *b = begin + min(len, w * per);
+    *e = begin + min(len, (w + 1) * per);
 }
 
 }  // namespace olap

@@ -31,15 +31,17 @@ double ms_since(Clock::time_point t0) {
 }
 
 // Device bytes one GPU request holds while it runs: its key-only input, the
-// selection scratch or the pair output, and its result staging.
-uint64_t device_need(const olap_serve_request& r) {
+// selection scratch or the pair output (and probe partitions), and its result
+// staging.  `ctx` (any slot context, all alike) decides the probe mode.
+uint64_t device_need(const olap_serve_request& r, const olap_ctx* ctx) {
     const uint64_t rid = r.rowids ? 4 * r.n : 0;
     if (r.op == OLAP_OP_TOPK) {
         const uint64_t w = r.key_type == OLAP_KEY_F32 ? 4 : 8;
         const uint64_t kk = std::min(r.k, r.n);
         return r.n * w + rid + olap::topk_scratch_bytes(olap::topk_plan(r.n, kk), kk) + kk * (w + 4) + 4096;
     }
-    return r.n * 8 + rid + r.capacity * 8 + 4096;
+    const uint64_t part = ctx && r.table ? olap::probe_scratch_bytes(ctx, r.table, r.n) : 0;
+    return r.n * 8 + rid + r.capacity * 8 + part + 4096;
 }
 
 bool decide_gpu(const olap_serve_request& r, const olap_serve_opts& o) {
@@ -166,28 +168,6 @@ extern "C" olap_status olap_serve(olap_serve_request* reqs, uint64_t n, const ol
     std::iota(order.begin(), order.end(), 0ull);
     std::stable_sort(order.begin(), order.end(),
                      [&](uint64_t a, uint64_t b) { return reqs[a].arrival_ms < reqs[b].arrival_ms; });
-    // Per-request device need, and the largest buffers a slot can be asked for,
-    // so no slot allocates (and synchronises the device) while serving.
-    uint64_t max_in = 0, max_out = 0, max_scratch = 0;
-    for (uint64_t i = 0; i < n; ++i) {
-        olap_serve_request& r = reqs[i];
-        r.status = OLAP_E_INVALID;
-        r.out_count = 0;
-        r.on_gpu = 0;
-        r.start_ms = r.done_ms = 0.0;
-        S.need[i] = device_need(r);
-        const uint64_t rid = r.rowids ? 4 * r.n : 0;
-        if (r.op == OLAP_OP_TOPK) {
-            const uint64_t w = r.key_type == OLAP_KEY_F32 ? 4 : 8;
-            const uint64_t kk = std::min(r.k, r.n);
-            max_in = std::max<uint64_t>(max_in, ((r.n * w + 255) & ~255ull) + rid);
-            max_out = std::max<uint64_t>(max_out, ((kk * w + 255) & ~255ull) + kk * 4);
-            max_scratch = std::max<uint64_t>(max_scratch, olap::topk_scratch_bytes(olap::topk_plan(r.n, kk), kk));
-        } else {
-            max_in = std::max<uint64_t>(max_in, ((r.n * 8 + 255) & ~255ull) + rid);
-            max_out = std::max<uint64_t>(max_out, ((r.capacity * 8 + 255) & ~255ull) + 256);
-        }
-    }
     std::vector<olap_ctx*> ctxs;
     auto cleanup = [&]() {
         for (olap_ctx* c : ctxs) olap_ctx_destroy(c);
@@ -201,14 +181,41 @@ extern "C" olap_status olap_serve(olap_serve_request* reqs, uint64_t n, const ol
                 return st;
             }
             ctxs.push_back(c);
-            if ((st = olap::ensure_dev_in(c, max_in)) != OLAP_OK || (st = olap::ensure_dev_out(c, max_out)) != OLAP_OK ||
-                (st = olap::ensure_scratch(c, std::max<uint64_t>(max_scratch, 4096))) != OLAP_OK ||
-                (st = olap::ensure_pinned(c)) != OLAP_OK) {
-                cleanup();
-                return st;
-            }
-            cudaStreamSynchronize(c->stream);
         }
+    }
+    // Per-request device need, and the largest buffers a slot can be asked for,
+    // so no slot allocates (and synchronises the device) while serving.
+    uint64_t max_in = 0, max_out = 0, max_scratch = 0, max_part = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        olap_serve_request& r = reqs[i];
+        r.status = OLAP_E_INVALID;
+        r.out_count = 0;
+        r.on_gpu = 0;
+        r.start_ms = r.done_ms = 0.0;
+        S.need[i] = device_need(r, ctxs.empty() ? nullptr : ctxs[0]);
+        const uint64_t rid = r.rowids ? 4 * r.n : 0;
+        if (r.op == OLAP_OP_TOPK) {
+            const uint64_t w = r.key_type == OLAP_KEY_F32 ? 4 : 8;
+            const uint64_t kk = std::min(r.k, r.n);
+            max_in = std::max<uint64_t>(max_in, ((r.n * w + 255) & ~255ull) + rid);
+            max_out = std::max<uint64_t>(max_out, ((kk * w + 255) & ~255ull) + kk * 4);
+            max_scratch = std::max<uint64_t>(max_scratch, olap::topk_scratch_bytes(olap::topk_plan(r.n, kk), kk));
+        } else {
+            max_in = std::max<uint64_t>(max_in, ((r.n * 8 + 255) & ~255ull) + rid);
+            max_out = std::max<uint64_t>(max_out, ((r.capacity * 8 + 255) & ~255ull) + 256);
+            if (!ctxs.empty() && r.table)
+                max_part = std::max<uint64_t>(max_part, olap::probe_scratch_bytes(ctxs[0], r.table, r.n));
+        }
+    }
+    for (olap_ctx* c : ctxs) {
+        olap_status st;
+        if ((st = olap::ensure_dev_in(c, max_in)) != OLAP_OK || (st = olap::ensure_dev_out(c, max_out)) != OLAP_OK ||
+            (st = olap::ensure_scratch(c, std::max<uint64_t>(max_scratch, 4096))) != OLAP_OK ||
+            (max_part && (st = olap::ensure_part(c, max_part)) != OLAP_OK) || (st = olap::ensure_pinned(c)) != OLAP_OK) {
+            cleanup();
+            return st;
+        }
+        cudaStreamSynchronize(c->stream);
     }
     std::vector<std::thread> threads;
     S.t0 = Clock::now();

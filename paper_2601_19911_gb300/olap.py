@@ -39,6 +39,7 @@ OP_TOPK, OP_PROBE = 0, 1
 CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
 FIT_ORDINARY, FIT_RELATIVE = 0, 1
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
+LOADS_AUTO, LOADS_L1, LOADS_L2_ONLY = 0, 1, 2
 NOALLOC_MAX_N = 1 << 24
 NOALLOC_MAX_K = 4096
 
@@ -62,6 +63,9 @@ class olap_opts(ctypes.Structure):
         ("topk_tile_bytes", ctypes.c_int),
         ("topk_stages", ctypes.c_int),
         ("topk_ctas_per_sm", ctypes.c_int),
+        ("join_partitions", ctypes.c_int),
+        ("join_bucket_loads", ctypes.c_int),
+        ("l2_fetch_bytes", ctypes.c_int),
     ]
 
 
@@ -285,10 +289,12 @@ class Context:
     def __init__(self, device: int = 0, stream: int | None = None, mem_budget_bytes: int = 0,
                  margin_ms: float = 0.0, load_factor: float = 0.0, staging_bytes: int = 0,
                  topk_filter: int = FILTER_AUTO, topk_tile_bytes: int = 0, topk_stages: int = 0,
-                 topk_ctas_per_sm: int = 0):
+                 topk_ctas_per_sm: int = 0, join_partitions: int = 0, join_bucket_loads: int = 0,
+                 l2_fetch_bytes: int = 0):
         self.lib = load()
         opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, 0, load_factor, staging_bytes,
-                         topk_filter, topk_tile_bytes, topk_stages, topk_ctas_per_sm)
+                         topk_filter, topk_tile_bytes, topk_stages, topk_ctas_per_sm, join_partitions,
+                         join_bucket_loads, l2_fetch_bytes)
         h = ctypes.c_void_p()
         st = self.lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h))
         if st != OK:

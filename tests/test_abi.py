@@ -43,6 +43,17 @@ def test_no_cpu_fallback_without_gpu(lib):
     assert ei.value.status == olap.E_CUDA
 
 
+@pytest.mark.parametrize("field,value", [("join_partitions", 3), ("join_partitions", 512), ("join_partitions", -1),
+                                         ("load_factor", 0.95), ("topk_filter", 7), ("join_bucket_loads", 3),
+                                         ("l2_fetch_bytes", 48)])
+def test_bad_options_are_rejected_before_any_device_call(lib, field, value):
+    opts = olap.olap_opts()
+    setattr(opts, field, value)
+    h = ctypes.c_void_p()
+    assert lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h)) == olap.E_INVALID
+    assert not h.value
+
+
 def test_null_context_is_rejected(lib):
     got = ctypes.c_uint64()
     assert lib.olap_topk(None, None, 0, None, 0, 0, 0, 0, None, None, 0, ctypes.byref(got)) == olap.E_INVALID

@@ -141,9 +141,68 @@ def test_golden_fixtures(ctx):
         t.free()
 
 
+@pytest.fixture(scope="module")
+def part_ctxs():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    cs = {p: olap.Context(0, join_partitions=p) for p in (2, 8, 64, 256)}
+    yield cs
+    for c in cs.values():
+        c.close()
+
+
+@pytest.mark.parametrize("parts", [2, 8, 64, 256])
+@pytest.mark.parametrize("mult,dist,hit", [("unique", "uniform", 0.9), ("mult14", "zipf", 0.5)])
+def test_partitioned_probe_matches_oracle(part_ctxs, parts, mult, dist, hit):
+    """The radix-partitioned probe, forced on: same pair multiset as the oracle
+    for every partition count (a table of 2^17 buckets, chains that cross
+    partition boundaries, a ragged last tile)."""
+    c = part_ctxs[parts]
+    b = datagen.join_build(100_003, mult, seed=21)
+    p = datagen.join_probe(700_001, b, hit, dist, seed=21)
+    cnt = _check(c, b.keys, p.keys)
+    assert cnt == p.expected_pairs(b)
+
+
+def test_partitioned_probe_edges(part_ctxs):
+    c = part_ctxs[64]
+    # fewer probe rows than partitions, one row, none; explicit row-ids; the
+    # empty-marker key on both sides; a build smaller than the partition count
+    rng = np.random.default_rng(22)
+    alphabet = np.array([I64_MIN, I64_MAX, 0, -1, 1, -2], dtype=np.int64)
+    bk = alphabet[rng.integers(0, len(alphabet), 3000)]
+    for npr in (0, 1, 5, 63, 64, 65, 2049, 50_000):
+        pk = alphabet[rng.integers(0, len(alphabet), npr)]
+        _check(c, bk, pk)
+    _check(c, np.array([5, -1, 5], dtype=np.int64), np.array([5, -1, 7, 5], dtype=np.int64))
+    b = datagen.join_build(40_000, "mult14", seed=23)
+    p = datagen.join_probe(300_000, b, 0.7, "zipf", seed=23)
+    br = (datagen.splitmix64(3, b.keys.shape[0]) >> np.uint64(33)).astype(np.uint32)
+    pr = (datagen.splitmix64(4, p.keys.shape[0]) >> np.uint64(33)).astype(np.uint32)
+    _check(c, b.keys, p.keys, br, pr)
+    _check(c, b.keys, p.keys, br, pr, device=False)       # host memory in and out
+
+
+@pytest.mark.parametrize("loads", [olap.LOADS_L1, olap.LOADS_L2_ONLY])
+@pytest.mark.parametrize("parts", [1, 16])
+def test_bucket_load_paths(loads, parts):
+    """Both cache paths of the 256-bit bucket reads, direct and partitioned."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0, join_partitions=parts, join_bucket_loads=loads)
+    try:
+        b = datagen.join_build(150_000, "mult14", seed=24)
+        p = datagen.join_probe(500_000, b, 0.8, "zipf", seed=24)
+        assert _check(c, b.keys, p.keys) == p.expected_pairs(b)
+        _check(c, np.array([-1, 3, -1], dtype=np.int64), np.array([-1, 3, 4, -1], dtype=np.int64))
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("mult,dist,hit", [("mult14", "zipf", 0.9), ("unique", "uniform", 0.1)])
 def test_full_size(ctx, mult, dist, hit):
-    """2^24 build rows, 2^28 probe keys, device resident (the benchmark's call)."""
+    """2^24 build rows, 2^28 probe keys, device resident (the benchmark's call;
+    the table is 8x L2, so the automatic mode takes the partitioned probe)."""
     b = datagen.join_build(1 << 24, mult, seed=2)
     p = datagen.join_probe(1 << 28, b, hit, dist, seed=2)
     need = p.expected_pairs(b)
