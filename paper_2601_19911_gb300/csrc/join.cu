@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs a) {
 // Pass 2: the same tiles again; each row goes to its partition at this CTA's
 // running offset (partition start + rows of that partition in lower CTAs +
 // rows already placed), reordered in shared memory so the writes of a
-// partition's run are contiguous.
+// partition's run are contiguous.  The keys of the CTA's next tile are loaded
+// while the current one is reordered.
 __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
     __shared__ unsigned h[JQ_PMAX];
     __shared__ unsigned off[JQ_PMAX];
@@ -165,24 +166,29 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
         if (blockIdx.x == 0 && p < a.parts) a.pstart[p] = start;
         if (blockIdx.x == 0 && p == 0) a.pstart[a.parts] = total;
     }
-    for (uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * JQ_TILE; t0 < a.n;
-         t0 += static_cast<uint64_t>(gridDim.x) * JQ_TILE) {
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * JQ_TILE;
+    uint64_t kc[JQ_PER];
+    const uint64_t first = static_cast<uint64_t>(blockIdx.x) * JQ_TILE;
+#pragma unroll
+    for (int j = 0; j < JQ_PER; ++j) {
+        const uint64_t idx = first + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
+        kc[j] = idx < a.n ? ld_stream_u64(a.keys + idx) : 0ull;
+    }
+    for (uint64_t t0 = first; t0 < a.n; t0 += stride) {
+        uint64_t kn[JQ_PER];
+#pragma unroll
+        for (int j = 0; j < JQ_PER; ++j) {
+            const uint64_t idx = t0 + stride + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
+            kn[j] = idx < a.n ? ld_stream_u64(a.keys + idx) : 0ull;
+        }
         if (p < a.parts) h[p] = 0;
         __syncthreads();
-        uint64_t k[JQ_PER];
-        uint32_t r[JQ_PER];
-        unsigned pp[JQ_PER], rk[JQ_PER];
+        unsigned pr[JQ_PER];                   // partition | rank in the tile << 8
 #pragma unroll
         for (int j = 0; j < JQ_PER; ++j) {
             const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
-            k[j] = idx < a.n ? ld_stream_u64(a.keys + idx) : 0ull;
-        }
-#pragma unroll
-        for (int j = 0; j < JQ_PER; ++j) {
-            const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
-            r[j] = idx < a.n ? (a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx)) : 0u;
-            pp[j] = part_of(k[j], a);
-            rk[j] = idx < a.n ? atomicAdd(&h[pp[j]], 1u) : 0u;
+            const unsigned q = part_of(kc[j], a);
+            pr[j] = idx < a.n ? (q | (atomicAdd(&h[q], 1u) << 8)) : 0u;
         }
         __syncthreads();
         const unsigned hv = p < a.parts ? h[p] : 0u;
@@ -193,10 +199,11 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
         for (int j = 0; j < JQ_PER; ++j) {
             const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
             if (idx < a.n) {
-                const unsigned pos = off[pp[j]] + rk[j];
-                sk[pos] = static_cast<int64_t>(k[j]);
-                sr[pos] = r[j];
-                sp[pos] = static_cast<uint8_t>(pp[j]);
+                const unsigned q = pr[j] & 0xFFu;
+                const unsigned pos = off[q] + (pr[j] >> 8);
+                sk[pos] = static_cast<int64_t>(kc[j]);
+                sr[pos] = a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx);
+                sp[pos] = static_cast<uint8_t>(q);
             }
         }
         __syncthreads();
@@ -209,6 +216,8 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
         }
         __syncthreads();
         if (p < a.parts) base[p] += hv;
+#pragma unroll
+        for (int j = 0; j < JQ_PER; ++j) kc[j] = kn[j];
     }
 }
 
