@@ -280,8 +280,15 @@ def batched_leg(args, ctx, torch):
     implicit row-ids) and 1024 probe batches (n ~ logU[1e3, 1e6)) against one
     resident 2^22-key unique table (hit rate 0.5), all device resident: one
     graph launch of the persistent executor against one library call per
-    query on one stream."""
+    query on one stream, both on a context whose digit width, filter block
+    size and load factor the autotuner picked."""
     from paper_2601_19911_gb300 import datagen, olap
+    # autotuned digit width, filter block size and load factor, on a context
+    # of its own: a 2^20-key Top-K (the large queries dominate the batch) and
+    # the batch's table shape
+    ctx = olap.Context(torch.cuda.current_device())
+    tune = ctx.autotune(topk_n=1 << 20, topk_k=500, join_build_n=1 << 22, join_probe_n=1 << 20,
+                        join_hit_rate=0.5, reps=5)
     ns, ks = datagen.batched_topk_queries(args.batch_topk, 1e3, 4e6, 1000, seed=3)
     offs = np.concatenate([[0], np.cumsum(ns)])
     keys = datagen.splitmix64_torch(datagen.stream_seed(3, 0), int(offs[-1]), device="cuda")
@@ -335,6 +342,7 @@ def batched_leg(args, ctx, torch):
     algo = float(offs[-1]) * 8 + float(ks.sum()) * 24 + float(poffs[-1]) * 40 + float(hits[-1]) * 8
     batch.free()
     table.free()
+    ctx.close()
     return {"metric": "batched vs per-query speedup", "value": ms_per_query / ms_graph, "unit": "x",
             "graph_ms": ms_graph, "per_query_ms": ms_per_query, "device_errors": errors, "all_ok": ok,
             "items": {"topk": args.batch_topk, "probe": args.batch_probe, "topk_keys": int(offs[-1]),
@@ -343,7 +351,8 @@ def batched_leg(args, ctx, torch):
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": algo / (ms_graph * 1e-3) / 1e9 / peak,
                          "bytes": "8 per Top-K key + 24 per selected row + 40 per probe + 8 per pair"},
-            "gpu_launches_graph": (1 if args.batch_topk else 0) + (2 if args.batch_probe else 0), "clocks": clk.summary()}
+            "gpu_launches_graph": (1 if args.batch_topk else 0) + (2 if args.batch_probe else 0),
+            "autotune": tune, "clocks": clk.summary()}
 
 
 def _median_ms(fn, reps=3):

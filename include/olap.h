@@ -68,7 +68,8 @@ typedef struct {
     void* stream;               /* cudaStream_t to run on; NULL => the context creates one */
     uint64_t mem_budget_bytes;  /* cap on device scratch + tables held by the context */
     double margin_ms;           /* gate margin (Sec. IV, gate margin 0/5/10 ms) */
-    int block_threads;          /* threads per CTA for streaming kernels (256/512/1024) */
+    int block_threads;          /* threads per CTA of the Top-K streaming filter (256/512/1024;
+                                   0 => 512) */
     double load_factor;         /* join table load factor in (0, 0.9]; 0 => 0.5 */
     uint64_t staging_bytes;     /* size of each pinned staging buffer; 0 => 64 MiB */
     int topk_filter;            /* olap_filter: how the Top-K streaming pass reads keys */
@@ -82,6 +83,8 @@ typedef struct {
     int l2_fetch_bytes;         /* 0 => leave the device's L2 fetch granularity; 32, 64 or 128
                                    => set it (cudaLimitMaxL2FetchGranularity) when the context
                                    is created; it applies to the whole process on that device */
+    int topk_digit_bits;        /* radix digit width of the Top-K selects (8..12; 0 => 12), also
+                                   for batches created on this context */
 } olap_opts;
 
 /* Cache path of the join probe's random bucket reads. */
@@ -167,6 +170,50 @@ typedef struct {
 /* Times of the last timed Top-K and join probe on this context (waits for
  * them); -1 for a kernel that was not timed. */
 olap_status olap_kernel_ms_last(olap_ctx* ctx, olap_kernel_ms* out);
+
+/* ------------------------------------------------------------------------
+ * Autotuner.  The paper fixes no kernel parameters; this picks them by
+ * measurement on the caller's shape: the Top-K streaming-filter block size
+ * (256/512/1024) and radix digit width (8/10/11/12 bits), and the join's load
+ * factor (0.25/0.35/0.5/0.7), probe mode (automatic partitioning or direct)
+ * and bucket-read cache path.  Candidates run on tuning inputs the library
+ * generates on the device (uniform keys; probe rows hitting the build side
+ * with the given rate); each is timed with CUDA events on the context
+ * stream, the median of `reps` runs after one untimed run.  On success the
+ * context keeps the fastest configuration (block_threads, topk_digit_bits,
+ * load_factor, join_partitions, join_bucket_loads of its options); batches
+ * created afterwards use its digit width.  Blocking.  Errors: E_INVALID for
+ * bad sizes (each below 2^32) or probe rows without build rows; E_NOMEM when
+ * no join candidate fits the budget; E_CUDA.  Device memory for the tuning
+ * inputs is allocated and freed inside the call.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    uint64_t topk_n;                 /* keys of the Top-K shape (0 => leave Top-K as is) */
+    int topk_key_type;               /* olap_key_type */
+    int reps;                        /* timed runs per candidate (0 => 5) */
+    uint64_t topk_k;
+    uint64_t join_build_n;           /* build rows of the join shape (0 => leave the join as is) */
+    uint64_t join_probe_n;           /* probe rows */
+    double join_hit_rate;            /* fraction of probe rows that find a build key */
+    uint64_t seed;                   /* of the tuning inputs */
+} olap_tune_request;
+
+typedef struct {
+    int block_threads;               /* chosen Top-K filter block size */
+    int topk_digit_bits;             /* chosen radix digit width */
+    double topk_ms;                  /* median Top-K time with the choice */
+    double topk_default_ms;          /* median Top-K time with 512 threads, 12-bit digits */
+    double load_factor;              /* chosen join load factor */
+    int join_partitions;             /* 0 automatic, 1 direct */
+    int join_bucket_loads;           /* olap_loads */
+    double join_probe_ms;            /* median probe time with the choice */
+    double join_probe_default_ms;    /* load 0.5, automatic partitioning, L2-only reads */
+    double join_build_ms;            /* build time at the chosen load factor */
+    int candidates;                  /* configurations timed */
+    int pad;
+} olap_tune_result;
+
+olap_status olap_autotune(olap_ctx* ctx, const olap_tune_request* req, olap_tune_result* out);
 
 /* ------------------------------------------------------------------------
  * Key-based hash join, build and probe (Sec. III-B: "parallel probing using a

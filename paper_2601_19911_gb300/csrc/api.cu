@@ -199,6 +199,7 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
     a.out_rowids = d_out_rowids;
     a.dev_status = dev_status;
     a.filter = ctx->opts.topk_filter == OLAP_FILTER_BULK ? TK_FILTER_BULK : TK_FILTER_REGS;
+    a.digit = ctx->opts.topk_digit_bits ? ctx->opts.topk_digit_bits : TK_DIG;
     ctx->last_topk_ctl = a.ctl;
     ctx->topk_timed = ctx->time_kernels;
     ctx->topk_filtered = plan.use_sample;
@@ -239,6 +240,9 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     if (ctx->opts.load_factor < 0.0 || ctx->opts.load_factor > 0.9 || ctx->opts.topk_filter < 0 ||
         ctx->opts.topk_filter > OLAP_FILTER_REGS || jp < 0 || jp > 256 || (jp > 1 && (jp & (jp - 1))) ||
         ctx->opts.join_bucket_loads < OLAP_LOADS_AUTO || ctx->opts.join_bucket_loads > OLAP_LOADS_L2_ONLY ||
+        (ctx->opts.topk_digit_bits != 0 && (ctx->opts.topk_digit_bits < 8 || ctx->opts.topk_digit_bits > 12)) ||
+        (ctx->opts.block_threads != 0 && ctx->opts.block_threads != 256 && ctx->opts.block_threads != 512 &&
+         ctx->opts.block_threads != 1024) ||
         (ctx->opts.l2_fetch_bytes != 0 && ctx->opts.l2_fetch_bytes != 32 && ctx->opts.l2_fetch_bytes != 64 &&
          ctx->opts.l2_fetch_bytes != 128)) {
         delete ctx;
@@ -275,7 +279,7 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
         return bail(e);
     TopkGeom g;
     if (!topk_geometry(ctx->device, ctx->opts.topk_tile_bytes, ctx->opts.topk_stages,
-                       ctx->opts.topk_ctas_per_sm, &g)) {
+                       ctx->opts.topk_ctas_per_sm, ctx->opts.block_threads, &g)) {
         cudaGetLastError();
         olap_ctx_destroy(ctx);
         return OLAP_E_INVALID;

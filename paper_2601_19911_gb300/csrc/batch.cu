@@ -87,9 +87,10 @@ __device__ __forceinline__ void put_result(const Item& it, uint64_t i, uint64_t 
     it.out_rowids[i] = rid;
 }
 
-// Threshold rank word from a stratified sample: 12-bit radix select with the
+// Threshold rank word from a stratified sample: radix select (digit bits) with the
 // early exit of the grid version (between r and r + 8 samples at or below).
-__device__ uint64_t cta_sample_threshold(const Item& it, unsigned r, unsigned* hist, unsigned long long* sc) {
+__device__ uint64_t cta_sample_threshold(const Item& it, unsigned r, unsigned* hist, unsigned long long* sc,
+                                         int digit) {
     uint64_t s[BT_SPT];
 #pragma unroll
     for (int j = 0; j < BT_SPT; ++j) {
@@ -101,8 +102,8 @@ __device__ uint64_t cta_sample_threshold(const Item& it, unsigned r, unsigned* h
     const int kb = it.f32 ? 32 : 64;
     uint64_t prefix = 0;
     unsigned long long rem = r, cum = 0;
-    for (int L = 0; L < kb; L += 12) {
-        const int d = min(12, kb - L);
+    for (int L = 0; L < kb; L += digit) {
+        const int d = min(digit, kb - L);
         for (int b = threadIdx.x; b < BT_BINS; b += BT_TPB) hist[b] = 0;
         __syncthreads();
 #pragma unroll
@@ -233,7 +234,7 @@ __device__ __forceinline__ void src_get(const Item& it, bool cand, const uint64_
 
 // Top-K of one item by one CTA.
 __device__ void cta_topk(const Item& it, unsigned char* smem, uint64_t* cand_r, uint32_t* cand_rid,
-                         unsigned long long* sc, unsigned* s_misc) {
+                         unsigned long long* sc, unsigned* s_misc, int digit) {
     const uint64_t n = it.n;
     const uint64_t kk = it.k < n ? it.k : n;
     if (kk == 0) {
@@ -260,7 +261,7 @@ __device__ void cta_topk(const Item& it, unsigned char* smem, uint64_t* cand_r, 
         const double lam = static_cast<double>(kk) * BT_SAMPLE / static_cast<double>(n);
         unsigned r = static_cast<unsigned>(ceil(lam + 4.0 * sqrt(lam))) + 3u;
         if (r > BT_SAMPLE) r = BT_SAMPLE;
-        const uint64_t t = cta_sample_threshold(it, r, hist, sc);
+        const uint64_t t = cta_sample_threshold(it, r, hist, sc, digit);
         __syncthreads();
         const unsigned c = it.f32 ? cta_filter<true>(it, t, smem, cand_r, cand_rid, &s_misc[0])
                                   : cta_filter<false>(it, t, smem, cand_r, cand_rid, &s_misc[0]);
@@ -275,7 +276,7 @@ __device__ void cta_topk(const Item& it, unsigned char* smem, uint64_t* cand_r, 
     uint64_t p0 = 0, p1 = 0, krem = kk, bcnt = src_n;
     const unsigned lane = threadIdx.x & 31u;
     while (bcnt > BT_SMALL && L < TB && krem < bcnt) {
-        const int d = min(12, TB - L);
+        const int d = min(digit, TB - L);
         for (int b = threadIdx.x; b < BT_BINS; b += BT_TPB) hist[b] = 0;
         __syncthreads();
         for (uint64_t wb = threadIdx.x & ~31u; wb < src_n; wb += BT_TPB) {
@@ -375,7 +376,7 @@ __device__ int item_check(const Item& it) {
 // Persistent Top-K executor: each CTA takes the next Top-K item off the queue.
 __global__ void __launch_bounds__(BT_TPB, 2) batch_topk_kernel(const Item* items, uint64_t n_items,
                                                                unsigned long long* next, uint64_t* cand_r_all,
-                                                               uint32_t* cand_rid_all, int* errors) {
+                                                               uint32_t* cand_rid_all, int* errors, int digit) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long sc[24];
     __shared__ unsigned s_misc[4];
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(BT_TPB, 2) batch_topk_kernel(const Item* items
         __syncthreads();
         const Item& it = s_it;
         const int st = it.op == OLAP_OP_TOPK ? item_check(it) : static_cast<int>(OLAP_E_DEVICE);
-        if (st == OLAP_OK) cta_topk(it, smem, cand_r, cand_rid, sc, s_misc);
+        if (st == OLAP_OK) cta_topk(it, smem, cand_r, cand_rid, sc, s_misc, digit);
         __syncthreads();
         if (threadIdx.x == 0) {
             if (it.status) *it.status = st;
@@ -480,6 +481,7 @@ struct olap_batch {
     uint64_t* cand_r = nullptr;
     uint32_t* cand_rid = nullptr;
     int grid_topk = 0, grid_probe = 0;
+    int digit = 12;                       // radix digit width of the per-CTA Top-K
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -492,7 +494,7 @@ olap_status enqueue_batch(olap_batch* b, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "batch reset");
     if (b->n_topk)
         batch_topk_kernel<<<b->grid_topk, BT_TPB, BT_SMEM, s>>>(b->d_items, b->n_topk, b->d_next, b->cand_r,
-                                                                b->cand_rid, b->d_errors);
+                                                                b->cand_rid, b->d_errors, b->digit);
     if (b->n_probe) {
         const Item* probe_items = b->d_items + b->n_topk;
         batch_probe_reset_kernel<<<static_cast<unsigned>((b->n_probe + 255) / 256), 256, 0, s>>>(
@@ -592,6 +594,7 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
 
     olap_batch* b = new olap_batch();
     b->ctx = ctx;
+    b->digit = ctx->opts.topk_digit_bits ? ctx->opts.topk_digit_bits : 12;
     b->n_chunks = chunks.size();
     b->items.assign(items, items + n_items);
     b->n_topk = n_topk;

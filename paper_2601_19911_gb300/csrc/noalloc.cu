@@ -56,7 +56,7 @@ olap_status setup_device(int dev, DeviceSetup* out) {
             return OLAP_E_CUDA;
         }
         olap::TopkGeom g;
-        if (!olap::topk_geometry(dev, 0, 0, 0, &g)) {
+        if (!olap::topk_geometry(dev, 0, 0, 0, 0, &g)) {
             cudaGetLastError();
             return OLAP_E_CUDA;
         }

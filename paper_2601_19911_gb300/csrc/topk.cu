@@ -67,7 +67,7 @@ __device__ __forceinline__ void write_result(const TopkArgs& a, uint64_t i, uint
 }
 
 // Prepare kernel: a threshold rank word for the streaming pass from a
-// stratified sample of TK_SAMPLE keys.  Radix select with 12-bit digits on the
+// stratified sample of TK_SAMPLE keys.  Radix select with a.digit-bit digits on the
 // sample held in registers; it stops as soon as the upper edge of the chosen
 // bucket has between r and r + 8 samples at or below it (any such threshold
 // serves), which for spread-out keys is after the first digit.
@@ -84,8 +84,8 @@ __device__ uint64_t sample_threshold(const TopkArgs& a, unsigned* sh, unsigned l
     const unsigned long long r = a.sample_rank;
     uint64_t prefix = 0;
     unsigned long long rem = r, cum = 0;
-    for (int L = 0; L < kb; L += TK_DIG) {
-        const int d = min(TK_DIG, kb - L);
+    for (int L = 0; L < kb; L += a.digit) {
+        const int d = min(a.digit, kb - L);
         for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB) sh[b] = 0;
         __syncthreads();
 #pragma unroll
@@ -512,12 +512,13 @@ __global__ void __launch_bounds__(TKF_TPB, 4) topk_filter_bulk_kernel(TopkArgs a
     filter_pass_bulk<F32, TKF_TPB>(a, t, fsmem);
 }
 
-// Kernel 2 of 3, register-load flavour.
-template <bool F32>
-__global__ void __launch_bounds__(TKR_TPB) topk_filter_regs_kernel(TopkArgs a) {
-    __shared__ __align__(16) unsigned char stage[(TKR_TPB / 32) * WS_BYTES];
+// Kernel 2 of 3, register-load flavour (TPB threads; the per-warp stages are
+// dynamic shared memory, (TPB / 32) * WS_BYTES).
+template <bool F32, int TPB>
+__global__ void __launch_bounds__(TPB) topk_filter_regs_kernel(TopkArgs a) {
+    extern __shared__ __align__(16) unsigned char stage[];
     const uint64_t t = __ldcg(&a.ctl->thresh);
-    filter_pass<F32, TKR_TPB>(a, t, stage);
+    filter_pass<F32, TPB>(a, t, stage);
 }
 
 // Kernel 3 of 3 (cooperative): refine, split, finish and sort.
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
         L = lz < kb ? lz : kb;
     }
     while (bcnt > TK_SMALL && L < TB && krem < bcnt) {
-        const int d = min(TK_DIG, TB - L);
+        const int d = min(a.digit, TB - L);
         unsigned* gh = a.ghist + (pass % 3) * TK_BINS;
         unsigned* gz = a.ghist + ((pass + 1) % 3) * TK_BINS;
         hist_pass(a, cand, src_n, p0, p1, L, d, kb, gh, gz, sh);
@@ -667,7 +668,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
         const int L0 = cand ? (__clzll(static_cast<long long>(__ldcg(&ctl->thresh))) < kb
                                    ? __clzll(static_cast<long long>(__ldcg(&ctl->thresh))) : kb)
                             : 0;
-        const int dp = min(TK_DIG, TB - L0);
+        const int dp = min(a.digit, TB - L0);
         unsigned* ph = a.ghist + (pass % 3) * TK_BINS;          // clean (zeroed by the last pass or prepare)
         unsigned* pc = a.ghist + ((pass + 1) % 3) * TK_BINS;    // cursors, zeroed here
         for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB) sh[b] = 0;
@@ -946,6 +947,10 @@ static bool set_kernel_attrs(int device) {
                              lim) != cudaSuccess ||
         cudaFuncSetAttribute(topk_filter_bulk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              lim) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_regs_kernel<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             32 * WS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_regs_kernel<true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             32 * WS_BYTES) != cudaSuccess ||
         cudaFuncSetAttribute(topk_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TK_SORT_SMEM) != cudaSuccess)
         return false;
@@ -953,8 +958,10 @@ static bool set_kernel_attrs(int device) {
     return true;
 }
 
-bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, TopkGeom* out) {
+bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, int regs_tpb, TopkGeom* out) {
     TopkGeom g;
+    g.regs_tpb = regs_tpb ? regs_tpb : TKR_TPB;
+    if (g.regs_tpb != 256 && g.regs_tpb != 512 && g.regs_tpb != 1024) return false;
     g.tile_bytes = tile_bytes ? tile_bytes : TK_TILE_DEFAULT;
     g.stages = stages ? stages : TK_STAGES_DEFAULT;
     g.ctas_per_sm = ctas_per_sm ? ctas_per_sm : TK_CTAS_PER_SM_DEFAULT;
@@ -974,10 +981,16 @@ bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, Topk
     per_sm = std::min(per_sm, g.ctas_per_sm);
     if (per_sm < 1) return false;
     g.filter_grid = sms * per_sm;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_filter_regs_kernel<false>, TKR_TPB, 0) !=
-        cudaSuccess)
-        return false;
-    g.regs_grid = sms * std::max(1, std::min(per_sm, 2048 / TKR_TPB));
+    cudaError_t oe;
+    const size_t rs = static_cast<size_t>(g.regs_tpb / 32) * WS_BYTES;
+    if (g.regs_tpb == 256)
+        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_filter_regs_kernel<false, 256>, 256, rs);
+    else if (g.regs_tpb == 512)
+        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_filter_regs_kernel<false, 512>, 512, rs);
+    else
+        oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_filter_regs_kernel<false, 1024>, 1024, rs);
+    if (oe != cudaSuccess) return false;
+    g.regs_grid = sms * std::max(1, std::min(per_sm, 2048 / g.regs_tpb));
     // Cooperative select kernel: every CTA resident, two per SM at most.
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_select_kernel, TK_TPB, TK_SORT_SMEM) !=
         cudaSuccess)
@@ -993,6 +1006,8 @@ cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t
     TopkArgs a = args;
     a.tile_bytes = geom.tile_bytes;
     a.stages = geom.stages;
+    if (a.digit == 0) a.digit = TK_DIG;
+    if (a.digit < TK_DIG_MIN || a.digit > TK_DIG) return cudaErrorInvalidValue;
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
     topk_prepare_kernel<<<1, TK_TPB, 0, stream>>>(a);
@@ -1001,8 +1016,18 @@ cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t
     if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
     if (a.use_sample) {
         if (a.filter == TK_FILTER_REGS) {
-            if (a.f32) topk_filter_regs_kernel<true><<<geom.regs_grid, TKR_TPB, 0, stream>>>(a);
-            else topk_filter_regs_kernel<false><<<geom.regs_grid, TKR_TPB, 0, stream>>>(a);
+            const size_t rs = static_cast<size_t>(geom.regs_tpb / 32) * WS_BYTES;
+            const unsigned gr = static_cast<unsigned>(geom.regs_grid);
+            if (geom.regs_tpb == 256) {
+                if (a.f32) topk_filter_regs_kernel<true, 256><<<gr, 256, rs, stream>>>(a);
+                else topk_filter_regs_kernel<false, 256><<<gr, 256, rs, stream>>>(a);
+            } else if (geom.regs_tpb == 1024) {
+                if (a.f32) topk_filter_regs_kernel<true, 1024><<<gr, 1024, rs, stream>>>(a);
+                else topk_filter_regs_kernel<false, 1024><<<gr, 1024, rs, stream>>>(a);
+            } else {
+                if (a.f32) topk_filter_regs_kernel<true, 512><<<gr, 512, rs, stream>>>(a);
+                else topk_filter_regs_kernel<false, 512><<<gr, 512, rs, stream>>>(a);
+            }
         } else {
             if (a.f32)
                 topk_filter_bulk_kernel<true><<<geom.filter_grid, TKF_TPB, geom.smem_bytes, stream>>>(a);

@@ -9,7 +9,8 @@
 namespace olap {
 
 constexpr int TK_TPB = 512;               // threads per CTA
-constexpr int TK_DIG = 12;                // radix digit width of the refine passes
+constexpr int TK_DIG = 12;                // default radix digit width (8..12; histograms hold 2^12 bins)
+constexpr int TK_DIG_MIN = 8;
 constexpr int TK_BINS = 1 << TK_DIG;
 constexpr int TK_SMALL = 4096;            // entries one CTA sorts in shared memory
 constexpr int TK_SAMPLE = 8192;           // sample size of the threshold estimate
@@ -22,7 +23,7 @@ constexpr int TK_MAX_STAGES = 16;         // full + empty mbarrier pairs reserve
 constexpr int TK_SMEM_MAX = 227 * 1024;   // opt-in shared memory per CTA
 // The streaming filter runs as its own kernel: 256-thread CTAs, several per
 // SM, each with a ring of bulk copies (default 16 KB x 3, four CTAs per SM);
-// the register-load flavour uses 512-thread CTAs.
+// the register-load flavour uses CTAs of 256, 512 (default) or 1024 threads.
 constexpr int TKF_TPB = 256;
 constexpr int TKR_TPB = 512;
 constexpr int TK_TILE_DEFAULT = 16384;
@@ -60,6 +61,7 @@ struct TopkArgs {
     int use_sample;
     unsigned sample_rank;            // 1-based rank of the threshold in the sample
     int filter;                      // TopkFilter
+    int digit;                       // radix digit width, TK_DIG_MIN..TK_DIG (0 => TK_DIG)
     int tile_bytes;                  // bulk-copy size (multiple of 16 * TK_TPB)
     int stages;                      // copies in flight per CTA (<= TK_MAX_STAGES)
     TopkCtl* ctl;
@@ -103,10 +105,12 @@ struct TopkGeom {
     int grid;              // cooperative select kernel CTAs
     int filter_grid;       // bulk-copy filter CTAs
     int regs_grid;         // register-load filter CTAs
+    int regs_tpb;          // register-load filter threads per CTA (256, 512, 1024)
 };
-// Fill in the geometry for the requested ring on `device`; 0 values take the
-// defaults.  Returns false if the ring does not fit or no CTA fits.
-bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, TopkGeom* out);
+// Fill in the geometry for the requested ring and register-filter block size
+// on `device`; 0 values take the defaults.  Returns false if the ring does not
+// fit, the block size is not one of 256/512/1024, or no CTA fits.
+bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, int regs_tpb, TopkGeom* out);
 
 // Enqueue one Top-K: prepare (1 CTA), the streaming filter when the sampled
 // path is taken, then the cooperative select kernel.  Returns the first CUDA

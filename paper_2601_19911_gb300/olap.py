@@ -28,7 +28,7 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
-    "olap_ctx_time_kernels", "olap_kernel_ms_last",
+    "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_autotune",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
     "olap_batch_create", "olap_batch_run", "olap_batch_run_per_query", "olap_batch_errors", "olap_batch_free",
@@ -66,6 +66,7 @@ class olap_opts(ctypes.Structure):
         ("join_partitions", ctypes.c_int),
         ("join_bucket_loads", ctypes.c_int),
         ("l2_fetch_bytes", ctypes.c_int),
+        ("topk_digit_bits", ctypes.c_int),
     ]
 
 
@@ -140,6 +141,20 @@ class olap_topk_info(ctypes.Structure):
     ]
 
 
+class olap_tune_request(ctypes.Structure):
+    _fields_ = [("topk_n", ctypes.c_uint64), ("topk_key_type", ctypes.c_int), ("reps", ctypes.c_int),
+                ("topk_k", ctypes.c_uint64), ("join_build_n", ctypes.c_uint64), ("join_probe_n", ctypes.c_uint64),
+                ("join_hit_rate", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class olap_tune_result(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int), ("topk_digit_bits", ctypes.c_int), ("topk_ms", ctypes.c_double),
+                ("topk_default_ms", ctypes.c_double), ("load_factor", ctypes.c_double),
+                ("join_partitions", ctypes.c_int), ("join_bucket_loads", ctypes.c_int),
+                ("join_probe_ms", ctypes.c_double), ("join_probe_default_ms", ctypes.c_double),
+                ("join_build_ms", ctypes.c_double), ("candidates", ctypes.c_int), ("pad", ctypes.c_int)]
+
+
 class olap_kernel_ms(ctypes.Structure):
     _fields_ = [(nm, ctypes.c_float) for nm in
                 ("topk_prepare_ms", "topk_filter_ms", "topk_select_ms", "join_probe_ms")]
@@ -180,6 +195,8 @@ def load(path: str | None = None):
         lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         lib.olap_topk_info_last.restype = i32
         lib.olap_topk_info_last.argtypes = [vp, ctypes.POINTER(olap_topk_info)]
+        lib.olap_autotune.restype = i32
+        lib.olap_autotune.argtypes = [vp, ctypes.POINTER(olap_tune_request), ctypes.POINTER(olap_tune_result)]
         lib.olap_ctx_time_kernels.restype = i32
         lib.olap_ctx_time_kernels.argtypes = [vp, i32]
         lib.olap_kernel_ms_last.restype = i32
@@ -290,11 +307,11 @@ class Context:
                  margin_ms: float = 0.0, load_factor: float = 0.0, staging_bytes: int = 0,
                  topk_filter: int = FILTER_AUTO, topk_tile_bytes: int = 0, topk_stages: int = 0,
                  topk_ctas_per_sm: int = 0, join_partitions: int = 0, join_bucket_loads: int = 0,
-                 l2_fetch_bytes: int = 0):
+                 l2_fetch_bytes: int = 0, topk_digit_bits: int = 0, block_threads: int = 0):
         self.lib = load()
-        opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, 0, load_factor, staging_bytes,
+        opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, block_threads, load_factor, staging_bytes,
                          topk_filter, topk_tile_bytes, topk_stages, topk_ctas_per_sm, join_partitions,
-                         join_bucket_loads, l2_fetch_bytes)
+                         join_bucket_loads, l2_fetch_bytes, topk_digit_bits)
         h = ctypes.c_void_p()
         st = self.lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h))
         if st != OK:
@@ -412,6 +429,15 @@ class Context:
         names = ["sample", "filter", "refine", "split", "finish", "total", "finish_small", "finish_sort"]
         return {"path": info.path, "refine_passes": info.refine_passes, "candidates": info.candidates,
                 "phase_us": {nm: info.phase_ns[i] / 1e3 for i, nm in enumerate(names)}}
+
+    def autotune(self, topk_n: int = 0, topk_k: int = 100, key_type: int = KEY_I64, join_build_n: int = 0,
+                 join_probe_n: int = 0, join_hit_rate: float = 0.5, reps: int = 5, seed: int = 7) -> dict:
+        """olap_autotune: time candidate configurations on this shape and keep
+        the fastest in this context; returns the olap_tune_result as a dict."""
+        req = olap_tune_request(topk_n, key_type, reps, topk_k, join_build_n, join_probe_n, join_hit_rate, seed)
+        res = olap_tune_result()
+        self.check(self.lib.olap_autotune(self.h, ctypes.byref(req), ctypes.byref(res)))
+        return {nm: getattr(res, nm) for nm, _ in olap_tune_result._fields_ if nm != "pad"}
 
     def time_kernels(self, on: bool = True):
         """olap_ctx_time_kernels: record CUDA events around each kernel."""

@@ -45,7 +45,8 @@ def test_no_cpu_fallback_without_gpu(lib):
 
 @pytest.mark.parametrize("field,value", [("join_partitions", 3), ("join_partitions", 512), ("join_partitions", -1),
                                          ("load_factor", 0.95), ("topk_filter", 7), ("join_bucket_loads", 3),
-                                         ("l2_fetch_bytes", 48)])
+                                         ("l2_fetch_bytes", 48), ("topk_digit_bits", 7), ("topk_digit_bits", 13),
+                                         ("block_threads", 384)])
 def test_bad_options_are_rejected_before_any_device_call(lib, field, value):
     opts = olap.olap_opts()
     setattr(opts, field, value)
@@ -67,6 +68,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     import subprocess
     structs = {
         "olap_opts": olap.olap_opts, "olap_topk_info": olap.olap_topk_info, "olap_kernel_ms": olap.olap_kernel_ms,
+        "olap_tune_request": olap.olap_tune_request, "olap_tune_result": olap.olap_tune_result,
         "olap_gate_samples": olap.olap_gate_samples, "olap_gate_model": olap.olap_gate_model,
         "olap_gate_query": olap.olap_gate_query, "olap_gate_decision": olap.olap_gate_decision,
         "olap_batch_item": olap.olap_batch_item, "olap_serve_request": olap.olap_serve_request,
