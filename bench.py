@@ -364,6 +364,115 @@ def _median_ms(fn, reps=3):
     return float(np.median(ts))
 
 
+def _crossover(ns, gain):
+    """Smallest N where the measured gain (ms) turns positive and stays so,
+    interpolated in log N between the two grid points around the sign change;
+    0 if it never turns positive, ns[0] if it is positive everywhere."""
+    pos = [g > 0.0 for g in gain]
+    if all(pos):
+        return float(ns[0])
+    if not pos[-1]:
+        return 0.0
+    i = max(j for j in range(len(pos)) if not pos[j])
+    g0, g1 = gain[i], gain[i + 1]
+    x0, x1 = np.log(ns[i]), np.log(ns[i + 1])
+    return float(np.exp(x0 + (x1 - x0) * (-g0) / (g1 - g0)))
+
+
+def gate_leg(args, ctx, torch):
+    """Risky Gate validation (Sec. V-D break-even, Sec. IV gate margin):
+    Top-K (K = 100, int64) and probe (against a resident 2^22-key table, hit
+    rate 0.9) over a log-spaced N grid from 1e3 to 1e8, keys in pageable host
+    memory.  At each N the host engine's time and the GPU path's end-to-end
+    time (key-only transfer, kernel, result return) are measured; the gate is
+    calibrated from the odd grid points (measured component times, 1/y^2
+    weights); its break-even N* for margins 0, 5 and 10 ms is compared with
+    the measured crossover (interpolated in log N over the whole grid), and
+    the offload decision at every grid point is reported per margin."""
+    from paper_2601_19911_gb300 import datagen, olap
+    ns = np.unique(np.floor(np.logspace(3, 8, args.gate_points)).astype(np.int64))
+    A = int(ns[-1])
+    host = olap.HostEngine(threads=args.serve_cpu_workers)
+    arena = datagen.topk_keys(A, "uniform", "i64", seed=5)
+    b = datagen.join_build(1 << 22, "unique", seed=5)
+    table = ctx.join_build(b.keys)
+    host.add_table(b.keys)
+    p = datagen.join_probe(A, b, 0.9, "uniform", seed=5)
+    cum = np.concatenate([[0], np.cumsum(p.hit)])
+    dev = torch.from_numpy(arena).cuda()
+    kk = 100
+    rows = {olap.OP_TOPK: [], olap.OP_PROBE: []}
+    for n in (int(x) for x in ns):
+        keys = arena[:n]
+        ok = np.empty(kk, dtype=np.int64)
+        orow = np.empty(kk, dtype=np.uint32)
+        req = olap.olap_serve_request(olap.OP_TOPK, olap.KEY_I64, olap.DESC, 0, keys.ctypes.data, None, n, kk,
+                                      None, 0.0, 0.0, ok.ctypes.data, orow.ctypes.data, None, 0)
+        t_cpu = _median_ms(lambda: host.run(req), args.gate_reps)
+        dok = torch.empty(kk, dtype=torch.int64, device="cuda")
+        dor = torch.empty(kk, dtype=torch.int32, device="cuda")
+        t_in = _median_ms(lambda: ctx.topk(keys, kk, olap.DESC, out_keys=dok, out_rowids=dor), args.gate_reps)
+        t_all = _median_ms(lambda: ctx.topk(keys, kk, olap.DESC, out_keys=ok, out_rowids=orow), args.gate_reps)
+
+        def kern():
+            ctx.topk_async(dev[:n], kk, olap.DESC, dok, dor)
+            ctx.sync()
+        t_ker = _median_ms(kern, args.gate_reps)
+        rows[olap.OP_TOPK].append((n, kk, 8.0 * n, min(kk, n), t_cpu, max(t_in - t_ker, 0.0), t_ker,
+                                   max(t_all - t_in, 0.0), t_all))
+        pk = p.keys[:n]
+        need = int(cum[n])
+        out = np.empty((need + 64, 2), dtype=np.uint32)
+        preq = olap.olap_serve_request(olap.OP_PROBE, olap.KEY_I64, 0, 0, pk.ctypes.data, None, n, 0,
+                                       table.h.value, float(need), 0.0, None, None, out.ctypes.data, need + 64)
+        t_cpu = _median_ms(lambda: host.run(preq), args.gate_reps)
+        dout = torch.empty((need + 64, 2), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        t_in = _median_ms(lambda: ctx.join_probe(table, pk, out=dout), args.gate_reps)
+        t_all = _median_ms(lambda: ctx.join_probe(table, pk, out=out), args.gate_reps)
+        dpk = torch.from_numpy(pk).cuda()
+
+        def pkern():
+            ctx.join_probe_async(table, dpk, dout, need + 64, cnt)
+            ctx.sync()
+        t_ker = _median_ms(pkern, args.gate_reps)
+        del dpk
+        rows[olap.OP_PROBE].append((n, 1.0 + need / n, 8.0 * n, need, t_cpu, max(t_in - t_ker, 0.0), t_ker,
+                                    max(t_all - t_in, 0.0), t_all))
+    del dev
+    table.free()
+    host.close()
+    torch.cuda.empty_cache()
+    result = {}
+    for op, name in ((olap.OP_TOPK, "topk_k100"), (olap.OP_PROBE, "probe_hit0.9")):
+        r = rows[op]
+        cal = r[1::2]                                          # calibration points
+        cols = list(zip(*[x[:8] for x in cal]))
+        gn = [x[0] for x in r]
+        per_margin = {}
+        for margin in (0.0, 5.0, 10.0):
+            m = olap.gate_calibrate(op, *cols, margin_ms=margin, weighting=olap.FIT_RELATIVE)
+            if op == olap.OP_TOPK:
+                nstar = olap.gate_estimate(m, op, 1 << 20, kk, 8.0 * (1 << 20), kk, 8.0).n_star
+                dec = [bool(olap.gate_estimate(m, op, x[0], kk, x[2], x[3], 8.0).offload) for x in r]
+            else:
+                mpp = r[-1][3] / r[-1][0]                      # pairs per probe
+                nstar = olap.gate_estimate(m, op, 1 << 20, 1.0 + mpp, 8.0 * (1 << 20), mpp * (1 << 20), 8.0,
+                                           mpp).n_star
+                dec = [bool(olap.gate_estimate(m, op, x[0], x[1], x[2], x[3], 8.0, mpp).offload) for x in r]
+            measured = _crossover(gn, [x[4] - x[8] - margin for x in r])
+            per_margin[f"{margin:g}ms"] = {
+                "n_star_predicted": int(nstar), "crossover_measured": measured,
+                "rel_error": (abs(nstar - measured) / measured) if measured > 0 and nstar > 0 else None,
+                "offload_at_n": dec}
+        result[name] = {"n": gn, "t_host_ms": [x[4] for x in r], "t_gpu_e2e_ms": [x[8] for x in r],
+                        "t_tx_ms": [x[5] for x in r], "t_kernel_ms": [x[6] for x in r],
+                        "t_post_ms": [x[7] for x in r], "margins": per_margin}
+    return {"metric": "gate break-even: predicted N* vs measured crossover", "unit": "relative error",
+            "grid_points": len(ns), "calibration": "odd grid points, 1/y^2-weighted least squares",
+            "reps": args.gate_reps, "host_threads": args.serve_cpu_workers, **result}
+
+
 def serving_leg(args, ctx, torch):
     """The serving stream: Poisson arrivals, half Top-K (N ~ logU[1e3, 1e8),
     K ~ logU[1, 1e5) clipped to N), half probes (n ~ logU[1e3, 1e8)) against
@@ -521,13 +630,15 @@ def run_ours(args):
     keys = datagen.topk_keys(n, args.dist, args.key_type, seed=1)
     w = keys.dtype.itemsize
     dk = torch.from_numpy(keys).cuda()
+    rid_host = datagen.identity_rowids(n) if args.rowids == "explicit" else None
+    dr = None if rid_host is None else torch.from_numpy(rid_host.view(np.int32)).cuda()
     ok = torch.empty(k, dtype=dk.dtype, device="cuda")
     orow = torch.empty(k, dtype=torch.int32, device="cuda")
     stream = torch.cuda.ExternalStream(ctx.stream)
 
     # -- kernel-only: device-resident keys, one launch per step ----------------
     for _ in range(max(3, args.warmup)):
-        ctx.topk_async(dk, k, olap.DESC, ok, orow)
+        ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
     ctx.sync()
     _barrier(world)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -539,7 +650,7 @@ def run_ours(args):
         start.record(stream)
         for i in range(args.steps):
             evs[i][0].record(stream)
-            ctx.topk_async(dk, k, olap.DESC, ok, orow)
+            ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
             evs[i][1].record(stream)
         end.record(stream)
         ctx.sync()
@@ -553,20 +664,21 @@ def run_ours(args):
 
     # -- end to end through the public blocking call, pinned host keys -----------
     hk = torch.from_numpy(keys).pin_memory()
+    hr = None if rid_host is None else torch.from_numpy(rid_host.view(np.int32)).pin_memory()
     hok = torch.empty(k, dtype=dk.dtype).pin_memory()
     horow = torch.empty(k, dtype=torch.int32).pin_memory()
     for _ in range(2):
-        ctx.topk(hk, k, olap.DESC, out_keys=hok, out_rowids=horow)
+        ctx.topk(hk, k, olap.DESC, rowids=hr, out_keys=hok, out_rowids=horow)
     _barrier(world)
     e2e_steps = max(3, min(args.steps, args.e2e_steps))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ctx.topk(hk, k, olap.DESC, out_keys=hok, out_rowids=horow)
+        ctx.topk(hk, k, olap.DESC, rowids=hr, out_keys=hok, out_rowids=horow)
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     e2e_value = world * n / e2e_s / 1e9
 
     # -- per-kernel device time (events around each kernel), same workload ----
-    kms = _kernel_pass(ctx, args.steps, lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow))
+    kms = _kernel_pass(ctx, args.steps, lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr))
     peak, peak_kind = _peaks()
     call_ms = float(np.mean(per_launch))
     # the dominant kernel: the streaming filter when the plan has one (it
@@ -584,7 +696,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"i64": "int64", "f32": "float32"}[args.key_type], "data": "synthetic",
         "config": {"workload": f"topk_{args.key_type}_{args.dist}_n2^{args.log2n}_k{k}_desc", "n": n, "k": k,
-                   "order": "desc", "rowids": "implicit",
+                   "order": "desc", "rowids": args.rowids,
                    "l2": f"inputs larger than L2 ({n * w / 2**30:.2f} GiB keys)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -600,13 +712,13 @@ def run_ours(args):
                                f"{args.steps} further steps after the timed region",
                      "filter": args.filter, "last_launch": phases,
                      "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
-        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w,
+        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w + (4 * n if hr is not None else 0),
                 "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
         "gpu_launches": args.steps * (3 if (n > (1 << 21) and k <= n // 256) else 2),
         "clocks": clk.summary(),
     }
     if "join" in workloads:
-        del dk, hk
+        del dk, hk, dr, hr
         torch.cuda.empty_cache()
         line["join"] = join_leg(args, ctx, torch, world)
         line["gpu_launches"] += line["join"]["gpu_launches"]
@@ -614,6 +726,9 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["batched"] = batched_leg(args, ctx, torch)
         line["gpu_launches"] += line["batched"]["gpu_launches_graph"] * args.batch_reps
+    if "gate" in workloads:
+        torch.cuda.empty_cache()
+        line["gate"] = gate_leg(args, ctx, torch)
     if "serving" in workloads:
         torch.cuda.empty_cache()
         line["serving"] = serving_leg(args, ctx, torch)
@@ -638,6 +753,8 @@ def main():
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--key-type", default="i64", choices=["i64", "f32"])
     ap.add_argument("--dist", default="uniform", choices=["uniform", "ascending", "dup1024"])
+    ap.add_argument("--rowids", default="implicit", choices=["implicit", "explicit"],
+                    help="explicit: uint32 row-ids 0..N-1 passed with the keys (read only for survivors)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
@@ -651,6 +768,8 @@ def main():
     ap.add_argument("--join-log2p", type=int, default=28)
     ap.add_argument("--join-steps", type=int, default=50)
     ap.add_argument("--join-traffic", type=float, default=None)
+    ap.add_argument("--gate-points", type=int, default=16, help="N grid points of the gate leg (1e3..1e8)")
+    ap.add_argument("--gate-reps", type=int, default=3)
     ap.add_argument("--join-partitions", type=int, default=0,
                     help="0 automatic, 1 direct probe, 2..256 forced partition count")
     ap.add_argument("--join-loads", type=int, default=0, help="bucket reads: 0 auto, 1 via L1, 2 L2 only")
