@@ -530,10 +530,13 @@ def serving_leg(args, ctx, torch):
     cal_n = np.unique(np.floor(np.logspace(3, 8, args.serve_cal_points)).astype(np.int64))
     cal_n = cal_n[cal_n <= A]
     samples = {olap.OP_TOPK: [], olap.OP_PROBE: []}
-    kcal = 100
+    # K varies over the calibration points (the stream's K spans 1..1e5), so
+    # the fit can tell the N*K and N*log N forms apart
+    k_cycle = [10, 1000, 100000, 1, 100, 10000]
     dev_keys = torch.from_numpy(topk_arena).cuda()
-    for n in cal_n:
+    for ci, n in enumerate(cal_n):
         n = int(n)
+        kcal = min(k_cycle[ci % len(k_cycle)], n)
         keys = topk_arena[:n]
         ok = np.empty(kcal, dtype=np.int64)
         orow = np.empty(kcal, dtype=np.uint32)
@@ -759,7 +762,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,join,batched,serving",
+    ap.add_argument("--workload", default="topk,join,batched,gate,serving",
                     help="comma list: topk (the headline value), join (probe sub-object), batched (executor), "
                          "serving (gated vs always-on stream)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",
@@ -769,7 +772,7 @@ def main():
     ap.add_argument("--join-steps", type=int, default=50)
     ap.add_argument("--join-traffic", type=float, default=None)
     ap.add_argument("--gate-points", type=int, default=16, help="N grid points of the gate leg (1e3..1e8)")
-    ap.add_argument("--gate-reps", type=int, default=3)
+    ap.add_argument("--gate-reps", type=int, default=5)
     ap.add_argument("--join-partitions", type=int, default=0,
                     help="0 automatic, 1 direct probe, 2..256 forced partition count")
     ap.add_argument("--join-loads", type=int, default=0, help="bucket reads: 0 auto, 1 via L1, 2 L2 only")
@@ -783,7 +786,7 @@ def main():
     ap.add_argument("--serve-cpu-workers", type=int, default=12)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-margin", type=float, default=0.0)
-    ap.add_argument("--serve-cal-points", type=int, default=12)
+    ap.add_argument("--serve-cal-points", type=int, default=18)
     ap.add_argument("--tile", type=int, default=0, help="bulk-copy bytes (0 = library default)")
     ap.add_argument("--stages", type=int, default=0, help="copies in flight per CTA (0 = default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM (0 = default)")

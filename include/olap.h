@@ -85,7 +85,18 @@ typedef struct {
                                    is created; it applies to the whole process on that device */
     int topk_digit_bits;        /* radix digit width of the Top-K selects (8..12; 0 => 12), also
                                    for batches created on this context */
+    int host_access;            /* olap_host_access: how pageable host memory is copied */
 } olap_opts;
+
+/* How pageable host inputs and outputs (OLAP_MEM_HOST) cross the host link. */
+typedef enum {
+    OLAP_HOST_AUTO = 0,         /* a copy kernel reads / writes the pageable memory itself when the
+                                   device accesses it coherently through the host page tables
+                                   (cudaDevAttrPageableMemoryAccessUsesHostPageTables, e.g. Grace
+                                   over NVLink-C2C); else as OLAP_HOST_STAGED */
+    OLAP_HOST_STAGED = 1        /* CPU copies through two pinned staging buffers, overlapped with
+                                   the DMA of the other */
+} olap_host_access;
 
 /* Cache path of the join probe's random bucket reads. */
 typedef enum {
@@ -109,6 +120,10 @@ const char* olap_last_error(const olap_ctx* ctx);
 void* olap_ctx_stream(const olap_ctx* ctx);
 /* Wait for all work the context enqueued. */
 olap_status olap_ctx_sync(olap_ctx* ctx);
+/* 1 when the context copies pageable host memory with a kernel that reads it
+ * directly (OLAP_HOST_AUTO on a device with host-page-table access), else 0;
+ * 0 for NULL. */
+int olap_ctx_host_direct(const olap_ctx* ctx);
 
 /* ------------------------------------------------------------------------
  * Top-K selection, ORDER BY key {ASC|DESC} LIMIT k (Sec. III-A; Sec. V-B

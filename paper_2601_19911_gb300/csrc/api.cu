@@ -93,9 +93,47 @@ olap_status ensure_pinned(olap_ctx* ctx) {
     return OLAP_OK;
 }
 
+// Copy between pageable host memory and device memory by a kernel that
+// dereferences the host addresses itself.  Used only when the device reads
+// and writes pageable memory coherently through the host's page tables
+// (Grace systems over NVLink-C2C), so no staging copy on the CPU is needed.
+// U is the widest access size with which source and destination line up.
+template <typename T>
+__global__ void __launch_bounds__(256) direct_copy_kernel(unsigned char* dst, const unsigned char* src, size_t head,
+                                                          size_t units, size_t tail) {
+    const size_t t = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t stride = static_cast<size_t>(gridDim.x) * blockDim.x;
+    for (size_t i = t; i < head; i += stride) dst[i] = src[i];
+    const T* s = reinterpret_cast<const T*>(src + head);
+    T* d = reinterpret_cast<T*>(dst + head);
+    for (size_t i = t; i < units; i += stride) d[i] = s[i];
+    const size_t base = head + units * sizeof(T);
+    for (size_t i = t; i < tail; i += stride) dst[base + i] = src[base + i];
+}
+
+static olap_status direct_copy(olap_ctx* ctx, void* dst, const void* src, size_t bytes, const char* what) {
+    const uintptr_t d = reinterpret_cast<uintptr_t>(dst), s = reinterpret_cast<uintptr_t>(src);
+    size_t u = 16;
+    while (u > 1 && ((d ^ s) & (u - 1))) u >>= 1;
+    const size_t head = std::min(bytes, static_cast<size_t>((u - (d & (u - 1))) & (u - 1)));
+    const size_t units = (bytes - head) / u;
+    const size_t tail = bytes - head - units * u;
+    const unsigned grid = static_cast<unsigned>(ctx->sm_count * 4);
+    unsigned char* dp = static_cast<unsigned char*>(dst);
+    const unsigned char* sp = static_cast<const unsigned char*>(src);
+    if (u == 16) direct_copy_kernel<uint4><<<grid, 256, 0, ctx->stream>>>(dp, sp, head, units, tail);
+    else if (u == 8) direct_copy_kernel<uint64_t><<<grid, 256, 0, ctx->stream>>>(dp, sp, head, units, tail);
+    else if (u == 4) direct_copy_kernel<uint32_t><<<grid, 256, 0, ctx->stream>>>(dp, sp, head, units, tail);
+    else if (u == 2) direct_copy_kernel<uint16_t><<<grid, 256, 0, ctx->stream>>>(dp, sp, head, units, tail);
+    else direct_copy_kernel<uint8_t><<<grid, 256, 0, ctx->stream>>>(dp, sp, head, units, tail);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, what);
+}
+
 olap_status copy_h2d(olap_ctx* ctx, void* dst, const void* src, size_t bytes, olap_mem where) {
     if (bytes == 0) return OLAP_OK;
     cudaError_t e;
+    if (where == OLAP_MEM_HOST && ctx->host_direct) return direct_copy(ctx, dst, src, bytes, "direct H2D copy");
     if (where == OLAP_MEM_DEVICE) {
         e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
         return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "device copy");
@@ -137,6 +175,7 @@ olap_status copy_d2h(olap_ctx* ctx, void* dst, const void* src, size_t bytes, ol
         e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream);
         return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "pinned D2H copy");
     }
+    if (ctx->host_direct) return direct_copy(ctx, dst, src, bytes, "direct D2H copy");
     olap_status st = ensure_pinned(ctx);
     if (st != OLAP_OK) return st;
     const unsigned char* s = static_cast<const unsigned char*>(src);
@@ -241,6 +280,7 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
         ctx->opts.topk_filter > OLAP_FILTER_REGS || jp < 0 || jp > 256 || (jp > 1 && (jp & (jp - 1))) ||
         ctx->opts.join_bucket_loads < OLAP_LOADS_AUTO || ctx->opts.join_bucket_loads > OLAP_LOADS_L2_ONLY ||
         (ctx->opts.topk_digit_bits != 0 && (ctx->opts.topk_digit_bits < 8 || ctx->opts.topk_digit_bits > 12)) ||
+        ctx->opts.host_access < OLAP_HOST_AUTO || ctx->opts.host_access > OLAP_HOST_STAGED ||
         (ctx->opts.block_threads != 0 && ctx->opts.block_threads != 256 && ctx->opts.block_threads != 512 &&
          ctx->opts.block_threads != 1024) ||
         (ctx->opts.l2_fetch_bytes != 0 && ctx->opts.l2_fetch_bytes != 32 && ctx->opts.l2_fetch_bytes != 64 &&
@@ -273,6 +313,12 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     int l2 = 0;
     if ((e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device)) != cudaSuccess) return bail(e);
     ctx->l2_bytes = static_cast<uint64_t>(l2);
+    int pageable = 0, host_pt = 0;
+    if ((e = cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, ctx->device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&host_pt, cudaDevAttrPageableMemoryAccessUsesHostPageTables, ctx->device)) !=
+            cudaSuccess)
+        return bail(e);
+    ctx->host_direct = ctx->opts.host_access != OLAP_HOST_STAGED && pageable && host_pt;
     if (ctx->opts.l2_fetch_bytes &&
         (e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, static_cast<size_t>(ctx->opts.l2_fetch_bytes))) !=
             cudaSuccess)
@@ -316,6 +362,8 @@ void olap_ctx_destroy(olap_ctx* ctx) {
 const char* olap_last_error(const olap_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
 
 void* olap_ctx_stream(const olap_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
+
+int olap_ctx_host_direct(const olap_ctx* ctx) { return ctx && ctx->host_direct ? 1 : 0; }
 
 olap_status olap_ctx_sync(olap_ctx* ctx) {
     if (!ctx) return OLAP_E_INVALID;

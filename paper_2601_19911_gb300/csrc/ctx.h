@@ -55,6 +55,7 @@ struct olap_ctx {
     void* part = nullptr;
     size_t part_bytes = 0;
     uint64_t l2_bytes = 0;            // device L2 size
+    bool host_direct = false;         // copy pageable host memory with a kernel (no CPU staging)
 
     // Device memory held by live join tables built through this context.
     uint64_t table_bytes = 0;

@@ -3,15 +3,21 @@
 // (Sec. II-A) that the GPU augments.  It is a separate library on purpose:
 // the GPU library has no CPU implementation of the primitives.
 //
-//   Top-K: each thread keeps a bounded max-heap of the K smallest composites
-//   (order-preserving key word, row-id) of its chunk; the heaps are merged and
-//   sorted.  Same ordering as the GPU: key in the requested order, row-id
-//   ascending on ties, float32 by IEEE totalOrder.
+//   Top-K: each thread keeps the K smallest composites (order-preserving key
+//   word, row-id) of its chunk -- a bounded max-heap when K is small against
+//   the chunk, else nth_element over the chunk -- then the K smallest of the
+//   union are selected with nth_element and sorted.  Same ordering as the
+//   GPU: key in the requested order, row-id ascending on ties, float32 by IEEE
+//   totalOrder.
 //   Probe: per table, rows sorted by key plus an open-addressing index from
 //   key to its run; threads probe chunks and the pairs are concatenated.
 #include <algorithm>
+#include <condition_variable>
 #include <cstdint>
 #include <cstring>
+#include <deque>
+#include <functional>
+#include <mutex>
 #include <queue>
 #include <thread>
 #include <vector>
@@ -59,24 +65,89 @@ inline uint64_t mix(uint64_t h) {
     return h;
 }
 
+// Persistent worker threads: a request's chunks are queued to them, so a
+// parallel request costs a queue hand-off rather than thread creation.
+// Tasks never wait on other tasks, so concurrent requests cannot deadlock.
+class Pool {
+public:
+    explicit Pool(int n) {
+        for (int i = 0; i < n; ++i) th_.emplace_back([this] { loop(); });
+    }
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : th_) t.join();
+    }
+    void post(std::function<void()> f) {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            q_.push_back(std::move(f));
+        }
+        cv_.notify_one();
+    }
+
+private:
+    void loop() {
+        while (true) {
+            std::function<void()> f;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || !q_.empty(); });
+                if (q_.empty()) return;
+                f = std::move(q_.front());
+                q_.pop_front();
+            }
+            f();
+        }
+    }
+    std::mutex mu_;
+    std::condition_variable cv_;
+    std::deque<std::function<void()>> q_;
+    std::vector<std::thread> th_;
+    bool stop_ = false;
+};
+
 struct Engine {
     int threads = 8;
     std::vector<Table> tables;
+    Pool* pool = nullptr;
+    ~Engine() { delete pool; }
 };
 
+constexpr uint64_t TOPK_CHUNK = 65536;    // rows per thread at least: Top-K (streaming)
+constexpr uint64_t PROBE_CHUNK = 8192;    // probe (a random table access per row)
+
+// Chunks a request of n rows is cut into.
+int chunks_for(const Engine* E, uint64_t n, uint64_t min_chunk) {
+    return static_cast<int>(std::max<uint64_t>(1, std::min<uint64_t>(E->threads, n / min_chunk)));
+}
+
+// Run f(i, a, b) over t chunks of [0, n): chunk 0 on the calling thread, the
+// others on the pool; returns when all are done.
 template <typename F>
-void parallel(int t, uint64_t n, F&& f) {
-    if (t <= 1 || n < 65536) {
+void parallel(Engine* E, int t, uint64_t n, F&& f) {
+    if (t <= 1) {
         f(0, 0, n);
         return;
     }
-    std::vector<std::thread> th;
     const uint64_t per = (n + t - 1) / t;
-    for (int i = 0; i < t; ++i) {
+    std::mutex mu;
+    std::condition_variable cv;
+    int left = t - 1;
+    for (int i = 1; i < t; ++i) {
         const uint64_t a = std::min(n, i * per), b = std::min(n, a + per);
-        th.emplace_back([&, i, a, b] { f(i, a, b); });
+        E->pool->post([&, i, a, b] {
+            f(i, a, b);
+            std::lock_guard<std::mutex> lk(mu);
+            if (--left == 0) cv.notify_one();
+        });
     }
-    for (auto& x : th) x.join();
+    f(0, 0, std::min(n, per));
+    std::unique_lock<std::mutex> lk(mu);
+    cv.wait(lk, [&] { return left == 0; });
 }
 
 int run_topk(Engine* E, olap_serve_request* r) {
@@ -86,22 +157,35 @@ int run_topk(Engine* E, olap_serve_request* r) {
         r->out_count = 0;
         return OLAP_OK;
     }
-    const int t = n < 65536 ? 1 : E->threads;
+    const int t = chunks_for(E, n, TOPK_CHUNK);
     std::vector<std::vector<Comp>> part(t);
-    parallel(t, n, [&](int ti, uint64_t a, uint64_t b) {
+    auto comp = [&](uint64_t i) {
+        Comp c;
+        c.r = f32 ? word_f32(static_cast<const uint32_t*>(r->keys)[i], desc)
+                  : word_i64(static_cast<const uint64_t*>(r->keys)[i], desc);
+        c.rid = r->rowids ? r->rowids[i] : static_cast<uint32_t>(i);
+        return c;
+    };
+    parallel(E, t, n, [&](int ti, uint64_t a, uint64_t b) {
+        auto& v = part[ti];
+        if (kk * 16 >= b - a) {                 // K large against the chunk: select
+            v.resize(b - a);
+            for (uint64_t i = a; i < b; ++i) v[i - a] = comp(i);
+            if (v.size() > kk) {
+                std::nth_element(v.begin(), v.begin() + static_cast<long>(kk), v.end());
+                v.resize(kk);
+            }
+            return;
+        }
         std::priority_queue<Comp> heap;
         for (uint64_t i = a; i < b; ++i) {
-            Comp c;
-            c.r = f32 ? word_f32(static_cast<const uint32_t*>(r->keys)[i], desc)
-                      : word_i64(static_cast<const uint64_t*>(r->keys)[i], desc);
-            c.rid = r->rowids ? r->rowids[i] : static_cast<uint32_t>(i);
+            const Comp c = comp(i);
             if (heap.size() < kk) heap.push(c);
             else if (c < heap.top()) {
                 heap.pop();
                 heap.push(c);
             }
         }
-        auto& v = part[ti];
         v.reserve(heap.size());
         while (!heap.empty()) {
             v.push_back(heap.top());
@@ -110,7 +194,8 @@ int run_topk(Engine* E, olap_serve_request* r) {
     });
     std::vector<Comp> all;
     for (auto& v : part) all.insert(all.end(), v.begin(), v.end());
-    std::partial_sort(all.begin(), all.begin() + static_cast<long>(kk), all.end());
+    if (all.size() > kk) std::nth_element(all.begin(), all.begin() + static_cast<long>(kk), all.end());
+    std::sort(all.begin(), all.begin() + static_cast<long>(kk));
     for (uint64_t i = 0; i < kk; ++i) {
         if (f32) static_cast<uint32_t*>(r->out_keys)[i] = unword_f32(all[i].r, desc);
         else static_cast<uint64_t*>(r->out_keys)[i] = unword_i64(all[i].r, desc);
@@ -124,9 +209,9 @@ int run_probe(Engine* E, olap_serve_request* r) {
     if (r->table_id < 0 || r->table_id >= static_cast<int>(E->tables.size())) return OLAP_E_INVALID;
     const Table& T = E->tables[r->table_id];
     const int64_t* keys = static_cast<const int64_t*>(r->keys);
-    const int t = r->n < 65536 ? 1 : E->threads;
+    const int t = chunks_for(E, r->n, PROBE_CHUNK);
     std::vector<std::vector<olap_pair>> part(t);
-    parallel(t, r->n, [&](int ti, uint64_t a, uint64_t b) {
+    parallel(E, t, r->n, [&](int ti, uint64_t a, uint64_t b) {
         auto& v = part[ti];
         for (uint64_t i = a; i < b; ++i) {
             const uint64_t key = static_cast<uint64_t>(keys[i]);
@@ -160,6 +245,7 @@ extern "C" {
 void* olap_host_engine_create(int threads) {
     Engine* e = new Engine();
     e->threads = threads > 0 ? threads : 8;
+    e->pool = new Pool(e->threads);
     return e;
 }
 

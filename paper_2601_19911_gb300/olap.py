@@ -27,6 +27,7 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 # Every symbol include/olap.h declares, checked by the ABI tests.
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
+    "olap_ctx_host_direct",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
     "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_autotune",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
@@ -40,6 +41,7 @@ CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
 FIT_ORDINARY, FIT_RELATIVE = 0, 1
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
 LOADS_AUTO, LOADS_L1, LOADS_L2_ONLY = 0, 1, 2
+HOST_AUTO, HOST_STAGED = 0, 1
 NOALLOC_MAX_N = 1 << 24
 NOALLOC_MAX_K = 4096
 
@@ -67,6 +69,7 @@ class olap_opts(ctypes.Structure):
         ("join_bucket_loads", ctypes.c_int),
         ("l2_fetch_bytes", ctypes.c_int),
         ("topk_digit_bits", ctypes.c_int),
+        ("host_access", ctypes.c_int),
     ]
 
 
@@ -189,6 +192,8 @@ def load(path: str | None = None):
         lib.olap_ctx_stream.argtypes = [vp]
         lib.olap_ctx_sync.restype = i32
         lib.olap_ctx_sync.argtypes = [vp]
+        lib.olap_ctx_host_direct.restype = i32
+        lib.olap_ctx_host_direct.argtypes = [vp]
         lib.olap_topk.restype = i32
         lib.olap_topk.argtypes = [vp, vp, i32, vp, i32, u64, u64, i32, vp, vp, i32, ctypes.POINTER(u64)]
         lib.olap_topk_async.restype = i32
@@ -307,11 +312,12 @@ class Context:
                  margin_ms: float = 0.0, load_factor: float = 0.0, staging_bytes: int = 0,
                  topk_filter: int = FILTER_AUTO, topk_tile_bytes: int = 0, topk_stages: int = 0,
                  topk_ctas_per_sm: int = 0, join_partitions: int = 0, join_bucket_loads: int = 0,
-                 l2_fetch_bytes: int = 0, topk_digit_bits: int = 0, block_threads: int = 0):
+                 l2_fetch_bytes: int = 0, topk_digit_bits: int = 0, block_threads: int = 0,
+                 host_access: int = 0):
         self.lib = load()
         opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, block_threads, load_factor, staging_bytes,
                          topk_filter, topk_tile_bytes, topk_stages, topk_ctas_per_sm, join_partitions,
-                         join_bucket_loads, l2_fetch_bytes, topk_digit_bits)
+                         join_bucket_loads, l2_fetch_bytes, topk_digit_bits, host_access)
         h = ctypes.c_void_p()
         st = self.lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h))
         if st != OK:
@@ -438,6 +444,11 @@ class Context:
         res = olap_tune_result()
         self.check(self.lib.olap_autotune(self.h, ctypes.byref(req), ctypes.byref(res)))
         return {nm: getattr(res, nm) for nm, _ in olap_tune_result._fields_ if nm != "pad"}
+
+    @property
+    def host_direct(self) -> bool:
+        """Whether pageable host memory is copied by a kernel reading it directly."""
+        return bool(self.lib.olap_ctx_host_direct(self.h))
 
     def time_kernels(self, on: bool = True):
         """olap_ctx_time_kernels: record CUDA events around each kernel."""

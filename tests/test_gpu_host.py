@@ -1,0 +1,62 @@
+"""Pageable host memory in and out, through both ways of crossing the host
+link: the copy kernel that reads and writes pageable memory itself (where the
+device supports it) and the pinned double-buffer staging.  Inputs are numpy
+slices at every alignment the copy has to line up (offsets of 1..3 elements),
+results bit-exact against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_19911_gb300 import datagen, olap
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", params=[olap.HOST_AUTO, olap.HOST_STAGED], ids=["auto", "staged"])
+def hctx(request):
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0, host_access=request.param)
+    if request.param == olap.HOST_STAGED:
+        assert not c.host_direct
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("off", [0, 1, 2, 3])
+@pytest.mark.parametrize("kt", ["i64", "f32"])
+def test_topk_pageable_slices(hctx, off, kt):
+    base = datagen.topk_keys(3_000_011, "uniform", kt, seed=50 + off)
+    keys = base[off:]                                   # 4- or 8-byte aligned, not 16
+    rid_base = (datagen.splitmix64(51, base.shape[0]) >> np.uint64(40)).astype(np.uint32)
+    rowids = rid_base[off:]
+    for k in (1, 333, 5000):
+        ok = np.empty(k + 3, dtype=keys.dtype)[3:] if off else np.empty(k, dtype=keys.dtype)
+        orow = np.empty(k + 1, dtype=np.uint32)[1:]     # outputs at odd offsets too
+        gk, gr = hctx.topk(keys, k, olap.DESC, rowids=rowids, out_keys=ok, out_rowids=orow)
+        wk, wr = oracle.topk(keys, k, olap.DESC, rowids)
+        np.testing.assert_array_equal(gr, wr)
+        np.testing.assert_array_equal(gk.view(np.uint8), wk.view(np.uint8))
+
+
+@pytest.mark.parametrize("off", [0, 1, 3])
+def test_join_pageable_slices(hctx, off):
+    b = datagen.join_build(120_000 + off, "mult14", seed=52)
+    p = datagen.join_probe(900_001, b, 0.7, "uniform", seed=52)
+    bk = np.concatenate([np.zeros(off, dtype=np.int64), b.keys])[off:]
+    pk = np.concatenate([np.zeros(off, dtype=np.int64), p.keys])[off:]
+    t = hctx.join_build(bk)
+    got = hctx.join_probe(t, pk)                       # pairs back into pageable memory
+    t.free()
+    got = got.astype(np.uint64)
+    got = np.sort((got[:, 0] << np.uint64(32)) | got[:, 1])
+    np.testing.assert_array_equal(got, oracle.join(b.keys, p.keys))
+
+
+def test_empty_and_tiny(hctx):
+    for n in (0, 1, 15, 17):
+        keys = datagen.topk_keys(n + 1, "uniform", "i64", seed=n)[1:]
+        gk, gr = hctx.topk(keys, 10, olap.ASC)
+        wk, wr = oracle.topk(keys, 10, olap.ASC)
+        np.testing.assert_array_equal(gr, wr)
