@@ -23,7 +23,9 @@ _OUT = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KEY_I64, KEY_F32 = 0, 1
+KEY_I64, KEY_F32, KEY_F64, KEY_U64, KEY_I32, KEY_U32 = 0, 1, 2, 3, 4, 5
+_KEY_OF = {np.dtype(np.int64): KEY_I64, np.dtype(np.float32): KEY_F32, np.dtype(np.float64): KEY_F64,
+           np.dtype(np.uint64): KEY_U64, np.dtype(np.int32): KEY_I32, np.dtype(np.uint32): KEY_U32}
 ASC, DESC = 0, 1
 
 
@@ -53,6 +55,8 @@ def _load():
             lib.oracle_free.argtypes = [vp]
             lib.oracle_f32_total_below.restype = i32
             lib.oracle_f32_total_below.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+            lib.oracle_f64_total_below.restype = i32
+            lib.oracle_f64_total_below.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
             _lib = lib
     return _lib
 
@@ -62,11 +66,11 @@ def _ptr(a):
 
 
 def _key_type(keys: np.ndarray) -> int:
-    if keys.dtype == np.int64:
-        return KEY_I64
-    if keys.dtype == np.float32:
-        return KEY_F32
-    raise TypeError(f"oracle keys must be int64 or float32, got {keys.dtype}")
+    try:
+        return _KEY_OF[keys.dtype]
+    except KeyError:
+        raise TypeError(f"oracle keys must be int64, float32, float64, uint64, int32 or uint32, "
+                        f"got {keys.dtype}") from None
 
 
 def topk(keys: np.ndarray, k: int, order: int = DESC, rowids: np.ndarray | None = None):
@@ -113,3 +117,7 @@ def join_nested(bkeys, pkeys, brow=None, prow=None) -> np.ndarray:
 
 def f32_total_below(x_bits: int, y_bits: int) -> bool:
     return bool(_load().oracle_f32_total_below(int(x_bits) & 0xFFFFFFFF, int(y_bits) & 0xFFFFFFFF))
+
+
+def f64_total_below(x_bits: int, y_bits: int) -> bool:
+    return bool(_load().oracle_f64_total_below(int(x_bits) & 0xFFFFFFFFFFFFFFFF, int(y_bits) & 0xFFFFFFFFFFFFFFFF))

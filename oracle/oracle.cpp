@@ -17,9 +17,11 @@
 //
 // Readings of points the paper leaves open (ties for ASC, K > N, float order)
 // follow the library's documented contract: row-id ascending breaks ties in
-// both orders; the output has min(k, n) entries; float32 keys are ordered by
-// IEEE 754-2019 totalOrder (Sec. 5.10), implemented below from its case
-// definition rather than from any bit trick.
+// both orders; the output has min(k, n) entries; float32 and float64 keys
+// (the paper's key column is a double, Sec. V-A) are ordered by IEEE 754-2019
+// totalOrder (Sec. 5.10), implemented below from its case definition rather
+// than from any bit trick; integer keys by their value (signed or unsigned).
+// Key types: 0 int64, 1 float32, 2 float64, 3 uint64, 4 int32, 5 uint32.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -38,36 +40,54 @@ namespace {
 //   * two NaNs: a negative one is below a positive one; for positive NaNs the
 //     smaller (quiet bit, payload) field, read as an integer, is below; for
 //     negative NaNs the larger one is below
-bool f32_total_below(uint32_t xb, uint32_t yb) {
-    float x, y;
-    std::memcpy(&x, &xb, 4);
-    std::memcpy(&y, &yb, 4);
+// The same case list for any binary format: F is float or double, B its bit
+// pattern type, FRAC the mask of its trailing significand (quiet bit and
+// payload) field.
+template <typename F, typename B, B FRAC>
+bool total_below(B xb, B yb) {
+    F x, y;
+    std::memcpy(&x, &xb, sizeof(F));
+    std::memcpy(&y, &yb, sizeof(F));
     const bool xn = std::isnan(x), yn = std::isnan(y);
     const bool xs = std::signbit(x), ys = std::signbit(y);
     if (xn && yn) {
         if (xs != ys) return xs;
-        const uint32_t xf = xb & 0x007FFFFFu, yf = yb & 0x007FFFFFu;
+        const B xf = xb & FRAC, yf = yb & FRAC;
         return xs ? (xf > yf) : (xf < yf);
     }
     if (xn) return xs;       // -NaN below all non-NaN, +NaN above all
     if (yn) return !ys;      // x below +NaN, above -NaN
     if (x < y) return true;
     if (x > y) return false;
-    if (x == 0.0f) return xs && !ys;   // -0 below +0
+    if (x == F(0)) return xs && !ys;   // -0 below +0
     return false;
 }
 
+bool f32_total_below(uint32_t xb, uint32_t yb) { return total_below<float, uint32_t, 0x007FFFFFu>(xb, yb); }
+bool f64_total_below(uint64_t xb, uint64_t yb) {
+    return total_below<double, uint64_t, 0x000FFFFFFFFFFFFFull>(xb, yb);
+}
+
+int key_width(int key_type) { return (key_type == 1 || key_type == 4 || key_type == 5) ? 4 : 8; }
+
 struct Row {
-    uint64_t key;     // raw key bits (int64 or float32 in the low half)
+    uint64_t key;     // raw key bits (4-byte keys in the low half)
     uint32_t rowid;
 };
 
 struct Less {
-    int key_type;     // 0 = int64, 1 = float32
+    int key_type;     // see the file header
     int order;        // 0 = ascending, 1 = descending
     bool key_below(uint64_t a, uint64_t b) const {
-        if (key_type == 0) return static_cast<int64_t>(a) < static_cast<int64_t>(b);
-        return f32_total_below(static_cast<uint32_t>(a), static_cast<uint32_t>(b));
+        switch (key_type) {
+            case 0: return static_cast<int64_t>(a) < static_cast<int64_t>(b);
+            case 1: return f32_total_below(static_cast<uint32_t>(a), static_cast<uint32_t>(b));
+            case 2: return f64_total_below(a, b);
+            case 3: return a < b;
+            case 4:
+                return static_cast<int32_t>(static_cast<uint32_t>(a)) < static_cast<int32_t>(static_cast<uint32_t>(b));
+            default: return static_cast<uint32_t>(a) < static_cast<uint32_t>(b);
+        }
     }
     bool operator()(const Row& a, const Row& b) const {
         const bool ab = order == 0 ? key_below(a.key, b.key) : key_below(b.key, a.key);
@@ -88,12 +108,11 @@ extern "C" {
 uint64_t oracle_topk(int key_type, const void* keys, const uint32_t* rowids, uint64_t n,
                      uint64_t k, int order, void* out_keys, uint32_t* out_rowids) {
     std::vector<Row> rows(n);
+    const int w = key_width(key_type);
     for (uint64_t i = 0; i < n; ++i) {
         uint64_t kb;
-        if (key_type == 0) {
-            int64_t v;
-            std::memcpy(&v, static_cast<const int64_t*>(keys) + i, 8);
-            kb = static_cast<uint64_t>(v);
+        if (w == 8) {
+            std::memcpy(&kb, static_cast<const uint64_t*>(keys) + i, 8);
         } else {
             uint32_t v;
             std::memcpy(&v, static_cast<const uint32_t*>(keys) + i, 4);
@@ -105,9 +124,8 @@ uint64_t oracle_topk(int key_type, const void* keys, const uint32_t* rowids, uin
     std::stable_sort(rows.begin(), rows.end(), Less{key_type, order});
     const uint64_t cnt = std::min(k, n);
     for (uint64_t i = 0; i < cnt; ++i) {
-        if (key_type == 0) {
-            const int64_t v = static_cast<int64_t>(rows[i].key);
-            std::memcpy(static_cast<int64_t*>(out_keys) + i, &v, 8);
+        if (w == 8) {
+            std::memcpy(static_cast<uint64_t*>(out_keys) + i, &rows[i].key, 8);
         } else {
             const uint32_t v = static_cast<uint32_t>(rows[i].key);
             std::memcpy(static_cast<uint32_t*>(out_keys) + i, &v, 4);
@@ -179,5 +197,6 @@ void oracle_free(void* p) { std::free(p); }
 // Exposed so a test can check the comparator alone against IEEE's listed
 // ordering of special values.
 int oracle_f32_total_below(uint32_t x, uint32_t y) { return f32_total_below(x, y) ? 1 : 0; }
+int oracle_f64_total_below(uint64_t x, uint64_t y) { return f64_total_below(x, y) ? 1 : 0; }
 
 }  // extern "C"

@@ -140,40 +140,66 @@ def _ascending_f32_bits(n: int) -> np.ndarray:
     return out
 
 
+def _ascending_f64_bits(n: int) -> np.ndarray:
+    """Strictly increasing finite float64 values, negatives then non-negatives
+    (the binary64 counterpart of ``_ascending_f32_bits``)."""
+    neg = n // 2
+    pos = n - neg
+    stride = max(1, 0x7FF0000000000000 // max(1, max(neg, pos)))
+    out = np.empty(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        out[:neg] = _U64(1 << 63) | ((neg - np.arange(neg, dtype=np.uint64)) * _U64(stride))
+        out[neg:] = np.arange(pos, dtype=np.uint64) * _U64(stride)
+    return out
+
+
+_DTYPE = {"i64": np.int64, "f32": np.float32, "f64": np.float64, "u64": np.uint64, "i32": np.int32,
+          "u32": np.uint32}
+
+
 def topk_keys(n: int, dist: str = "uniform", key_type: str = "i64", seed: int = 0) -> np.ndarray:
-    """A key column of ``n`` keys.
+    """A key column of ``n`` keys of type ``key_type`` (i64, f32, f64, u64,
+    i32, u32).
 
     dist:
-      * ``uniform``: int64 uniform over the full int64 range, or float32 with a
-        uniform 32-bit pattern (all classes: NaN, inf, subnormal, +-0).
-      * ``ascending``: strictly increasing.  int64: ``INT64_MIN + i*floor(2^64/n)``;
-        float32: see ``_ascending_f32_bits``.
+      * ``uniform``: uniform bit patterns of the type's width (integers over
+        their full range; floats over all classes: NaN, inf, subnormal, +-0).
+      * ``ascending``: strictly increasing.  int64: ``INT64_MIN + i*floor(2^64/n)``,
+        uint64 the same offset by 2^63, 32-bit integers likewise over 2^32 (for
+        n <= 2^32); floats: see ``_ascending_f32_bits`` / ``_ascending_f64_bits``.
       * ``dup1024``: each key one of 1024 distinct uniform draws, picked by a
         second stream.
-    Returned as int64, or as float32 (a view of the drawn bits).
     """
     n = int(n)
-    if key_type not in ("i64", "f32"):
+    if key_type not in _DTYPE:
         raise ValueError(key_type)
+    wide = key_type in ("i64", "f64", "u64")
+    dt = _DTYPE[key_type]
     if dist == "uniform":
         raw = splitmix64(stream_seed(seed, 0), n)
-        if key_type == "i64":
-            return raw.view(np.int64)
-        return (raw >> _U64(32)).astype(np.uint32).view(np.float32)
+        if wide:
+            return raw.view(dt)
+        return (raw >> _U64(32)).astype(np.uint32).view(dt)
     if dist == "ascending":
-        if key_type == "i64":
-            step = min((1 << 64) // max(n, 1), (1 << 64) - 1)   # n = 1: only i = 0 is used
-            with np.errstate(over="ignore"):
-                v = np.arange(n, dtype=np.uint64) * _U64(step) + _U64(1 << 63)
-            return v.view(np.int64)
-        return _ascending_f32_bits(n).view(np.float32)
+        if key_type == "f64":
+            return _ascending_f64_bits(n).view(np.float64)
+        if key_type == "f32":
+            return _ascending_f32_bits(n).view(np.float32)
+        span = 1 << (64 if wide else 32)
+        step = min(span // max(n, 1), span - 1)          # n = 1: only i = 0 is used
+        with np.errstate(over="ignore"):
+            v = np.arange(n, dtype=np.uint64) * _U64(step)
+        if wide:
+            return (v + _U64(1 << 63)).view(np.int64) if key_type == "i64" else v.view(dt)
+        v32 = v.astype(np.uint32)
+        return (v32 ^ np.uint32(1 << 31)).view(np.int32) if key_type == "i32" else v32
     if dist == "dup1024":
-        if key_type == "i64":
-            vals = _distinct_u64(stream_seed(seed, 1), 1024).view(np.int64)
+        if wide:
+            vals = _distinct_u64(stream_seed(seed, 1), 1024).view(dt)
         else:
             bits = (splitmix64(stream_seed(seed, 1), 4096) >> _U64(32)).astype(np.uint32)
             _, first = np.unique(bits, return_index=True)
-            vals = bits[np.sort(first)[:1024]].view(np.float32)
+            vals = bits[np.sort(first)[:1024]].view(dt)
             assert vals.shape[0] == 1024
         pick = splitmix64(stream_seed(seed, 2), n) % _U64(1024)
         return vals[pick.astype(np.int64)]
