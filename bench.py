@@ -693,11 +693,13 @@ def run_ours(args):
     traffic = args.traffic
     if traffic is None and top == "topk_filter_ms" and k == 1000 and args.dist == "uniform" \
             and args.filter == "regs":
-        traffic = FILTER_DRAM_BYTES_PER_KEY[args.key_type] * n
+        traffic = FILTER_DRAM_BYTES_PER_KEY[args.key_type] * n if args.key_type in FILTER_DRAM_BYTES_PER_KEY \
+            else None
     line = {
         "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"i64": "int64", "f32": "float32"}[args.key_type], "data": "synthetic",
+        "vs_baseline": None, "dtype": {"i64": "int64", "f32": "float32", "f64": "float64", "u64": "uint64",
+                                       "i32": "int32", "u32": "uint32"}[args.key_type], "data": "synthetic",
         "config": {"workload": f"topk_{args.key_type}_{args.dist}_n2^{args.log2n}_k{k}_desc", "n": n, "k": k,
                    "order": "desc", "rowids": args.rowids,
                    "l2": f"inputs larger than L2 ({n * w / 2**30:.2f} GiB keys)",
@@ -754,7 +756,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=1000)
     ap.add_argument("--log2n", type=int, default=28)
-    ap.add_argument("--key-type", default="i64", choices=["i64", "f32"])
+    ap.add_argument("--key-type", default="i64", choices=["i64", "f32", "f64", "u64", "i32", "u32"])
     ap.add_argument("--dist", default="uniform", choices=["uniform", "ascending", "dup1024"])
     ap.add_argument("--rowids", default="implicit", choices=["implicit", "explicit"],
                     help="explicit: uint32 row-ids 0..N-1 passed with the keys (read only for survivors)")

@@ -55,7 +55,17 @@ typedef enum {
     OLAP_E_DEVICE = 7          /* device-side validation rejected a descriptor */
 } olap_status;
 
-typedef enum { OLAP_KEY_I64 = 0, OLAP_KEY_F32 = 1 } olap_key_type;
+/* Key types of Top-K.  Floats are ordered by IEEE 754-2019 totalOrder (the
+ * paper's key column is a double, Sec. V-A); integers by value.  The join
+ * takes int64 keys only. */
+typedef enum {
+    OLAP_KEY_I64 = 0,
+    OLAP_KEY_F32 = 1,
+    OLAP_KEY_F64 = 2,
+    OLAP_KEY_U64 = 3,
+    OLAP_KEY_I32 = 4,
+    OLAP_KEY_U32 = 5
+} olap_key_type;
 typedef enum { OLAP_ASC = 0, OLAP_DESC = 1 } olap_order;
 typedef enum { OLAP_MEM_HOST = 0, OLAP_MEM_HOST_PINNED = 1, OLAP_MEM_DEVICE = 2 } olap_mem;
 
@@ -129,9 +139,11 @@ int olap_ctx_host_direct(const olap_ctx* ctx);
  * Top-K selection, ORDER BY key {ASC|DESC} LIMIT k (Sec. III-A; Sec. V-B
  * names the query form ORDER BY value DESC LIMIT 100).
  *
- * keys        n keys of `type` (int64, or float32 ordered by IEEE 754-2019
- *             totalOrder, so -0 < +0 and NaNs sort outside +-inf by sign),
- *             in memory `in_where`.
+ * keys        n keys of `type` (olap_key_type: int64, uint64, int32, uint32
+ *             by value; float32 / float64 by IEEE 754-2019 totalOrder, so
+ *             -0 < +0 and NaNs sort outside +-inf by sign), in memory
+ *             `in_where`; 8-byte keys 8-byte aligned, 4-byte keys 4-byte
+ *             aligned.
  * rowids      n uint32 row-ids in the same memory kind, or NULL for
  *             row-id = index.
  * order       OLAP_ASC or OLAP_DESC on the key; ties on equal keys are always

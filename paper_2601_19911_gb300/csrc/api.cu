@@ -231,7 +231,8 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
     a.rowids = d_rowids;
     a.n = n;
     a.k = kk;
-    a.f32 = type == OLAP_KEY_F32;
+    a.kind = type;
+    a.w4 = key_bytes(type) == 4;
     a.desc = order == OLAP_DESC;
     topk_carve(a, plan, ctx->scratch);
     a.out_keys = d_out_keys;
@@ -254,12 +255,12 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
 static olap_status check_topk_args(olap_ctx* ctx, const void* keys, olap_key_type type, uint64_t n,
                                    uint64_t kk, olap_order order, const void* out_keys,
                                    const void* out_rowids) {
-    if (type != OLAP_KEY_I64 && type != OLAP_KEY_F32) return fail(ctx, OLAP_E_INVALID, "bad key type");
+    if (type < OLAP_KEY_I64 || type > OLAP_KEY_U32) return fail(ctx, OLAP_E_INVALID, "bad key type");
     if (order != OLAP_ASC && order != OLAP_DESC) return fail(ctx, OLAP_E_INVALID, "bad order");
     if (n >= (1ull << 32)) return fail(ctx, OLAP_E_INVALID, "n must be below 2^32");
     if (n && !keys) return fail(ctx, OLAP_E_INVALID, "keys is NULL");
     if (kk && (!out_keys || !out_rowids)) return fail(ctx, OLAP_E_INVALID, "output pointer is NULL");
-    const size_t w = type == OLAP_KEY_I64 ? 8 : 4;
+    const size_t w = key_bytes(type);
     if (reinterpret_cast<uintptr_t>(keys) % w) return fail(ctx, OLAP_E_INVALID, "keys misaligned");
     return OLAP_OK;
 }
@@ -387,7 +388,7 @@ olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const
     if (kk == 0) return OLAP_OK;
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
-    const size_t w = type == OLAP_KEY_I64 ? 8 : 4;
+    const size_t w = key_bytes(type);
 
     // Key-only input: keys (and explicit row-ids) to the device.
     const void* dk = keys;

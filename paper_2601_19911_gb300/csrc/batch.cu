@@ -47,9 +47,9 @@ static_assert((BT_TPB / 32) * BT_WS * 12 <= BT_SMEM, "warp stages must fit");
 
 struct __align__(8) Item {
     int op;                      // OLAP_OP_TOPK / OLAP_OP_PROBE
-    int f32;
+    int w4;                      // 4-byte keys
     int desc;
-    int pad;
+    int kind;                    // olap_key_type
     const void* keys;
     const uint32_t* rowids;
     uint64_t n;
@@ -75,15 +75,16 @@ struct ProbeChunk {
 
 __device__ __forceinline__ uint64_t item_rank(const Item& it, uint64_t i, uint32_t* rid) {
     uint64_t r;
-    if (it.f32) r = rank_f32(static_cast<const uint32_t*>(it.keys)[i], it.desc);
-    else r = rank_i64(static_cast<const uint64_t*>(it.keys)[i], it.desc);
+    const uint64_t bits = it.w4 ? static_cast<uint64_t>(static_cast<const uint32_t*>(it.keys)[i])
+                                : static_cast<const uint64_t*>(it.keys)[i];
+    r = rank_key(bits, it.kind, it.desc);
     *rid = it.rowids ? it.rowids[i] : static_cast<uint32_t>(i);
     return r;
 }
 
 __device__ __forceinline__ void put_result(const Item& it, uint64_t i, uint64_t r, uint32_t rid) {
-    if (it.f32) static_cast<uint32_t*>(it.out_keys)[i] = unrank_f32(r, it.desc);
-    else static_cast<uint64_t*>(it.out_keys)[i] = unrank_i64(r, it.desc);
+    if (it.w4) static_cast<uint32_t*>(it.out_keys)[i] = static_cast<uint32_t>(unrank_key(r, it.kind, it.desc));
+    else static_cast<uint64_t*>(it.out_keys)[i] = unrank_key(r, it.kind, it.desc);
     it.out_rowids[i] = rid;
 }
 
@@ -99,7 +100,7 @@ __device__ uint64_t cta_sample_threshold(const Item& it, unsigned r, unsigned* h
         uint32_t rid;
         s[j] = item_rank(it, pos, &rid);
     }
-    const int kb = it.f32 ? 32 : 64;
+    const int kb = it.w4 ? 32 : 64;
     uint64_t prefix = 0;
     unsigned long long rem = r, cum = 0;
     for (int L = 0; L < kb; L += digit) {
@@ -143,35 +144,35 @@ __device__ __forceinline__ void cta_flush_stage(uint64_t* ws_r, uint32_t* ws_idx
 
 // Test one key (rank via the key-domain limit) and stage a hit; the whole
 // warp calls with its lanes' keys.
-template <bool F32>
+template <bool W4>
 __device__ __forceinline__ void cta_filter_key(const Item& it, const KeyLimit& lim, bool valid, uint64_t bits,
                                                uint64_t idx, uint64_t* ws_r, uint32_t* ws_idx, unsigned& cnt,
                                                uint64_t* cand_r, uint32_t* cand_rid, unsigned* s_cand) {
-    const bool hit = valid && (F32 ? pass_f32(static_cast<uint32_t>(bits), lim) : pass_i64(bits, lim));
+    const bool hit = valid && (W4 ? pass32(static_cast<uint32_t>(bits), lim) : pass64(bits, lim));
     const unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
     if (!bal) return;
     if (cnt + __popc(bal) > BT_WS) cta_flush_stage(ws_r, ws_idx, cnt, it, cand_r, cand_rid, s_cand);
     const unsigned lane = threadIdx.x & 31u;
     if (hit) {
         const unsigned pos = cnt + __popc(bal & ((1u << lane) - 1u));
-        ws_r[pos] = F32 ? rank_f32(static_cast<uint32_t>(bits), it.desc) : rank_i64(bits, it.desc);
+        ws_r[pos] = rank_key(bits, it.kind, it.desc);
         ws_idx[pos] = static_cast<uint32_t>(idx);
     }
     cnt += __popc(bal);
 }
 
 // The streaming pass of one item by one CTA.  Returns the candidate count.
-template <bool F32>
+template <bool W4>
 __device__ unsigned cta_filter(const Item& it, uint64_t t, unsigned char* smem, uint64_t* cand_r,
                                uint32_t* cand_rid, unsigned* s_cand) {
-    const KeyLimit lim = key_limit(t, it.desc);
+    const KeyLimit lim = key_limit(t, it.kind, it.desc);
     const unsigned w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     uint64_t* ws_r = reinterpret_cast<uint64_t*>(smem + w * BT_WS * 12);
     uint32_t* ws_idx = reinterpret_cast<uint32_t*>(smem + w * BT_WS * 12 + BT_WS * 8);
     unsigned cnt = 0;
     if (threadIdx.x == 0) *s_cand = 0;
     __syncthreads();
-    constexpr int W = F32 ? 4 : 8;
+    constexpr int W = W4 ? 4 : 8;
     const uint64_t n = it.n;
     const uintptr_t addr = reinterpret_cast<uintptr_t>(it.keys);
     const uint64_t head0 = ((16 - (addr & 15)) & 15) / W;
@@ -193,15 +194,15 @@ __device__ unsigned cta_filter(const Item& it, uint64_t t, unsigned char* smem, 
             const uint64_t vi = bb + static_cast<uint64_t>(u) * BT_TPB + threadIdx.x;
             const bool ok = vi < nvec;
             const uint64_t i0 = head + vi * VEC;
-            if (F32) {
+            if (W4) {
                 const uint32_t x[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    cta_filter_key<F32>(it, lim, ok, x[e], i0 + e, ws_r, ws_idx, cnt, cand_r, cand_rid, s_cand);
+                    cta_filter_key<W4>(it, lim, ok, x[e], i0 + e, ws_r, ws_idx, cnt, cand_r, cand_rid, s_cand);
             } else {
-                cta_filter_key<F32>(it, lim, ok, static_cast<uint64_t>(v[u].x) | (static_cast<uint64_t>(v[u].y) << 32),
+                cta_filter_key<W4>(it, lim, ok, static_cast<uint64_t>(v[u].x) | (static_cast<uint64_t>(v[u].y) << 32),
                                i0, ws_r, ws_idx, cnt, cand_r, cand_rid, s_cand);
-                cta_filter_key<F32>(it, lim, ok, static_cast<uint64_t>(v[u].z) | (static_cast<uint64_t>(v[u].w) << 32),
+                cta_filter_key<W4>(it, lim, ok, static_cast<uint64_t>(v[u].z) | (static_cast<uint64_t>(v[u].w) << 32),
                                i0 + 1, ws_r, ws_idx, cnt, cand_r, cand_rid, s_cand);
             }
         }
@@ -213,9 +214,9 @@ __device__ unsigned cta_filter(const Item& it, uint64_t t, unsigned char* smem, 
         uint64_t idx = 0, bits = 0;
         if (ok) {
             idx = lane < head ? lane : tail0 + (lane - head);
-            bits = F32 ? static_cast<const uint32_t*>(it.keys)[idx] : static_cast<const uint64_t*>(it.keys)[idx];
+            bits = W4 ? static_cast<const uint32_t*>(it.keys)[idx] : static_cast<const uint64_t*>(it.keys)[idx];
         }
-        cta_filter_key<F32>(it, lim, ok, bits, idx, ws_r, ws_idx, cnt, cand_r, cand_rid, s_cand);
+        cta_filter_key<W4>(it, lim, ok, bits, idx, ws_r, ws_idx, cnt, cand_r, cand_rid, s_cand);
     }
     cta_flush_stage(ws_r, ws_idx, cnt, it, cand_r, cand_rid, s_cand);
     __syncthreads();
@@ -252,7 +253,7 @@ __device__ void cta_topk(const Item& it, unsigned char* smem, uint64_t* cand_r, 
         if (threadIdx.x == 0) *it.count = kk;
         return;
     }
-    const int kb = it.f32 ? 32 : 64;
+    const int kb = it.w4 ? 32 : 64;
     const int TB = kb + 32;
     bool cand = false;
     uint64_t src_n = n;
@@ -263,7 +264,7 @@ __device__ void cta_topk(const Item& it, unsigned char* smem, uint64_t* cand_r, 
         if (r > BT_SAMPLE) r = BT_SAMPLE;
         const uint64_t t = cta_sample_threshold(it, r, hist, sc, digit);
         __syncthreads();
-        const unsigned c = it.f32 ? cta_filter<true>(it, t, smem, cand_r, cand_rid, &s_misc[0])
+        const unsigned c = it.w4 ? cta_filter<true>(it, t, smem, cand_r, cand_rid, &s_misc[0])
                                   : cta_filter<false>(it, t, smem, cand_r, cand_rid, &s_misc[0]);
         if (c >= kk && c <= BT_CAND) {
             cand = true;
@@ -364,7 +365,9 @@ __device__ int item_check(const Item& it) {
     if (it.op == OLAP_OP_TOPK) {
         if (it.k > BT_SMALL) return OLAP_E_DEVICE;
         if (it.k && it.n && (!it.out_keys || !it.out_rowids)) return OLAP_E_DEVICE;
-        if (reinterpret_cast<uintptr_t>(it.keys) % (it.f32 ? 4 : 8)) return OLAP_E_DEVICE;
+        if (it.kind < OLAP_KEY_I64 || it.kind > OLAP_KEY_U32 || it.w4 != (key_bytes(it.kind) == 4))
+            return OLAP_E_DEVICE;
+        if (reinterpret_cast<uintptr_t>(it.keys) % (it.w4 ? 4 : 8)) return OLAP_E_DEVICE;
     } else {
         if (!it.table || ((it.mask + 1) & it.mask)) return OLAP_E_DEVICE;
         if (it.cap && !it.out_pairs) return OLAP_E_DEVICE;
@@ -543,15 +546,16 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
         d.count = reinterpret_cast<unsigned long long*>(x.count);
         d.status = x.status;
         if (x.op == OLAP_OP_TOPK) {
-            if (x.key_type != OLAP_KEY_I64 && x.key_type != OLAP_KEY_F32)
+            if (x.key_type < OLAP_KEY_I64 || x.key_type > OLAP_KEY_U32)
                 return fail(ctx, OLAP_E_INVALID, "batch item: bad key type");
             if (x.k > BT_SMALL) return fail(ctx, OLAP_E_INVALID, "batch item: Top-K k above 4096 (use olap_topk)");
-            d.f32 = x.key_type == OLAP_KEY_F32;
+            d.kind = x.key_type;
+            d.w4 = key_bytes(x.key_type) == 4;
             d.desc = x.order == OLAP_DESC;
             d.k = x.k;
             d.out_keys = x.out_keys;
             d.out_rowids = x.out_rowids;
-            cost[i] = static_cast<double>(x.n) * (d.f32 ? 4.0 : 8.0);
+            cost[i] = static_cast<double>(x.n) * (d.w4 ? 4.0 : 8.0);
         } else if (x.op == OLAP_OP_PROBE) {
             if (!x.table || !x.table->slots) return fail(ctx, OLAP_E_INVALID, "batch item: NULL join table");
             if (x.table->device != ctx->device) return fail(ctx, OLAP_E_INVALID, "batch item: table on another device");

@@ -131,42 +131,69 @@ __device__ void block_sort(uint64_t* sr, uint32_t* srid, int count) {
 
 // The threshold of the streaming pass moved into the key domain, so that a
 // key is tested with one XOR and one unsigned comparison and no transform:
-// `rank <= t` holds exactly when `(key ^ m) >= c` for the (m, c) below.
-//   int64: rank = key ^ SIGN (ASC) or its complement (DESC); the signed key
-//     order is the unsigned order of key ^ SIGN, and "<=" becomes ">=" on
-//     the complement.
-//   float32: the rank's significant half u(x) is <= t32 = t >> 32 (its low
-//     half is zero).  With y = x ^ ((x >> 31) & 0x7FFFFFFF) the signed image of
-//     totalOrder and L the signed limit on y, each of the four cases (order x
-//     sign of L) is one unsigned comparison of x under a fixed XOR mask:
-//       DESC, L >= 0: y >= L  <=>  x ^ 0x80000000 >= L ^ 0x80000000
-//       DESC, L <  0: y >= L  <=>  ~x >= ~(L ^ 0x7FFFFFFF)
-//       ASC,  L >= 0: y <= L  <=>  x ^ 0x7FFFFFFF >= L ^ 0x7FFFFFFF
-//       ASC,  L <  0: y <= L  <=>  x >= L ^ 0x7FFFFFFF
-//     (XOR with 0x7FFFFFFF reverses the signed order among negative values.)
+// `rank <= t` holds exactly when `(key ^ m) >= c` for the (m, c) below (m64 /
+// c64 for 8-byte keys, m32 / c32 for 4-byte keys, whose rank is t's upper
+// half t32 = t >> 32; the lower half of a 4-byte key's rank is zero).
+//   signed integers: rank = key ^ SIGN (ASC) or its complement (DESC); the
+//     signed key order is the unsigned order of key ^ SIGN, and "<=" becomes
+//     ">=" on the complement.
+//   unsigned integers: ASC  key <= t  <=>  ~key >= ~t;  DESC  ~key <= t  <=>  key >= ~t.
+//   floats: with y = x ^ ((x >> (w-1)) & MAG) the signed image of totalOrder
+//     (MAG = all bits but the sign) and L the signed limit on y, each of the
+//     four cases (order x sign of L) is one unsigned comparison of x under a
+//     fixed XOR mask:
+//       DESC, L >= 0: y >= L  <=>  x ^ SIGN >= L ^ SIGN
+//       DESC, L <  0: y >= L  <=>  ~x >= ~(L ^ MAG)
+//       ASC,  L >= 0: y <= L  <=>  x ^ MAG >= L ^ MAG
+//       ASC,  L <  0: y <= L  <=>  x >= L ^ MAG
+//     (XOR with MAG reverses the signed order among negative values.)
 struct KeyLimit {
     uint64_t m64, c64;
     uint32_t m32, c32;
 };
-__device__ __forceinline__ KeyLimit key_limit(uint64_t t, bool desc) {
-    KeyLimit k;
-    const uint64_t lim = (desc ? ~t : t) ^ SIGN64;              // signed limit on the int64 key
-    // DESC: key >= lim  <=> key ^ SIGN >= lim ^ SIGN;  ASC: key <= lim <=> key ^ ~SIGN >= lim ^ ~SIGN
-    k.m64 = desc ? SIGN64 : ~SIGN64;
-    k.c64 = lim ^ k.m64;
-    const uint32_t t32 = static_cast<uint32_t>(t >> 32);
-    const int32_t L = static_cast<int32_t>((desc ? ~t32 : t32) ^ 0x80000000u);
-    const uint32_t uL = static_cast<uint32_t>(L);
+
+template <typename U>
+__device__ __forceinline__ void float_limit(U t, bool desc, U* m, U* c) {
+    constexpr U SIGN = static_cast<U>(1) << (sizeof(U) * 8 - 1);
+    constexpr U MAG = ~SIGN;
+    const U uL = (desc ? static_cast<U>(~t) : t) ^ SIGN;          // signed limit on y, as bits
+    const bool neg = (uL & SIGN) != 0;
     if (desc) {
-        if (L >= 0) { k.m32 = 0x80000000u; k.c32 = uL ^ 0x80000000u; }
-        else        { k.m32 = 0xFFFFFFFFu; k.c32 = ~(uL ^ 0x7FFFFFFFu); }
+        if (!neg) { *m = SIGN; *c = uL ^ SIGN; }
+        else      { *m = static_cast<U>(~static_cast<U>(0)); *c = static_cast<U>(~(uL ^ MAG)); }
     } else {
-        if (L >= 0) { k.m32 = 0x7FFFFFFFu; k.c32 = uL ^ 0x7FFFFFFFu; }
-        else        { k.m32 = 0u;          k.c32 = uL ^ 0x7FFFFFFFu; }
+        if (!neg) { *m = MAG; *c = uL ^ MAG; }
+        else      { *m = 0;   *c = uL ^ MAG; }
+    }
+}
+
+template <typename U>
+__device__ __forceinline__ void int_limit(U t, bool desc, bool is_signed, U* m, U* c) {
+    constexpr U SIGN = static_cast<U>(1) << (sizeof(U) * 8 - 1);
+    if (is_signed) {
+        const U lim = (desc ? static_cast<U>(~t) : t) ^ SIGN;      // signed limit on the key
+        *m = desc ? SIGN : static_cast<U>(~SIGN);
+        *c = lim ^ *m;
+    } else {
+        *m = desc ? static_cast<U>(0) : static_cast<U>(~static_cast<U>(0));
+        *c = static_cast<U>(~t);
+    }
+}
+
+__device__ __forceinline__ KeyLimit key_limit(uint64_t t, int kind, bool desc) {
+    KeyLimit k{0, 0, 0, 0};
+    const uint32_t t32 = static_cast<uint32_t>(t >> 32);
+    switch (kind) {
+        case OLAP_KEY_I64: int_limit<uint64_t>(t, desc, true, &k.m64, &k.c64); break;
+        case OLAP_KEY_U64: int_limit<uint64_t>(t, desc, false, &k.m64, &k.c64); break;
+        case OLAP_KEY_F64: float_limit<uint64_t>(t, desc, &k.m64, &k.c64); break;
+        case OLAP_KEY_I32: int_limit<uint32_t>(t32, desc, true, &k.m32, &k.c32); break;
+        case OLAP_KEY_U32: int_limit<uint32_t>(t32, desc, false, &k.m32, &k.c32); break;
+        default: float_limit<uint32_t>(t32, desc, &k.m32, &k.c32); break;   // float32
     }
     return k;
 }
-__device__ __forceinline__ bool pass_i64(uint64_t bits, const KeyLimit& k) { return (bits ^ k.m64) >= k.c64; }
-__device__ __forceinline__ bool pass_f32(uint32_t bits, const KeyLimit& k) { return (bits ^ k.m32) >= k.c32; }
+__device__ __forceinline__ bool pass64(uint64_t bits, const KeyLimit& k) { return (bits ^ k.m64) >= k.c64; }
+__device__ __forceinline__ bool pass32(uint32_t bits, const KeyLimit& k) { return (bits ^ k.m32) >= k.c32; }
 
 }  // namespace olap

@@ -19,29 +19,47 @@ constexpr long long WAIT_LIMIT_CYCLES = 2000000000ll;
 // Order-preserving transform of a key into an unsigned "rank word".  Selection
 // in either order then becomes "smallest rank words first", with the row-id
 // ascending as the second field of the composite (key, row-id) order.
-//   int64: flip the sign bit (two's complement -> offset binary).
-//   float32: IEEE 754 totalOrder as an unsigned order: negative patterns are
+//   signed integers: flip the sign bit (two's complement -> offset binary).
+//   unsigned integers: the bits as they are.
+//   floats: IEEE 754 totalOrder as an unsigned order: negative patterns are
 //   inverted, non-negative ones get the sign bit set.
 //   DESC: the word is complemented.
-// The float word is left-aligned in 64 bits, so every rank word is 64 bits and
-// its first `key_bits` bits are significant.
+// A 4-byte key's word is left-aligned in 64 bits, so every rank word is 64
+// bits and its first `key_bits` bits are significant.
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ uint64_t rank_i64(uint64_t bits, bool desc) {
-    const uint64_t u = bits ^ SIGN64;
-    return desc ? ~u : u;
+// Every key type (olap_key_type): width and the rank word of raw key bits
+// (4-byte keys in the low half of `bits`), and back.
+__host__ __device__ __forceinline__ int key_bytes(int kind) {
+    return (kind == OLAP_KEY_F32 || kind == OLAP_KEY_I32 || kind == OLAP_KEY_U32) ? 4 : 8;
 }
-__host__ __device__ __forceinline__ uint64_t rank_f32(uint32_t bits, bool desc) {
-    uint32_t u = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
+__host__ __device__ __forceinline__ uint64_t rank_key(uint64_t bits, int kind, bool desc) {
+    if (key_bytes(kind) == 8) {
+        uint64_t u;
+        if (kind == OLAP_KEY_I64) u = bits ^ SIGN64;
+        else if (kind == OLAP_KEY_U64) u = bits;
+        else u = (bits & SIGN64) ? ~bits : (bits | SIGN64);        // float64
+        return desc ? ~u : u;
+    }
+    const uint32_t b = static_cast<uint32_t>(bits);
+    uint32_t u;
+    if (kind == OLAP_KEY_I32) u = b ^ 0x80000000u;
+    else if (kind == OLAP_KEY_U32) u = b;
+    else u = (b & 0x80000000u) ? ~b : (b | 0x80000000u);            // float32
     if (desc) u = ~u;
     return static_cast<uint64_t>(u) << 32;
 }
-__host__ __device__ __forceinline__ uint64_t unrank_i64(uint64_t r, bool desc) {
-    return (desc ? ~r : r) ^ SIGN64;
-}
-__host__ __device__ __forceinline__ uint32_t unrank_f32(uint64_t r, bool desc) {
+__host__ __device__ __forceinline__ uint64_t unrank_key(uint64_t r, int kind, bool desc) {
+    if (key_bytes(kind) == 8) {
+        const uint64_t u = desc ? ~r : r;
+        if (kind == OLAP_KEY_I64) return u ^ SIGN64;
+        if (kind == OLAP_KEY_U64) return u;
+        return (u & SIGN64) ? (u & ~SIGN64) : ~u;                   // float64
+    }
     uint32_t u = static_cast<uint32_t>(r >> 32);
     if (desc) u = ~u;
-    return (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+    if (kind == OLAP_KEY_I32) return u ^ 0x80000000u;
+    if (kind == OLAP_KEY_U32) return u;
+    return (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : static_cast<uint32_t>(~u);
 }
 
 // ---------------------------------------------------------------------------

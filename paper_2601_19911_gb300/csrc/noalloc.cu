@@ -73,14 +73,14 @@ olap_status setup_device(int dev, DeviceSetup* out) {
 extern "C" olap_status olap_topk_noalloc(const void* d_keys, olap_key_type type, const uint32_t* d_rowids,
                                          uint64_t n, uint64_t k, olap_order order, void* d_out_keys,
                                          uint32_t* d_out_rowids, int32_t* dev_status, void* stream) {
-    if (type != OLAP_KEY_I64 && type != OLAP_KEY_F32) return OLAP_E_INVALID;
+    if (type < OLAP_KEY_I64 || type > OLAP_KEY_U32) return OLAP_E_INVALID;
     if (order != OLAP_ASC && order != OLAP_DESC) return OLAP_E_INVALID;
     // Sizes beyond the fixed array are refused before anything is launched.
     if (n > OLAP_NOALLOC_MAX_N || k > OLAP_NOALLOC_MAX_K) return OLAP_E_INVALID;
     const uint64_t kk = k < n ? k : n;
     if (n && !d_keys) return OLAP_E_INVALID;
     if (kk && (!d_out_keys || !d_out_rowids)) return OLAP_E_INVALID;
-    const size_t w = type == OLAP_KEY_I64 ? 8 : 4;
+    const size_t w = olap::key_bytes(type);
     if (reinterpret_cast<uintptr_t>(d_keys) % w) return OLAP_E_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (kk == 0) {
@@ -106,7 +106,8 @@ extern "C" olap_status olap_topk_noalloc(const void* d_keys, olap_key_type type,
     a.rowids = d_rowids;
     a.n = n;
     a.k = kk;
-    a.f32 = type == OLAP_KEY_F32;
+    a.kind = type;
+    a.w4 = olap::key_bytes(type) == 4;
     a.desc = order == OLAP_DESC;
     olap::topk_carve(a, plan, ds.scratch);
     a.filter = olap::TK_FILTER_REGS;

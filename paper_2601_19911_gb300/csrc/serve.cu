@@ -36,7 +36,7 @@ double ms_since(Clock::time_point t0) {
 uint64_t device_need(const olap_serve_request& r, const olap_ctx* ctx) {
     const uint64_t rid = r.rowids ? 4 * r.n : 0;
     if (r.op == OLAP_OP_TOPK) {
-        const uint64_t w = r.key_type == OLAP_KEY_F32 ? 4 : 8;
+        const uint64_t w = olap::key_bytes(r.key_type);
         const uint64_t kk = std::min(r.k, r.n);
         return r.n * w + rid + olap::topk_scratch_bytes(olap::topk_plan(r.n, kk), kk) + kk * (w + 4) + 4096;
     }
@@ -54,7 +54,7 @@ bool decide_gpu(const olap_serve_request& r, const olap_serve_opts& o) {
     const double rid = r.rowids ? 4.0 : 0.0;
     olap_gate_decision d;
     if (r.op == OLAP_OP_TOPK) {
-        const double w = r.key_type == OLAP_KEY_F32 ? 4.0 : 8.0;
+        const double w = olap::key_bytes(r.key_type);
         q.op = OLAP_OP_TOPK;
         q.k_or_m = static_cast<double>(r.k);
         q.tx_bytes = nd * (w + rid);
@@ -195,7 +195,7 @@ extern "C" olap_status olap_serve(olap_serve_request* reqs, uint64_t n, const ol
         S.need[i] = device_need(r, ctxs.empty() ? nullptr : ctxs[0]);
         const uint64_t rid = r.rowids ? 4 * r.n : 0;
         if (r.op == OLAP_OP_TOPK) {
-            const uint64_t w = r.key_type == OLAP_KEY_F32 ? 4 : 8;
+            const uint64_t w = olap::key_bytes(r.key_type);
             const uint64_t kk = std::min(r.k, r.n);
             max_in = std::max<uint64_t>(max_in, ((r.n * w + 255) & ~255ull) + rid);
             max_out = std::max<uint64_t>(max_out, ((kk * w + 255) & ~255ull) + kk * 4);

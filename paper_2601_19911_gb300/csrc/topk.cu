@@ -45,10 +45,9 @@ struct Elem {
 
 __device__ __forceinline__ Elem load_input(const TopkArgs& a, uint64_t i) {
     Elem e;
-    if (a.f32)
-        e.r = rank_f32(static_cast<const uint32_t*>(a.keys)[i], a.desc);
-    else
-        e.r = rank_i64(static_cast<const uint64_t*>(a.keys)[i], a.desc);
+    const uint64_t bits = a.w4 ? static_cast<uint64_t>(static_cast<const uint32_t*>(a.keys)[i])
+                               : static_cast<const uint64_t*>(a.keys)[i];
+    e.r = rank_key(bits, a.kind, a.desc);
     e.rid = a.rowids ? a.rowids[i] : static_cast<uint32_t>(i);
     return e;
 }
@@ -59,10 +58,10 @@ __device__ __forceinline__ Elem load_src(const TopkArgs& a, bool cand, uint64_t 
 }
 
 __device__ __forceinline__ void write_result(const TopkArgs& a, uint64_t i, uint64_t r, uint32_t rid) {
-    if (a.f32)
-        static_cast<uint32_t*>(a.out_keys)[i] = unrank_f32(r, a.desc);
+    if (a.w4)
+        static_cast<uint32_t*>(a.out_keys)[i] = static_cast<uint32_t>(unrank_key(r, a.kind, a.desc));
     else
-        static_cast<uint64_t*>(a.out_keys)[i] = unrank_i64(r, a.desc);
+        static_cast<uint64_t*>(a.out_keys)[i] = unrank_key(r, a.kind, a.desc);
     a.out_rowids[i] = rid;
 }
 
@@ -80,7 +79,7 @@ __device__ uint64_t sample_threshold(const TopkArgs& a, unsigned* sh, unsigned l
         const uint64_t pos = (idx * n) / TK_SAMPLE + (n / TK_SAMPLE) / 2;
         s[j] = load_input(a, pos).r;
     }
-    const int kb = a.f32 ? 32 : 64;
+    const int kb = a.w4 ? 32 : 64;
     const unsigned long long r = a.sample_rank;
     uint64_t prefix = 0;
     unsigned long long rem = r, cum = 0;
@@ -144,26 +143,26 @@ __device__ __forceinline__ void stage_flush(const TopkArgs& a, WarpStage& ws) {
 // Test the VEC keys of one 16-byte vector (keys idx0 .. idx0 + VEC - 1)
 // against the threshold and stage the hits.  Called by all 32 lanes of a
 // warp together.
-template <bool F32>
+template <bool W4>
 __device__ __forceinline__ void filter_vector(const TopkArgs& a, const KeyLimit& lim, uint4 x, bool valid,
                                               uint64_t idx0, WarpStage& ws) {
-    constexpr int VEC = F32 ? 4 : 2;
+    constexpr int VEC = W4 ? 4 : 2;
     bool any;
-    if (F32) {
-        any = pass_f32(x.x, lim) | pass_f32(x.y, lim) | pass_f32(x.z, lim) | pass_f32(x.w, lim);
+    if (W4) {
+        any = pass32(x.x, lim) | pass32(x.y, lim) | pass32(x.z, lim) | pass32(x.w, lim);
     } else {
-        any = pass_i64(static_cast<uint64_t>(x.x) | (static_cast<uint64_t>(x.y) << 32), lim) |
-              pass_i64(static_cast<uint64_t>(x.z) | (static_cast<uint64_t>(x.w) << 32), lim);
+        any = pass64(static_cast<uint64_t>(x.x) | (static_cast<uint64_t>(x.y) << 32), lim) |
+              pass64(static_cast<uint64_t>(x.z) | (static_cast<uint64_t>(x.w) << 32), lim);
     }
     if (!__any_sync(0xFFFFFFFFu, any && valid)) return;
     unsigned hit = 0;
     if (valid) {
-        if (F32) {
-            hit = (pass_f32(x.x, lim) ? 1u : 0u) | (pass_f32(x.y, lim) ? 2u : 0u) |
-                  (pass_f32(x.z, lim) ? 4u : 0u) | (pass_f32(x.w, lim) ? 8u : 0u);
+        if (W4) {
+            hit = (pass32(x.x, lim) ? 1u : 0u) | (pass32(x.y, lim) ? 2u : 0u) | (pass32(x.z, lim) ? 4u : 0u) |
+                  (pass32(x.w, lim) ? 8u : 0u);
         } else {
-            hit = (pass_i64(static_cast<uint64_t>(x.x) | (static_cast<uint64_t>(x.y) << 32), lim) ? 1u : 0u) |
-                  (pass_i64(static_cast<uint64_t>(x.z) | (static_cast<uint64_t>(x.w) << 32), lim) ? 2u : 0u);
+            hit = (pass64(static_cast<uint64_t>(x.x) | (static_cast<uint64_t>(x.y) << 32), lim) ? 1u : 0u) |
+                  (pass64(static_cast<uint64_t>(x.z) | (static_cast<uint64_t>(x.w) << 32), lim) ? 2u : 0u);
         }
     }
     const unsigned lane = threadIdx.x & 31u;
@@ -183,8 +182,8 @@ __device__ __forceinline__ void filter_vector(const TopkArgs& a, const KeyLimit&
         if ((hit >> e) & 1u) {
             const unsigned pos = before + __popc(bal[e] & lt);
             uint64_t r;
-            if (F32) r = rank_f32(w[e], a.desc);
-            else r = rank_i64(static_cast<uint64_t>(w[2 * e]) | (static_cast<uint64_t>(w[2 * e + 1]) << 32), a.desc);
+            if (W4) r = rank_key(w[e], a.kind, a.desc);
+            else r = rank_key(static_cast<uint64_t>(w[2 * e]) | (static_cast<uint64_t>(w[2 * e + 1]) << 32), a.kind, a.desc);
             ws.r[pos] = r;
             ws.idx[pos] = static_cast<uint32_t>(idx0 + e);
         }
@@ -222,9 +221,9 @@ __device__ __forceinline__ void filter_ends(const TopkArgs& a, uint64_t t, uint6
 
 // Phase 1: the single streaming pass.  Appends (rank word, row-id) of every
 // key whose rank word is <= t; counts all of them.
-template <bool F32, int TPB>
+template <bool W4, int TPB>
 __device__ void filter_pass(const TopkArgs& a, uint64_t t, unsigned char* stage_smem) {
-    constexpr int W = F32 ? 4 : 8;
+    constexpr int W = W4 ? 4 : 8;
     constexpr int VEC = 16 / W;
     const uint64_t n = a.n;
     const uintptr_t addr = reinterpret_cast<uintptr_t>(a.keys);
@@ -233,7 +232,7 @@ __device__ void filter_pass(const TopkArgs& a, uint64_t t, unsigned char* stage_
     const uint64_t nvec = (n - head) / VEC;
     const uint64_t tail0 = head + nvec * VEC;
     const unsigned char* vbase = static_cast<const unsigned char*>(a.keys) + head * W;
-    const KeyLimit lim = key_limit(t, a.desc);
+    const KeyLimit lim = key_limit(t, a.kind, a.desc);
     WarpStage ws = warp_stage(stage_smem);
 
     const uint64_t per_block = static_cast<uint64_t>(TPB) * TK_UNROLL;
@@ -249,7 +248,7 @@ __device__ void filter_pass(const TopkArgs& a, uint64_t t, unsigned char* stage_
 #pragma unroll
         for (int u = 0; u < TK_UNROLL; ++u) {
             const uint64_t vi = bb + static_cast<uint64_t>(u) * TPB + threadIdx.x;
-            filter_vector<F32>(a, lim, v[u], vi < nvec, head + vi * VEC, ws);
+            filter_vector<W4>(a, lim, v[u], vi < nvec, head + vi * VEC, ws);
         }
     }
     stage_flush(a, ws);
@@ -273,9 +272,9 @@ __device__ __forceinline__ void issue_tile(unsigned char* smem, uint64_t* full, 
 // when its bytes land, and its "empty" mbarrier when every warp has read it,
 // after which thread 0 refills it.  No CTA-wide barrier per tile.  Returns
 // false if a copy never landed (bounded waits).
-template <bool F32, int TPB>
+template <bool W4, int TPB>
 __device__ bool filter_pass_bulk(const TopkArgs& a, uint64_t t, unsigned char* smem) {
-    constexpr int W = F32 ? 4 : 8;
+    constexpr int W = W4 ? 4 : 8;
     constexpr int VEC = 16 / W;
     constexpr unsigned NWARPS = TPB / 32;
     const uint32_t tile = static_cast<uint32_t>(a.tile_bytes);
@@ -290,7 +289,7 @@ __device__ bool filter_pass_bulk(const TopkArgs& a, uint64_t t, unsigned char* s
     const uint64_t body = nvec * 16;
     const uint64_t ntiles = (body + tile - 1) / tile;
     const uint64_t my_n = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const KeyLimit lim = key_limit(t, a.desc);
+    const KeyLimit lim = key_limit(t, a.kind, a.desc);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(tile) * stages);
     uint64_t* empty = full + TK_MAX_STAGES;
     WarpStage ws = warp_stage(reinterpret_cast<unsigned char*>(empty + TK_MAX_STAGES));
@@ -330,7 +329,7 @@ __device__ bool filter_pass_bulk(const TopkArgs& a, uint64_t t, unsigned char* s
             const bool valid = v < nv;
             uint4 x = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
             if (valid) x = ld_shared_v4(st + v * 16);
-            filter_vector<F32>(a, lim, x, valid, idx_base + static_cast<uint64_t>(v) * VEC, ws);
+            filter_vector<W4>(a, lim, x, valid, idx_base + static_cast<uint64_t>(v) * VEC, ws);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
@@ -505,20 +504,20 @@ __global__ void __launch_bounds__(TK_TPB) topk_prepare_kernel(TopkArgs a) {
 
 // Kernel 2 of 3 (sampled path only): the single streaming pass over the keys,
 // bulk-copy flavour.  Independent CTAs, several per SM.
-template <bool F32>
+template <bool W4>
 __global__ void __launch_bounds__(TKF_TPB, 4) topk_filter_bulk_kernel(TopkArgs a) {
     extern __shared__ __align__(128) unsigned char fsmem[];
     const uint64_t t = __ldcg(&a.ctl->thresh);
-    filter_pass_bulk<F32, TKF_TPB>(a, t, fsmem);
+    filter_pass_bulk<W4, TKF_TPB>(a, t, fsmem);
 }
 
 // Kernel 2 of 3, register-load flavour (TPB threads; the per-warp stages are
 // dynamic shared memory, (TPB / 32) * WS_BYTES).
-template <bool F32, int TPB>
+template <bool W4, int TPB>
 __global__ void __launch_bounds__(TPB) topk_filter_regs_kernel(TopkArgs a) {
     extern __shared__ __align__(16) unsigned char stage[];
     const uint64_t t = __ldcg(&a.ctl->thresh);
-    filter_pass<F32, TPB>(a, t, stage);
+    filter_pass<W4, TPB>(a, t, stage);
 }
 
 // Kernel 3 of 3 (cooperative): refine, split, finish and sort.
@@ -526,7 +525,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long sc[24];
     TopkCtl* ctl = a.ctl;
-    const int kb = a.f32 ? 32 : 64;
+    const int kb = a.w4 ? 32 : 64;
     const int TB = kb + 32;
     unsigned* sh = reinterpret_cast<unsigned*>(smem);
     uint64_t* sr = reinterpret_cast<uint64_t*>(smem);
@@ -1019,17 +1018,17 @@ cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t
             const size_t rs = static_cast<size_t>(geom.regs_tpb / 32) * WS_BYTES;
             const unsigned gr = static_cast<unsigned>(geom.regs_grid);
             if (geom.regs_tpb == 256) {
-                if (a.f32) topk_filter_regs_kernel<true, 256><<<gr, 256, rs, stream>>>(a);
+                if (a.w4) topk_filter_regs_kernel<true, 256><<<gr, 256, rs, stream>>>(a);
                 else topk_filter_regs_kernel<false, 256><<<gr, 256, rs, stream>>>(a);
             } else if (geom.regs_tpb == 1024) {
-                if (a.f32) topk_filter_regs_kernel<true, 1024><<<gr, 1024, rs, stream>>>(a);
+                if (a.w4) topk_filter_regs_kernel<true, 1024><<<gr, 1024, rs, stream>>>(a);
                 else topk_filter_regs_kernel<false, 1024><<<gr, 1024, rs, stream>>>(a);
             } else {
-                if (a.f32) topk_filter_regs_kernel<true, 512><<<gr, 512, rs, stream>>>(a);
+                if (a.w4) topk_filter_regs_kernel<true, 512><<<gr, 512, rs, stream>>>(a);
                 else topk_filter_regs_kernel<false, 512><<<gr, 512, rs, stream>>>(a);
             }
         } else {
-            if (a.f32)
+            if (a.w4)
                 topk_filter_bulk_kernel<true><<<geom.filter_grid, TKF_TPB, geom.smem_bytes, stream>>>(a);
             else
                 topk_filter_bulk_kernel<false><<<geom.filter_grid, TKF_TPB, geom.smem_bytes, stream>>>(a);

@@ -56,7 +56,8 @@ struct TopkArgs {
     const uint32_t* rowids;          // NULL => row-id = index
     uint64_t n;
     uint64_t k;                      // already min(k, n), > 0
-    int f32;
+    int kind;                        // olap_key_type
+    int w4;                          // 4-byte keys (float32, int32, uint32)
     int desc;
     int use_sample;
     unsigned sample_rank;            // 1-based rank of the threshold in the sample

@@ -27,11 +27,11 @@ __device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t i) {
     return z ^ (z >> 31);
 }
 
-__global__ void gen_topk_keys(void* keys, uint64_t n, int f32, uint64_t seed) {
+__global__ void gen_topk_keys(void* keys, uint64_t n, int w4, uint64_t seed) {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
     for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint64_t v = splitmix(seed, i);
-        if (f32) static_cast<uint32_t*>(keys)[i] = static_cast<uint32_t>(v >> 32);
+        if (w4) static_cast<uint32_t*>(keys)[i] = static_cast<uint32_t>(v >> 32);
         else static_cast<uint64_t*>(keys)[i] = v;
     }
 }
@@ -96,7 +96,7 @@ extern "C" olap_status olap_autotune(olap_ctx* ctx, const olap_tune_request* req
     std::memset(out, 0, sizeof(*out));
     if (req->topk_n >= (1ull << 32) || req->join_probe_n >= (1ull << 32) || req->join_build_n >= (1ull << 32))
         return fail(ctx, OLAP_E_INVALID, "tuning sizes must be below 2^32");
-    if (req->topk_n && req->topk_key_type != OLAP_KEY_I64 && req->topk_key_type != OLAP_KEY_F32)
+    if (req->topk_n && (req->topk_key_type < OLAP_KEY_I64 || req->topk_key_type > OLAP_KEY_U32))
         return fail(ctx, OLAP_E_INVALID, "bad key type");
     if (req->join_probe_n && !req->join_build_n) return fail(ctx, OLAP_E_INVALID, "probe without build rows");
     if (!(req->join_hit_rate >= 0.0 && req->join_hit_rate <= 1.0)) return fail(ctx, OLAP_E_INVALID, "bad hit rate");
@@ -130,15 +130,15 @@ extern "C" olap_status olap_autotune(olap_ctx* ctx, const olap_tune_request* req
     // ---- Top-K: filter block size, then digit width --------------------------
     if (req->topk_n) {
         const uint64_t n = req->topk_n, kk = std::min<uint64_t>(std::max<uint64_t>(req->topk_k, 1), n);
-        const bool f32 = req->topk_key_type == OLAP_KEY_F32;
-        const size_t w = f32 ? 4 : 8;
+        const bool w4 = key_bytes(req->topk_key_type) == 4;
+        const size_t w = w4 ? 4 : 8;
         DevBuf keys, ok, orow;
         if ((e = cudaMalloc(&keys.p, n * w)) != cudaSuccess || (e = cudaMalloc(&ok.p, kk * w)) != cudaSuccess ||
             (e = cudaMalloc(&orow.p, kk * 4)) != cudaSuccess) {
             cudaGetLastError();
             return cuda_fail(ctx, e, "tuning allocation");
         }
-        gen_topk_keys<<<ctx->sm_count * 4, 256, 0, s>>>(keys.p, n, f32 ? 1 : 0, req->seed);
+        gen_topk_keys<<<ctx->sm_count * 4, 256, 0, s>>>(keys.p, n, w4 ? 1 : 0, req->seed);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "tuning input");
         const olap_key_type kt = static_cast<olap_key_type>(req->topk_key_type);
         auto run = [&]() {

@@ -32,20 +32,42 @@ struct Comp {
     bool operator<(const Comp& o) const { return r < o.r || (r == o.r && rid < o.rid); }
 };
 
-inline uint64_t word_i64(uint64_t bits, bool desc) {
-    const uint64_t u = bits ^ 0x8000000000000000ull;
-    return desc ? ~u : u;
-}
-inline uint64_t word_f32(uint32_t bits, bool desc) {
-    uint32_t u = (bits & 0x80000000u) ? ~bits : (bits | 0x80000000u);
-    if (desc) u = ~u;
+// Order-preserving word of a key (4-byte keys in the low half of `bits`):
+// signed integers offset by the sign bit, unsigned as they are, floats by
+// IEEE 754 totalOrder (negatives inverted, non-negatives with the sign bit
+// set); complemented for DESC.  And its inverse.
+inline bool wide(int kind) { return kind == OLAP_KEY_I64 || kind == OLAP_KEY_F64 || kind == OLAP_KEY_U64; }
+
+inline uint64_t word(uint64_t bits, int kind, bool desc) {
+    uint64_t u;
+    switch (kind) {
+        case OLAP_KEY_I64: u = bits ^ 0x8000000000000000ull; break;
+        case OLAP_KEY_U64: u = bits; break;
+        case OLAP_KEY_F64: u = (bits >> 63) ? ~bits : (bits | 0x8000000000000000ull); break;
+        case OLAP_KEY_I32: u = static_cast<uint32_t>(bits) ^ 0x80000000u; break;
+        case OLAP_KEY_U32: u = static_cast<uint32_t>(bits); break;
+        default: {
+            const uint32_t b = static_cast<uint32_t>(bits);
+            u = (b >> 31) ? static_cast<uint32_t>(~b) : (b | 0x80000000u);
+        }
+    }
+    if (desc) u = wide(kind) ? ~u : (~u & 0xFFFFFFFFull);
     return u;
 }
-inline uint64_t unword_i64(uint64_t r, bool desc) { return (desc ? ~r : r) ^ 0x8000000000000000ull; }
-inline uint32_t unword_f32(uint64_t r, bool desc) {
-    uint32_t u = static_cast<uint32_t>(r);
-    if (desc) u = ~u;
-    return (u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u;
+
+inline uint64_t unword(uint64_t r, int kind, bool desc) {
+    uint64_t u = desc ? (wide(kind) ? ~r : (~r & 0xFFFFFFFFull)) : r;
+    switch (kind) {
+        case OLAP_KEY_I64: return u ^ 0x8000000000000000ull;
+        case OLAP_KEY_U64: return u;
+        case OLAP_KEY_F64: return (u >> 63) ? (u & 0x7FFFFFFFFFFFFFFFull) : ~u;
+        case OLAP_KEY_I32: return static_cast<uint32_t>(u) ^ 0x80000000u;
+        case OLAP_KEY_U32: return static_cast<uint32_t>(u);
+        default: {
+            const uint32_t v = static_cast<uint32_t>(u);
+            return (v >> 31) ? (v & 0x7FFFFFFFu) : static_cast<uint32_t>(~v);
+        }
+    }
 }
 
 struct Table {
@@ -151,7 +173,8 @@ void parallel(Engine* E, int t, uint64_t n, F&& f) {
 }
 
 int run_topk(Engine* E, olap_serve_request* r) {
-    const bool f32 = r->key_type == OLAP_KEY_F32, desc = r->order == OLAP_DESC;
+    const int kind = r->key_type;
+    const bool desc = r->order == OLAP_DESC, w8 = wide(kind);
     const uint64_t n = r->n, kk = std::min(r->k, n);
     if (kk == 0) {
         r->out_count = 0;
@@ -161,8 +184,8 @@ int run_topk(Engine* E, olap_serve_request* r) {
     std::vector<std::vector<Comp>> part(t);
     auto comp = [&](uint64_t i) {
         Comp c;
-        c.r = f32 ? word_f32(static_cast<const uint32_t*>(r->keys)[i], desc)
-                  : word_i64(static_cast<const uint64_t*>(r->keys)[i], desc);
+        c.r = word(w8 ? static_cast<const uint64_t*>(r->keys)[i] : static_cast<const uint32_t*>(r->keys)[i], kind,
+                   desc);
         c.rid = r->rowids ? r->rowids[i] : static_cast<uint32_t>(i);
         return c;
     };
@@ -197,8 +220,8 @@ int run_topk(Engine* E, olap_serve_request* r) {
     if (all.size() > kk) std::nth_element(all.begin(), all.begin() + static_cast<long>(kk), all.end());
     std::sort(all.begin(), all.begin() + static_cast<long>(kk));
     for (uint64_t i = 0; i < kk; ++i) {
-        if (f32) static_cast<uint32_t*>(r->out_keys)[i] = unword_f32(all[i].r, desc);
-        else static_cast<uint64_t*>(r->out_keys)[i] = unword_i64(all[i].r, desc);
+        if (w8) static_cast<uint64_t*>(r->out_keys)[i] = unword(all[i].r, kind, desc);
+        else static_cast<uint32_t*>(r->out_keys)[i] = static_cast<uint32_t>(unword(all[i].r, kind, desc));
         r->out_rowids[i] = all[i].rid;
     }
     r->out_count = kk;

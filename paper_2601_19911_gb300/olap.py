@@ -20,7 +20,9 @@ from . import build as _build
 OK, E_INVALID, E_NOMEM, E_CUDA, E_OVERFLOW, E_TIMEOUT, E_UNIMPLEMENTED, E_DEVICE = range(8)
 STATUS_NAMES = ["OK", "E_INVALID", "E_NOMEM", "E_CUDA", "E_OVERFLOW", "E_TIMEOUT",
                 "E_UNIMPLEMENTED", "E_DEVICE"]
-KEY_I64, KEY_F32 = 0, 1
+KEY_I64, KEY_F32, KEY_F64, KEY_U64, KEY_I32, KEY_U32 = 0, 1, 2, 3, 4, 5
+KEY_NUMPY = {KEY_I64: np.int64, KEY_F32: np.float32, KEY_F64: np.float64, KEY_U64: np.uint64,
+             KEY_I32: np.int32, KEY_U32: np.uint32}
 ASC, DESC = 0, 1
 MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 
@@ -284,17 +286,17 @@ def ptr(buf) -> int | None:
 def key_type_of(buf) -> int:
     dt = buf.dtype
     if isinstance(buf, np.ndarray):
-        if dt == np.int64:
-            return KEY_I64
-        if dt == np.float32:
-            return KEY_F32
+        for kind, npdt in KEY_NUMPY.items():
+            if dt == npdt:
+                return kind
     else:
         torch = _torch()
-        if dt == torch.int64:
-            return KEY_I64
-        if dt == torch.float32:
-            return KEY_F32
-    raise TypeError(f"keys must be int64 or float32, got {dt}")
+        names = {KEY_I64: "int64", KEY_F32: "float32", KEY_F64: "float64", KEY_U64: "uint64",
+                 KEY_I32: "int32", KEY_U32: "uint32"}
+        for kind, nm in names.items():
+            if getattr(torch, nm, None) is not None and dt == getattr(torch, nm):
+                return kind
+    raise TypeError(f"keys must be int64, float32, float64, uint64, int32 or uint32, got {dt}")
 
 
 def numel(buf) -> int:
@@ -365,7 +367,7 @@ class Context:
         kt = key_type_of(keys)
         cnt = min(int(k), n)
         if out_keys is None:
-            out_keys = np.empty(max(cnt, 1), dtype=np.int64 if kt == KEY_I64 else np.float32)
+            out_keys = np.empty(max(cnt, 1), dtype=KEY_NUMPY[kt])
             out_rowids = np.empty(max(cnt, 1), dtype=np.uint32)
         where = mem_kind(keys)
         if rowids is not None:

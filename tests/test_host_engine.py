@@ -19,7 +19,8 @@ def eng():
 
 
 @pytest.mark.parametrize("kt,dist", [("i64", "uniform"), ("f32", "uniform"), ("i64", "dup1024"),
-                                     ("f32", "ascending")])
+                                     ("f32", "ascending"), ("f64", "uniform"), ("f64", "ascending"),
+                                     ("u64", "uniform"), ("i32", "dup1024"), ("u32", "uniform")])
 @pytest.mark.parametrize("n", [1, 1000, 200_003])
 def test_topk_matches_oracle(eng, kt, dist, n):
     keys = datagen.topk_keys(n, dist, kt, seed=n)
