@@ -612,9 +612,53 @@ def serving_leg(args, ctx, torch):
                      "topk_n_star_k100": int(nstar), "calibration_points": len(cal_n)}}
 
 
+def _gpu_cpu_affinity(index: int):
+    """CPU cores local to GPU `index` from `nvidia-smi topo -m` (its "CPU
+    Affinity" column), as a set, or None when unknown."""
+    import subprocess
+    try:
+        out = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True, timeout=30).stdout
+    except Exception:
+        return None
+    lines = [ln for ln in out.splitlines() if ln.strip()]
+    if not lines:
+        return None
+    head = lines[0].split("\t")
+    col = next((i for i, h in enumerate(head) if "CPU Affinity" in h), None)
+    row = next((ln for ln in lines[1:] if ln.split("\t")[0].strip() == f"GPU{index}"), None)
+    if col is None or row is None:
+        return None
+    fields = row.split("\t")
+    if col >= len(fields):
+        return None
+    cpus = set()
+    try:
+        for part in fields[col].strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+    except ValueError:
+        return None
+    return cpus or None
+
+
+def _bind_near_gpu(index: int):
+    """Run this process on the cores of the GPU's own socket, so host buffers
+    (first-touch) sit next to its NVLink-C2C link; returns the binding made."""
+    cpus = _gpu_cpu_affinity(index)
+    if not cpus:
+        return None
+    try:
+        os.sched_setaffinity(0, cpus & os.sched_getaffinity(0) or cpus)
+    except OSError:
+        return None
+    got = sorted(os.sched_getaffinity(0))
+    return f"{got[0]}-{got[-1]} ({len(got)} cores)"
+
+
 def run_ours(args):
     import torch
     world, rank, local = _dist()
+    affinity = _bind_near_gpu(local if world > 1 else 0)
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -703,6 +747,7 @@ def run_ours(args):
         "config": {"workload": f"topk_{args.key_type}_{args.dist}_n2^{args.log2n}_k{k}_desc", "n": n, "k": k,
                    "order": "desc", "rowids": args.rowids,
                    "l2": f"inputs larger than L2 ({n * w / 2**30:.2f} GiB keys)",
+                   "cpu_affinity": affinity,
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
