@@ -364,6 +364,79 @@ def _median_ms(fn, reps=3):
     return float(np.median(ts))
 
 
+def fullrow_leg(args, ctx, torch):
+    """Full-row vs key-only transfer with late materialization (Sec. V-E, the
+    Stage-1 proxy; Sec. II-C).  A table of N rows, each a float64 key (the
+    paper's `value double`) followed by a payload of `--fullrow-payload`
+    bytes, in pinned host memory, and its key column (a columnar engine's
+    key-only source).  ORDER BY key DESC LIMIT 100:
+      * full row: olap_topk_rows moves the whole rows H2D, extracts the keys,
+        selects and returns the 100 rows whole;
+      * key only: olap_topk moves only the key column (row-ids implicit) and
+        returns 100 row-ids; the host then gathers those 100 rows (late
+        materialization).
+    Also the H2D copy alone of each (the transfer term), and the host cost of
+    cutting the key column out of the row table for a row store.  Medians."""
+    from paper_2601_19911_gb300 import datagen, olap
+    P = args.fullrow_payload
+    rb = 8 + P
+    host = olap.HostEngine(threads=args.serve_cpu_workers)
+    kk = 100
+    reps = args.fullrow_reps
+    out = {}
+    for n in (3_000_000, 1 << 24):
+        keys = datagen.topk_keys(n, "uniform", "f64", seed=7)
+        rows = torch.empty((n, rb), dtype=torch.uint8).pin_memory()
+        rn = rows.numpy()
+        rn[:, 8:] = np.frombuffer(datagen.splitmix64(8, (n * P + 7) // 8).tobytes(), dtype=np.uint8)[: n * P] \
+            .reshape(n, P)
+        rn[:, :8] = keys.view(np.uint8).reshape(n, 8)
+        kcol = torch.from_numpy(keys).pin_memory()
+        orows = torch.empty(kk * rb, dtype=torch.uint8).pin_memory()
+        orid = torch.empty(kk, dtype=torch.int32).pin_memory()
+        okeys = torch.empty(kk, dtype=torch.float64).pin_memory()
+        dev_rows = torch.empty((n, rb), dtype=torch.uint8, device="cuda")
+        dev_keys = torch.empty(n, dtype=torch.float64, device="cuda")
+
+        def full():
+            ctx.topk_rows(rows, rb, 0, olap.KEY_F64, kk, olap.DESC, out_rows=orows, out_rowids=orid)
+
+        def key_only():
+            _, rid = ctx.topk(kcol, kk, olap.DESC, out_keys=okeys, out_rowids=orid)
+            return rn[rid.numpy().view(np.uint32)]                  # late materialization on the host
+
+        def tx_rows():
+            dev_rows.copy_(rows, non_blocking=True)
+            torch.cuda.synchronize()
+
+        def tx_keys():
+            dev_keys.copy_(kcol, non_blocking=True)
+            torch.cuda.synchronize()
+
+        def extract():
+            host.extract(rn, rb, 0, np.float64)
+
+        got = key_only()
+        full()
+        assert np.array_equal(got.reshape(-1), orows.numpy()[: kk * rb])   # same rows either way
+        t = {nm: _median_ms(fn, reps) for nm, fn in (("full_row_e2e", full), ("key_only_e2e", key_only),
+                                                     ("full_row_transfer", tx_rows),
+                                                     ("key_only_transfer", tx_keys),
+                                                     ("row_store_key_extraction", extract))}
+        out[f"n{n}"] = {**{k: round(v, 4) for k, v in t.items()},
+                        "transfer_reduction": t["full_row_transfer"] / t["key_only_transfer"],
+                        "e2e_speedup": t["full_row_e2e"] / t["key_only_e2e"],
+                        "e2e_speedup_row_store": t["full_row_e2e"] / (t["key_only_e2e"] +
+                                                                      t["row_store_key_extraction"]),
+                        "bytes_full_row": n * rb, "bytes_key_only": n * 8}
+        del rows, kcol, dev_rows, dev_keys
+        torch.cuda.empty_cache()
+    host.close()
+    return {"metric": "full-row vs key-only + late materialization (Top-100, float64 key)",
+            "host_threads": args.serve_cpu_workers,
+            "payload_bytes": P, "row_bytes": rb, "reps": reps, "unit": "ms (medians) and ratios", **out}
+
+
 def _crossover(ns, gain):
     """Smallest N where the measured gain (ms) turns positive and stays so,
     interpolated in log N between the two grid points around the sign change;
@@ -776,6 +849,9 @@ def run_ours(args):
         torch.cuda.empty_cache()
         line["batched"] = batched_leg(args, ctx, torch)
         line["gpu_launches"] += line["batched"]["gpu_launches_graph"] * args.batch_reps
+    if "fullrow" in workloads:
+        torch.cuda.empty_cache()
+        line["fullrow"] = fullrow_leg(args, ctx, torch)
     if "gate" in workloads:
         torch.cuda.empty_cache()
         line["gate"] = gate_leg(args, ctx, torch)
@@ -809,7 +885,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,join,batched,gate,serving",
+    ap.add_argument("--workload", default="topk,join,batched,fullrow,gate,serving",
                     help="comma list: topk (the headline value), join (probe sub-object), batched (executor), "
                          "serving (gated vs always-on stream)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",
@@ -819,6 +895,8 @@ def main():
     ap.add_argument("--join-steps", type=int, default=50)
     ap.add_argument("--join-traffic", type=float, default=None)
     ap.add_argument("--gate-points", type=int, default=16, help="N grid points of the gate leg (1e3..1e8)")
+    ap.add_argument("--fullrow-payload", type=int, default=100, help="payload bytes per row of the full-row leg")
+    ap.add_argument("--fullrow-reps", type=int, default=11)
     ap.add_argument("--gate-reps", type=int, default=5)
     ap.add_argument("--join-partitions", type=int, default=0,
                     help="0 automatic, 1 direct probe, 2..256 forced partition count")

@@ -243,6 +243,26 @@ typedef struct {
 olap_status olap_autotune(olap_ctx* ctx, const olap_tune_request* req, olap_tune_result* out);
 
 /* ------------------------------------------------------------------------
+ * Full-row offload, the foil of key-only transfer with late materialization
+ * (Sec. II-C: only (key, row-id) cross the link and the host re-reads the
+ * other columns for the few returned row-ids; Sec. V-E measures both).  Here
+ * the whole rows cross the link: the key field is extracted on the device,
+ * the Top-K is selected as in olap_topk, and the K selected rows are gathered
+ * on the device and returned whole.
+ *
+ * rows        n fixed-width rows of row_bytes bytes in memory `in_where`; the
+ *             key of row i (type `type`) is at byte key_offset of it.
+ * out_rows    min(k, n) rows of row_bytes, in order, in memory `out_where`.
+ * out_rowids  min(k, n) row indices, or NULL.
+ * Errors: E_INVALID for a key field outside the row (key_offset + key width >
+ * row_bytes), bad kinds, n >= 2^32 or NULL buffers; E_NOMEM; E_CUDA;
+ * E_TIMEOUT as olap_topk.  Blocking.
+ * ------------------------------------------------------------------------ */
+olap_status olap_topk_rows(olap_ctx* ctx, const void* rows, olap_mem in_where, uint64_t n, uint32_t row_bytes,
+                           uint32_t key_offset, olap_key_type type, uint64_t k, olap_order order, void* out_rows,
+                           uint32_t* out_rowids, olap_mem out_where, uint64_t* out_count);
+
+/* ------------------------------------------------------------------------
  * Key-based hash join, build and probe (Sec. III-B: "parallel probing using a
  * key-only hash table", pointers returned for late materialization, Sec. II-C).
  *

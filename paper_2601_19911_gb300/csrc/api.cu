@@ -73,6 +73,10 @@ olap_status ensure_dev_out(olap_ctx* ctx, size_t bytes) {
     return grow(ctx, &ctx->dev_out, &ctx->dev_out_bytes, bytes, "output staging allocation");
 }
 
+static olap_status grow_rows_buf(olap_ctx* ctx, size_t bytes) {
+    return grow(ctx, &ctx->rows_buf, &ctx->rows_buf_bytes, bytes, "full-row scratch allocation");
+}
+
 olap_status ensure_part(olap_ctx* ctx, size_t bytes) {
     return grow(ctx, &ctx->part, &ctx->part_bytes, bytes, "probe partition allocation");
 }
@@ -347,6 +351,7 @@ void olap_ctx_destroy(olap_ctx* ctx) {
     if (ctx->dev_in) cudaFree(ctx->dev_in);
     if (ctx->dev_out) cudaFree(ctx->dev_out);
     if (ctx->part) cudaFree(ctx->part);
+    if (ctx->rows_buf) cudaFree(ctx->rows_buf);
     for (int i = 0; i < 2; ++i) {
         if (ctx->pinned[i]) cudaFreeHost(ctx->pinned[i]);
         if (ctx->pinned_ev[i]) cudaEventDestroy(ctx->pinned_ev[i]);
@@ -370,6 +375,65 @@ olap_status olap_ctx_sync(olap_ctx* ctx) {
     if (!ctx) return OLAP_E_INVALID;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "stream synchronize");
+}
+
+olap_status olap_topk_rows(olap_ctx* ctx, const void* rows, olap_mem in_where, uint64_t n, uint32_t row_bytes,
+                           uint32_t key_offset, olap_key_type type, uint64_t k, olap_order order, void* out_rows,
+                           uint32_t* out_rowids, olap_mem out_where, uint64_t* out_count) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (!out_count) return fail(ctx, OLAP_E_INVALID, "out_count is NULL");
+    *out_count = 0;
+    if (in_where < OLAP_MEM_HOST || in_where > OLAP_MEM_DEVICE || out_where < OLAP_MEM_HOST ||
+        out_where > OLAP_MEM_DEVICE)
+        return fail(ctx, OLAP_E_INVALID, "bad memory kind");
+    if (type < OLAP_KEY_I64 || type > OLAP_KEY_U32) return fail(ctx, OLAP_E_INVALID, "bad key type");
+    if (order != OLAP_ASC && order != OLAP_DESC) return fail(ctx, OLAP_E_INVALID, "bad order");
+    const size_t w = key_bytes(type);
+    if (row_bytes == 0 || static_cast<uint64_t>(key_offset) + w > row_bytes)
+        return fail(ctx, OLAP_E_INVALID, "key field outside the row");
+    if (n >= (1ull << 32)) return fail(ctx, OLAP_E_INVALID, "n must be below 2^32");
+    if (n && !rows) return fail(ctx, OLAP_E_INVALID, "rows is NULL");
+    const uint64_t kk = std::min(k, n);
+    if (kk && !out_rows) return fail(ctx, OLAP_E_INVALID, "out_rows is NULL");
+    if (kk == 0) return OLAP_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
+    const uint64_t tbytes = n * row_bytes;
+    const void* dr = rows;
+    olap_status st;
+    if (in_where != OLAP_MEM_DEVICE) {                      // the whole rows cross the link
+        if ((st = ensure_dev_in(ctx, tbytes)) != OLAP_OK) return st;
+        if ((st = copy_h2d(ctx, ctx->dev_in, rows, tbytes, in_where)) != OLAP_OK) return st;
+        dr = ctx->dev_in;
+    }
+    // scratch: key column | selected keys | selected row-ids | gathered rows
+    auto al = [](size_t x) { return (x + 255) & ~static_cast<size_t>(255); };
+    const size_t o_keys = 0, o_sel = al(n * w), o_rid = o_sel + al(kk * w), o_rows = o_rid + al(kk * 4);
+    if ((st = grow_rows_buf(ctx, o_rows + al(kk * row_bytes))) != OLAP_OK) return st;
+    unsigned char* b = static_cast<unsigned char*>(ctx->rows_buf);
+    const int grid = ctx->sm_count * 4;
+    if ((e = rows_extract(dr, n, row_bytes, key_offset, static_cast<int>(w), b + o_keys, grid, ctx->stream)) !=
+        cudaSuccess)
+        return cuda_fail(ctx, e, "key extraction");
+    TopkCtl* ctl = nullptr;
+    uint32_t* drid = reinterpret_cast<uint32_t*>(b + o_rid);
+    if ((st = topk_enqueue(ctx, b + o_keys, type, nullptr, n, kk, order, b + o_sel, drid, nullptr, ctx->stream,
+                           &ctl)) != OLAP_OK)
+        return st;
+    if ((e = rows_gather(dr, row_bytes, drid, kk, b + o_rows, grid, ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "row gather");
+    e = cudaMemcpyAsync(ctx->host_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
+    if ((st = copy_d2h(ctx, out_rows, b + o_rows, kk * row_bytes, out_where)) != OLAP_OK) return st;
+    if (out_rowids && (st = copy_d2h(ctx, out_rowids, drid, kk * 4, out_where)) != OLAP_OK) return st;
+    if ((e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "full-row Top-K");
+    if (*ctx->host_status != OLAP_OK) {
+        ctx->barrier_dirty = true;
+        return fail(ctx, static_cast<olap_status>(*ctx->host_status), "Top-K device wait expired");
+    }
+    *out_count = kk;
+    return OLAP_OK;
 }
 
 olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const uint32_t* rowids,

@@ -50,6 +50,11 @@ struct olap_ctx {
     cudaEvent_t kev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool topk_timed = false, probe_timed = false, topk_filtered = false;
 
+    // Full-row offload scratch (grow-only): the extracted key column, the
+    // selection's outputs and the gathered rows.
+    void* rows_buf = nullptr;
+    size_t rows_buf_bytes = 0;
+
     // Partitioned-probe scratch (grow-only): partitioned keys, row-ids and
     // the per-CTA partition counts.
     void* part = nullptr;
@@ -91,5 +96,12 @@ olap_status copy_d2h(olap_ctx* ctx, void* dst, const void* src, size_t bytes, ol
 
 // Bytes of device memory the context may still allocate under its budget.
 bool within_budget(const olap_ctx* ctx, size_t extra);
+
+// Row-store helpers (full-row offload): pull the key field out of n rows
+// into a dense column; gather k rows by index.  Enqueue only.
+cudaError_t rows_extract(const void* rows, uint64_t n, uint32_t row_bytes, uint32_t key_offset, int key_width,
+                         void* keys, int grid, cudaStream_t s);
+cudaError_t rows_gather(const void* rows, uint32_t row_bytes, const uint32_t* idx, uint64_t k, void* out, int grid,
+                        cudaStream_t s);
 
 }  // namespace olap

@@ -312,6 +312,21 @@ int olap_host_engine_run(void* eng, olap_serve_request* r) {
     return OLAP_E_INVALID;
 }
 
+// Cut the key column out of a row table (a row store's key-only extraction,
+// Sec. V-C): key i = the key_width bytes at rows + i * row_bytes + key_offset.
+void olap_host_engine_extract(void* eng, const void* rows, uint64_t n, uint32_t row_bytes, uint32_t key_offset,
+                              uint32_t key_width, void* out) {
+    Engine* E = static_cast<Engine*>(eng);
+    const unsigned char* r = static_cast<const unsigned char*>(rows);
+    unsigned char* o = static_cast<unsigned char*>(out);
+    parallel(E, chunks_for(E, n, TOPK_CHUNK), n, [&](int, uint64_t a, uint64_t b) {
+        if (key_width == 8)
+            for (uint64_t i = a; i < b; ++i) std::memcpy(o + i * 8, r + i * row_bytes + key_offset, 8);
+        else
+            for (uint64_t i = a; i < b; ++i) std::memcpy(o + i * key_width, r + i * row_bytes + key_offset, key_width);
+    });
+}
+
 void olap_host_engine_free(void* eng) { delete static_cast<Engine*>(eng); }
 
 }  // extern "C"

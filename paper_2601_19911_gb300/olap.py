@@ -30,7 +30,7 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
     "olap_ctx_host_direct",
-    "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last",
+    "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last", "olap_topk_rows",
     "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_autotune",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
@@ -200,6 +200,9 @@ def load(path: str | None = None):
         lib.olap_topk.argtypes = [vp, vp, i32, vp, i32, u64, u64, i32, vp, vp, i32, ctypes.POINTER(u64)]
         lib.olap_topk_async.restype = i32
         lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
+        lib.olap_topk_rows.restype = i32
+        lib.olap_topk_rows.argtypes = [vp, vp, i32, u64, ctypes.c_uint32, ctypes.c_uint32, i32, u64, i32, vp, vp,
+                                       i32, ctypes.POINTER(u64)]
         lib.olap_topk_info_last.restype = i32
         lib.olap_topk_info_last.argtypes = [vp, ctypes.POINTER(olap_topk_info)]
         lib.olap_autotune.restype = i32
@@ -379,6 +382,25 @@ class Context:
         self.check(st)
         assert got.value == cnt
         return out_keys[:cnt], out_rowids[:cnt]
+
+    def topk_rows(self, rows, row_bytes: int, key_offset: int, key_type: int, k: int, order: int = DESC,
+                  out_rows=None, out_rowids=None):
+        """olap_topk_rows (full-row offload): `rows` holds n rows of row_bytes
+        bytes (numpy, pinned or CUDA tensor); returns (rows, row-ids) of the
+        min(k, n) selected rows, whole."""
+        nbytes = rows.nbytes if isinstance(rows, np.ndarray) else rows.numel() * rows.element_size()
+        assert nbytes % row_bytes == 0
+        n = nbytes // row_bytes
+        cnt = min(int(k), n)
+        if out_rows is None:
+            out_rows = np.empty(max(cnt, 1) * row_bytes, dtype=np.uint8)
+            out_rowids = np.empty(max(cnt, 1), dtype=np.uint32)
+        got = ctypes.c_uint64()
+        self.check(self.lib.olap_topk_rows(self.h, ptr(rows), mem_kind(rows), n, row_bytes, key_offset, key_type,
+                                           int(k), int(order), ptr(out_rows), ptr(out_rowids), mem_kind(out_rows),
+                                           ctypes.byref(got)))
+        assert got.value == cnt
+        return out_rows, (None if out_rowids is None else out_rowids[:cnt])
 
     # -- Join ----------------------------------------------------------------
     def join_build(self, keys, rowids=None, load_factor: float = 0.0) -> "JoinTable":
@@ -606,6 +628,9 @@ class HostEngine:
         self.lib.olap_host_engine_add_table.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                         ctypes.c_uint64]
         self.lib.olap_host_engine_free.argtypes = [ctypes.c_void_p]
+        self.lib.olap_host_engine_extract.restype = None
+        self.lib.olap_host_engine_extract.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                                      ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
         self.h = self.lib.olap_host_engine_create(threads)
         self._keep = []
 
@@ -620,6 +645,15 @@ class HostEngine:
     def run(self, req: olap_serve_request) -> int:
         f = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(olap_serve_request))(self.fn)
         return f(self.h, ctypes.byref(req))
+
+    def extract(self, rows: np.ndarray, row_bytes: int, key_offset: int, dtype) -> np.ndarray:
+        """The key column of a row table (one field per row), cut out on the
+        engine's threads."""
+        n = rows.nbytes // row_bytes
+        out = np.empty(n, dtype=dtype)
+        self.lib.olap_host_engine_extract(self.h, rows.ctypes.data, n, row_bytes, key_offset, out.itemsize,
+                                          out.ctypes.data)
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -48,3 +48,12 @@ def test_probe_matches_oracle(eng, mult, hit):
     assert eng.run(r) == olap.OK and r.out_count == need
     got = np.sort((out[:, 0].astype(np.uint64) << np.uint64(32)) | out[:, 1])
     np.testing.assert_array_equal(got, oracle.join(b.keys, p.keys))
+
+
+@pytest.mark.parametrize("row_bytes,off,dtype", [(108, 0, np.float64), (13, 5, np.uint32), (64, 56, np.int64)])
+def test_extract_key_column(eng, row_bytes, off, dtype):
+    rng = np.random.default_rng(row_bytes)
+    rows = rng.integers(0, 256, (300_001, row_bytes), dtype=np.uint8)
+    got = eng.extract(rows, row_bytes, off, dtype)
+    w = np.dtype(dtype).itemsize
+    np.testing.assert_array_equal(got.view(np.uint8).reshape(-1, w), rows[:, off:off + w])
