@@ -105,6 +105,52 @@ __device__ __forceinline__ int prefix_cmp(uint64_t w0, uint64_t w1, uint64_t p0,
     return a < b ? -1 : (a > b ? 1 : 0);
 }
 
+// Fold (w0, w1) into running AND / OR words.
+__device__ __forceinline__ void and_or(uint64_t w0, uint64_t w1, uint64_t* ao) {
+    ao[0] &= w0;
+    ao[1] &= w1;
+    ao[2] |= w0;
+    ao[3] |= w1;
+}
+
+// Warp-reduce running AND / OR words and merge them into `dst` (lane 0).
+__device__ __forceinline__ void and_or_merge(uint64_t* ao, unsigned long long* dst) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ao[0] &= __shfl_xor_sync(0xFFFFFFFFu, ao[0], o);
+        ao[1] &= __shfl_xor_sync(0xFFFFFFFFu, ao[1], o);
+        ao[2] |= __shfl_xor_sync(0xFFFFFFFFu, ao[2], o);
+        ao[3] |= __shfl_xor_sync(0xFFFFFFFFu, ao[3], o);
+    }
+    if ((threadIdx.x & 31u) == 0) {
+        atomicAnd(dst + 0, static_cast<unsigned long long>(ao[0]));
+        atomicAnd(dst + 1, static_cast<unsigned long long>(ao[1]));
+        atomicOr(dst + 2, static_cast<unsigned long long>(ao[2]));
+        atomicOr(dst + 3, static_cast<unsigned long long>(ao[3]));
+    }
+}
+
+// First bit position (0 = MSB of w0) where the entries behind merged AND / OR
+// words differ; `total` when they agree everywhere.
+__device__ __forceinline__ int first_diff(const unsigned long long* ao, int total) {
+    const uint64_t d0 = __ldcg(ao + 0) ^ __ldcg(ao + 2), d1 = __ldcg(ao + 1) ^ __ldcg(ao + 3);
+    const int f = d0 ? __clzll(static_cast<long long>(d0)) : (d1 ? 64 + __clzll(static_cast<long long>(d1)) : 128);
+    return f < total ? f : total;
+}
+
+// Bits [lo, hi) of a 64-bit word counted from its MSB (0 <= lo <= hi <= 64).
+__device__ __forceinline__ uint64_t bit_range(int lo, int hi) {
+    if (hi <= lo) return 0ull;
+    const uint64_t ones = (hi - lo == 64) ? ~0ull : ((1ull << (hi - lo)) - 1ull);
+    return ones << (64 - hi);
+}
+
+// Copy bits [from, to) of (a0, a1) into (p0, p1), whose bits there are zero.
+__device__ __forceinline__ void prefix_copy(uint64_t& p0, uint64_t& p1, uint64_t a0, uint64_t a1, int from, int to) {
+    if (from < 64) p0 |= a0 & bit_range(from, to < 64 ? to : 64);
+    if (to > 64) p1 |= a1 & bit_range((from > 64 ? from : 64) - 64, to - 64);
+}
+
 // Set bits [L, L + d) of (p0, p1) to `digit`.
 __device__ __forceinline__ void prefix_set(uint64_t& p0, uint64_t& p1, int L, int d, uint32_t digit) {
     const uint64_t v = static_cast<uint64_t>(digit);

@@ -373,13 +373,22 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 
 // One refine pass: histogram of digit [L, L+d) of the composites that match
-// the prefix, merged into `gh`.  `gz` (another buffer) is cleared by CTA 0.
+// the prefix, merged into `gh`, and the AND / OR of those composites merged
+// into `ao`.  `gz` and `az` (the buffers of the pass after next) are reset by
+// CTA 0.
 __device__ void hist_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_t p0, uint64_t p1,
-                          int L, int d, int kb, unsigned* gh, unsigned* gz, unsigned* sh) {
+                          int L, int d, int kb, unsigned* gh, unsigned* gz, unsigned* sh, unsigned long long* ao,
+                          unsigned long long* az) {
     for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB) sh[b] = 0;
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB) gz[b] = 0;
+        if (threadIdx.x == 0) {
+            az[0] = az[1] = ~0ull;
+            az[2] = az[3] = 0ull;
+        }
+    }
     __syncthreads();
+    uint64_t acc[4] = {~0ull, ~0ull, 0ull, 0ull};
     const uint64_t stride = static_cast<uint64_t>(TK_TPB) * gridDim.x;
     const unsigned lane = threadIdx.x & 31u;
     for (uint64_t wb = static_cast<uint64_t>(blockIdx.x) * TK_TPB + (threadIdx.x & ~31u); wb < src_n;
@@ -390,12 +399,16 @@ __device__ void hist_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_t
             const Elem e = load_src(a, cand, i);
             uint64_t w0, w1;
             comp_words(e.r, e.rid, kb, w0, w1);
-            if (prefix_cmp(w0, w1, p0, p1, L) == 0) dig = comp_digit(w0, w1, L, d);
+            if (prefix_cmp(w0, w1, p0, p1, L) == 0) {
+                dig = comp_digit(w0, w1, L, d);
+                and_or(w0, w1, acc);
+            }
         }
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, dig);
         if (dig != 0xFFFFFFFFu && lane == static_cast<unsigned>(__ffs(peers) - 1))
             atomicAdd(&sh[dig], static_cast<unsigned>(__popc(peers)));
     }
+    and_or_merge(acc, ao);
     __syncthreads();
     for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB)
         if (sh[b]) atomicAdd(&gh[b], sh[b]);
@@ -493,6 +506,12 @@ __global__ void __launch_bounds__(TK_TPB) topk_prepare_kernel(TopkArgs a) {
         ctl->path = a.use_sample ? 1 : 0;
         ctl->passes = 0;
         ctl->thresh = ~0ull;
+        for (int s = 0; s < 3; ++s) {
+            ctl->ao[s][0] = ctl->ao[s][1] = ~0ull;
+            ctl->ao[s][2] = ctl->ao[s][3] = 0ull;
+        }
+        ctl->fin[0] = ctl->fin[1] = ~0ull;
+        ctl->fin[2] = ctl->fin[3] = 0ull;
     }
     for (int b = threadIdx.x; b < 3 * TK_BINS; b += TK_TPB) a.ghist[b] = 0;
     if (a.use_sample) {
@@ -559,13 +578,25 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
         const int d = min(a.digit, TB - L);
         unsigned* gh = a.ghist + (pass % 3) * TK_BINS;
         unsigned* gz = a.ghist + ((pass + 1) % 3) * TK_BINS;
-        hist_pass(a, cand, src_n, p0, p1, L, d, kb, gh, gz, sh);
+        unsigned long long* ao = ctl->ao[pass % 3];
+        hist_pass(a, cand, src_n, p0, p1, L, d, kb, gh, gz, sh, ao, ctl->ao[(pass + 1) % 3]);
         if (!grid_sync(a.bar, &ctl->err)) return report(a);
         const Pick pk = pick_bucket<TK_TPB>(gh, krem, sc);
+        const bool whole = pk.below == 0 && pk.in_b == bcnt;     // every matching entry in one bucket
         krem -= pk.below;
         bcnt = pk.in_b;
         prefix_set(p0, p1, L, d, pk.b);
         L += d;
+        if (whole) {
+            // The bucket holds exactly the entries the AND / OR saw: their
+            // common bits join the prefix and the next digit starts where
+            // they first differ.
+            const int f = first_diff(ao, TB);
+            if (f > L) {
+                prefix_copy(p0, p1, __ldcg(ao + 0), __ldcg(ao + 1), L, f);
+                L = f;
+            }
+        }
         ++pass;
     }
     if (stamp) {
@@ -663,10 +694,24 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
             }
             __syncthreads();
         }
-        // (b) partition histogram of the below entries.
-        const int L0 = cand ? (__clzll(static_cast<long long>(__ldcg(&ctl->thresh))) < kb
-                                   ? __clzll(static_cast<long long>(__ldcg(&ctl->thresh))) : kb)
-                            : 0;
+        // (b) partition histogram of the below entries, on the digit that
+        // starts at the first bit where they differ (AND / OR over the grid),
+        // so that clustered keys and ties on the key spread over the buckets.
+        {
+            uint64_t acc[4] = {~0ull, ~0ull, 0ull, 0ull};
+            const uint64_t gs = static_cast<uint64_t>(TK_TPB) * gridDim.x;
+            for (uint64_t wb = static_cast<uint64_t>(blockIdx.x) * TK_TPB + (threadIdx.x & ~31u); wb < nb; wb += gs) {
+                const uint64_t i = wb + lane;
+                if (i < nb) {
+                    uint64_t w0, w1;
+                    comp_words(__ldcg(a.out_r0 + i), __ldcg(a.out_rid0 + i), kb, w0, w1);
+                    and_or(w0, w1, acc);
+                }
+            }
+            and_or_merge(acc, ctl->fin);
+        }
+        if (!grid_sync(a.bar, &ctl->err)) return report(a);
+        const int L0 = min(first_diff(ctl->fin, TB), TB - 1);
         const int dp = min(a.digit, TB - L0);
         unsigned* ph = a.ghist + (pass % 3) * TK_BINS;          // clean (zeroed by the last pass or prepare)
         unsigned* pc = a.ghist + ((pass + 1) % 3) * TK_BINS;    // cursors, zeroed here

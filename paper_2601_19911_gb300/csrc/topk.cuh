@@ -45,6 +45,12 @@ struct TopkCtl {
     int path;                        // 0 direct, 1 sampled candidates, 2 fallback
     int passes;                      // refine passes run
     int pad;
+    // AND and OR of the composite words (w0, w1) of the entries a refine pass
+    // saw (three slots, by pass), and of the selected entries before the
+    // finish partition: {and0, and1, or0, or1}.  Bits where AND == OR are
+    // common to all those entries.
+    unsigned long long ao[3][4];
+    unsigned long long fin[4];
     // %globaltimer stamps: prepare start, prepare end (sample done), select
     // start (filter done), source decided, refine done, split done, end,
     // small-buffer finish done, survivor sort done.
