@@ -574,6 +574,15 @@ def serving_leg(args, ctx, torch):
         p = datagen.join_probe(A, common, hit, "uniform", seed=40 + j)
         arenas.append((hit, p.keys, np.concatenate([[0], np.cumsum(p.hit)])))
 
+    # Long streams write their results into a ring of output buffers shared
+    # by requests i, i + R, ... (their contents are not checked; per-request
+    # buffers for 10^5 requests would take terabytes).
+    ring = args.serve_requests > 5000
+    R = 8
+    ring_topk = [(np.empty(100_000, dtype=np.int64), np.empty(100_000, dtype=np.uint32)) for _ in range(R)] \
+        if ring else None
+    ring_probe = [np.empty((A + 64, 2), dtype=np.uint32) for _ in range(R)] if ring else None
+
     def make_requests(count, seed):
         r_ = np.random.default_rng(seed)
         reqs, keep = [], []
@@ -582,8 +591,11 @@ def serving_leg(args, ctx, torch):
             off = int(r_.integers(0, A - n + 1))
             if i % 2 == 0:
                 k = int(min(n, np.floor(1e5 ** r_.random())))
-                ok = np.empty(max(1, k), dtype=np.int64)
-                orow = np.empty(max(1, k), dtype=np.uint32)
+                if ring:
+                    ok, orow = ring_topk[(i // 2) % R]
+                else:
+                    ok = np.empty(max(1, k), dtype=np.int64)
+                    orow = np.empty(max(1, k), dtype=np.uint32)
                 keys = topk_arena[off:off + n]
                 keep.append((ok, orow))
                 reqs.append(olap.olap_serve_request(olap.OP_TOPK, olap.KEY_I64, olap.DESC, 0, keys.ctypes.data, None,
@@ -592,14 +604,17 @@ def serving_leg(args, ctx, torch):
                 t = int(r_.integers(0, 8))
                 hit, pk, cum = arenas[int(r_.integers(0, 2))]
                 need = int(cum[off + n] - cum[off])
-                out = np.empty((need + 64, 2), dtype=np.uint32)
+                out = ring_probe[(i // 2) % R] if ring else np.empty((need + 64, 2), dtype=np.uint32)
                 keep.append((out,))
                 reqs.append(olap.olap_serve_request(olap.OP_PROBE, olap.KEY_I64, 0, t, pk[off:off + n].ctypes.data,
                                                     None, n, 0, tables[t].h.value, float(need), 0.0, None, None,
                                                     out.ctypes.data, need + 64))
         return (olap.olap_serve_request * count)(*reqs), keep
 
-    # -- gate calibration from measured times (one request at a time) ----------
+    # -- gate calibration from measured times (one request at a time), on a
+    # context with the same host path as the serving slots --------------------
+    hacc = olap.HOST_STAGED if args.serve_host == "staged" else olap.HOST_AUTO
+    sctx = olap.Context(torch.cuda.current_device(), host_access=hacc)
     cal_n = np.unique(np.floor(np.logspace(3, 8, args.serve_cal_points)).astype(np.int64))
     cal_n = cal_n[cal_n <= A]
     samples = {olap.OP_TOPK: [], olap.OP_PROBE: []}
@@ -618,11 +633,11 @@ def serving_leg(args, ctx, torch):
         t_cpu = _median_ms(lambda: host.run(req))
         dok = torch.empty(kcal, dtype=torch.int64, device="cuda")
         dor = torch.empty(kcal, dtype=torch.int32, device="cuda")
-        t_in = _median_ms(lambda: ctx.topk(keys, kcal, olap.DESC, out_keys=dok, out_rowids=dor))
-        t_all = _median_ms(lambda: ctx.topk(keys, kcal, olap.DESC))
+        t_in = _median_ms(lambda: sctx.topk(keys, kcal, olap.DESC, out_keys=dok, out_rowids=dor))
+        t_all = _median_ms(lambda: sctx.topk(keys, kcal, olap.DESC))
         def kern():
-            ctx.topk_async(dev_keys[:n], kcal, olap.DESC, dok, dor)
-            ctx.sync()
+            sctx.topk_async(dev_keys[:n], kcal, olap.DESC, dok, dor)
+            sctx.sync()
         t_ker = _median_ms(kern)
         samples[olap.OP_TOPK].append((n, kcal, 8.0 * n, min(kcal, n), t_cpu, max(t_in - t_ker, 0.0), t_ker,
                                       max(t_all - t_in, 0.0)))
@@ -637,11 +652,11 @@ def serving_leg(args, ctx, torch):
         dpk[:n].copy_(torch.from_numpy(pkeys))
         dout = torch.empty((need + 64, 2), dtype=torch.int32, device="cuda")
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-        t_in = _median_ms(lambda: ctx.join_probe(tables[0], pkeys, out=dout))
-        t_all = _median_ms(lambda: ctx.join_probe(tables[0], pkeys, out=out))
+        t_in = _median_ms(lambda: sctx.join_probe(tables[0], pkeys, out=dout))
+        t_all = _median_ms(lambda: sctx.join_probe(tables[0], pkeys, out=out))
         def pkern():
-            ctx.join_probe_async(tables[0], dpk[:n], dout, need + 64, cnt)
-            ctx.sync()
+            sctx.join_probe_async(tables[0], dpk[:n], dout, need + 64, cnt)
+            sctx.sync()
         t_ker = _median_ms(pkern)
         samples[olap.OP_PROBE].append((n, 1.0 + need / n, 8.0 * n, need, t_cpu, max(t_in - t_ker, 0.0), t_ker,
                                        max(t_all - t_in, 0.0)))
@@ -651,12 +666,15 @@ def serving_leg(args, ctx, torch):
     models = {}
     for op, rows in samples.items():
         cols = list(zip(*rows))
-        models[op] = olap.gate_calibrate(op, *cols, margin_ms=args.serve_margin, weighting=olap.FIT_RELATIVE)
+        models[op] = olap.gate_calibrate(op, *cols, margin_ms=args.serve_margin, weighting=olap.FIT_RELATIVE,
+                                         topk_cpu=olap.CPU_MAX if args.serve_topk_cpu == "max" else 0)
     # -- arrival rate from the closed-loop always-on throughput -----------------
     reqs, keep = make_requests(args.serve_requests, seed=4)
     budget = max(1, args.serve_budget_gb * (1 << 30) - tbytes)
-    closed = olap.serve(reqs, olap.SERVE_ALWAYS_GPU, gpu_slots=args.serve_slots, mem_budget_bytes=budget,
-                        closed_loop=True)
+    # closed-loop throughput on the first (at most 2000) requests of the trace
+    cl_reqs, _cl_keep = make_requests(min(args.serve_requests, 2000), seed=4)
+    closed = olap.serve(cl_reqs, olap.SERVE_ALWAYS_GPU, gpu_slots=args.serve_slots, mem_budget_bytes=budget,
+                        closed_loop=True, host_access=hacc)
     lam = 0.7 * closed.throughput_rps
     arrivals = datagen.poisson_arrivals(args.serve_requests, lam, seed=4) * 1e3
     out = {}
@@ -664,22 +682,27 @@ def serving_leg(args, ctx, torch):
         for i in range(args.serve_requests):
             reqs[i].arrival_ms = float(arrivals[i])
         st = olap.serve(reqs, policy, models[olap.OP_TOPK], models[olap.OP_PROBE], host,
-                        gpu_slots=args.serve_slots, cpu_workers=args.serve_cpu_workers, mem_budget_bytes=budget)
+                        gpu_slots=args.serve_slots, cpu_workers=args.serve_cpu_workers, mem_budget_bytes=budget,
+                        host_access=hacc)
         out[name] = {"p50_ms": st.p50_ms, "p95_ms": st.p95_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms,
                      "max_ms": st.max_ms, "throughput_rps": st.throughput_rps, "wall_ms": st.wall_ms,
                      "offload_fraction": st.offload_fraction, "n_gpu": st.n_gpu, "n_host": st.n_host,
                      "failed": st.n_failed, "peak_reserved_gb": st.peak_reserved_bytes / 2**30}
     def mdict(m):
-        return {"cpu_form": ["n_log2_n", "n_k", "n_m"][m.cpu_form], "a": m.a, "b": m.b, "c_ms_per_byte": m.c,
+        return {"cpu_form": ["n_log2_n", "n_k", "n_m", "max(n_log2_n, n_k)"][m.cpu_form], "a": m.a, "b": m.b,
+                "a2": m.a2, "b2": m.b2, "c_ms_per_byte": m.c,
                 "d": m.d, "e": m.e, "f": m.f, "g": m.g, "h": m.h, "margin_ms": m.margin_ms}
     nstar = olap.gate_estimate(models[olap.OP_TOPK], olap.OP_TOPK, 1 << 20, 100, 8.0 * (1 << 20), 100, 8.0).n_star
     for t in tables:
         t.free()
     host.close()
+    hdirect = sctx.host_direct
+    sctx.close()
     return {"metric": "gated vs always-on P99 latency (ms)", "value": out["gated"]["p99_ms"], "unit": "ms",
             "higher_is_better": False, "requests": args.serve_requests, "arrival_rate_rps": lam,
             "closed_loop_always_on_rps": closed.throughput_rps, "gpu_slots": args.serve_slots,
             "budget_gb": args.serve_budget_gb, "arena_keys": A, "tables": [int(x) for x in sizes],
+            "host_path": "direct device access" if hdirect else "pinned staging",
             "gated": out["gated"], "always_on": out["always_on"],
             "gate": {"topk": mdict(models[olap.OP_TOPK]), "probe": mdict(models[olap.OP_PROBE]),
                      "topk_n_star_k100": int(nstar), "calibration_points": len(cal_n)}}
@@ -912,6 +935,11 @@ def main():
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-margin", type=float, default=0.0)
     ap.add_argument("--serve-cal-points", type=int, default=18)
+    ap.add_argument("--serve-host", default="staged", choices=["auto", "staged"],
+                    help="how the serving contexts copy pageable keys: direct device access where supported, "
+                         "or CPU staging through pinned buffers")
+    ap.add_argument("--serve-topk-cpu", default="max", choices=["best", "max"],
+                    help="Top-K CPU model of the serving gate: the better-fitting form, or both forms' maximum")
     ap.add_argument("--tile", type=int, default=0, help="bulk-copy bytes (0 = library default)")
     ap.add_argument("--stages", type=int, default=0, help="copies in flight per CTA (0 = default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM (0 = default)")

@@ -384,7 +384,11 @@ void olap_batch_free(olap_batch* batch);
  * calls touch no device.  The gate only advises; it runs no CPU path.
  * ------------------------------------------------------------------------ */
 typedef enum { OLAP_OP_TOPK = 0, OLAP_OP_PROBE = 1 } olap_op;
-typedef enum { OLAP_CPU_NLOGN = 0, OLAP_CPU_NK = 1, OLAP_CPU_NM = 2 } olap_cpu_form;
+/* CPU cost forms (Sec. II-B names alpha*N*log N and alpha*N*K).  OLAP_CPU_MAX
+ * keeps both Top-K fits and estimates the larger of the two: a risk-averse
+ * reading for a host engine whose cost follows neither form alone (a heap
+ * selection costs about N for small K and grows with K log K for large K). */
+typedef enum { OLAP_CPU_NLOGN = 0, OLAP_CPU_NK = 1, OLAP_CPU_NM = 2, OLAP_CPU_MAX = 3 } olap_cpu_form;
 typedef enum { OLAP_FIT_ORDINARY = 0, OLAP_FIT_RELATIVE = 1 } olap_fit;
 
 typedef struct {
@@ -399,6 +403,9 @@ typedef struct {
     const double* t_tx_ms;        /* measured transfer time */
     const double* t_ker_ms;       /* measured kernel time */
     const double* t_post_ms;      /* measured result return + materialization time */
+    int topk_cpu;                 /* Top-K: 0 => the form with the smaller residual;
+                                     OLAP_CPU_MAX => both forms, the larger estimate */
+    int pad;
 } olap_gate_samples;
 
 typedef struct {
@@ -410,6 +417,7 @@ typedef struct {
     double g, h;                  /* post-processing: g * rows + h */
     double margin_ms;
     double rss_nlogn, rss_nk;     /* Top-K: residual sums of squares of both CPU forms */
+    double a2, b2;                /* OLAP_CPU_MAX: the N*K form (a, b hold the N*log2 N form) */
 } olap_gate_model;
 
 typedef struct {

@@ -21,7 +21,8 @@ Readings where it is open (kept identical in the library's contract):
     unweighted the largest sizes decide the small-N costs the gate exists
     for);
   * Top-K fits both CPU forms, x = N*log2(N) and x = N*K, and keeps the one
-    with the smaller residual sum of squares (N*log2 N on a tie);
+    with the smaller residual sum of squares (N*log2 N on a tie); or, on
+    request (CPU_MAX), keeps both and estimates the larger of the two;
   * probe CPU cost uses x = N*M, M the expected candidates per probe;
   * kernel time is linear in N (e*N + f), post-processing linear in the
     number of returned rows (g*out + h);
@@ -37,7 +38,7 @@ import math
 import numpy as np
 
 TOPK, PROBE = 0, 1
-CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
+CPU_NLOGN, CPU_NK, CPU_NM, CPU_MAX = 0, 1, 2, 3
 N_STAR_HI = 1 << 34
 
 
@@ -85,15 +86,16 @@ def cpu_x(form, n, k_or_m):
 
 
 class Model:
-    def __init__(self, op, cpu_form, a, b, c, d, e, f, g, h, margin_ms):
+    def __init__(self, op, cpu_form, a, b, c, d, e, f, g, h, margin_ms, a2=0.0, b2=0.0):
         self.op, self.cpu_form = op, cpu_form
+        self.a2, self.b2 = a2, b2
         self.a, self.b, self.c, self.d = a, b, c, d
         self.e, self.f, self.g, self.h = e, f, g, h
         self.margin_ms = margin_ms
 
 
 def calibrate(op, n, k_or_m, tx_bytes, out_rows, t_cpu, t_tx, t_ker, t_post, margin_ms=0.0,
-              weighting=ORDINARY):
+              weighting=ORDINARY, topk_cpu=0):
     """Fit every cost term from measured samples (all times in ms)."""
     wt = weighting
     if op == TOPK:
@@ -101,18 +103,27 @@ def calibrate(op, n, k_or_m, tx_bytes, out_rows, t_cpu, t_tx, t_ker, t_post, mar
         fits = {f: ols(xs[f], t_cpu, wt) for f in xs}
         res = {f: rss(xs[f], t_cpu, *fits[f], wt) for f in xs}
         form = CPU_NLOGN if res[CPU_NLOGN] <= res[CPU_NK] else CPU_NK
+        if topk_cpu == CPU_MAX:
+            form = CPU_MAX
     else:
         form = CPU_NM
         fits = {form: ols([cpu_x(form, ni, mi) for ni, mi in zip(n, k_or_m)], t_cpu, wt)}
-    a, b = fits[form]
+    a2 = b2 = 0.0
+    if form == CPU_MAX:
+        (a, b), (a2, b2) = fits[CPU_NLOGN], fits[CPU_NK]
+    else:
+        a, b = fits[form]
     c, d = ols(tx_bytes, t_tx, wt)
     e, f = ols(n, t_ker, wt)
     g, h = ols(out_rows, t_post, wt)
-    return Model(op, form, a, b, c, d, e, f, g, h, margin_ms)
+    return Model(op, form, a, b, c, d, e, f, g, h, margin_ms, a2, b2)
 
 
 def costs(m: Model, n, k_or_m, tx_bytes, out_rows):
-    c_cpu = m.a * cpu_x(m.cpu_form, n, k_or_m) + m.b
+    if m.cpu_form == CPU_MAX:
+        c_cpu = max(m.a * cpu_x(CPU_NLOGN, n, k_or_m) + m.b, m.a2 * cpu_x(CPU_NK, n, k_or_m) + m.b2)
+    else:
+        c_cpu = m.a * cpu_x(m.cpu_form, n, k_or_m) + m.b
     c_tx = m.c * float(tx_bytes) + m.d
     c_ker = m.e * float(n) + m.f
     c_post = m.g * float(out_rows) + m.h

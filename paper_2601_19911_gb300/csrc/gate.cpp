@@ -1,5 +1,6 @@
 // Risky Gate (Sec. II-B) with measured constants fitted by least squares and
 // the break-even N* (Sec. V-D).  Pure host arithmetic in fp64.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -71,7 +72,10 @@ struct Costs {
 
 Costs costs(const olap_gate_model& m, double n, double k_or_m, double tx_bytes, double out_rows) {
     Costs c;
-    c.cpu = m.a * cpu_x(m.cpu_form, n, k_or_m) + m.b;
+    if (m.cpu_form == OLAP_CPU_MAX)
+        c.cpu = std::max(m.a * cpu_x(OLAP_CPU_NLOGN, n, k_or_m) + m.b, m.a2 * cpu_x(OLAP_CPU_NK, n, k_or_m) + m.b2);
+    else
+        c.cpu = m.a * cpu_x(m.cpu_form, n, k_or_m) + m.b;
     c.tx = m.c * tx_bytes + m.d;
     c.ker = m.e * n + m.f;
     c.post = m.g * out_rows + m.h;
@@ -110,6 +114,7 @@ olap_status olap_gate_calibrate(const olap_gate_samples* s, double margin_ms, ol
         return OLAP_E_INVALID;
     if (s->op != OLAP_OP_TOPK && s->op != OLAP_OP_PROBE) return OLAP_E_INVALID;
     if (s->weighting != OLAP_FIT_ORDINARY && s->weighting != OLAP_FIT_RELATIVE) return OLAP_E_INVALID;
+    if (s->topk_cpu != 0 && s->topk_cpu != OLAP_CPU_MAX) return OLAP_E_INVALID;
     const uint64_t n = s->count;
     olap_gate_model m;
     std::memset(&m, 0, sizeof(m));
@@ -124,7 +129,13 @@ olap_status olap_gate_calibrate(const olap_gate_samples* s, double margin_ms, ol
         for (uint64_t i = 0; i < n; ++i) x[i] = cpu_x(OLAP_CPU_NK, s->n[i], s->k_or_m[i]);
         ols(x, s->t_cpu_ms, n, s->weighting, &a2, &b2);
         m.rss_nk = rss(x, s->t_cpu_ms, n, s->weighting, a2, b2);
-        if (m.rss_nlogn <= m.rss_nk) {
+        if (s->topk_cpu == OLAP_CPU_MAX) {
+            m.cpu_form = OLAP_CPU_MAX;
+            m.a = a1;
+            m.b = b1;
+            m.a2 = a2;
+            m.b2 = b2;
+        } else if (m.rss_nlogn <= m.rss_nk) {
             m.cpu_form = OLAP_CPU_NLOGN;
             m.a = a1;
             m.b = b1;

@@ -39,7 +39,7 @@ EXPORTS = [
 ]
 SERVE_GATED, SERVE_ALWAYS_GPU, SERVE_ALWAYS_HOST = 0, 1, 2
 OP_TOPK, OP_PROBE = 0, 1
-CPU_NLOGN, CPU_NK, CPU_NM = 0, 1, 2
+CPU_NLOGN, CPU_NK, CPU_NM, CPU_MAX = 0, 1, 2, 3
 FIT_ORDINARY, FIT_RELATIVE = 0, 1
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
 LOADS_AUTO, LOADS_L1, LOADS_L2_ONLY = 0, 1, 2
@@ -82,13 +82,13 @@ class olap_gate_samples(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("weighting", ctypes.c_int), ("count", ctypes.c_uint64), ("n", _dp),
                 ("k_or_m", _dp),
                 ("tx_bytes", _dp), ("out_rows", _dp), ("t_cpu_ms", _dp), ("t_tx_ms", _dp),
-                ("t_ker_ms", _dp), ("t_post_ms", _dp)]
+                ("t_ker_ms", _dp), ("t_post_ms", _dp), ("topk_cpu", ctypes.c_int), ("pad", ctypes.c_int)]
 
 
 class olap_gate_model(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("cpu_form", ctypes.c_int)] + \
         [(nm, ctypes.c_double) for nm in ("a", "b", "c", "d", "e", "f", "g", "h", "margin_ms", "rss_nlogn",
-                                          "rss_nk")]
+                                          "rss_nk", "a2", "b2")]
 
 
 class olap_gate_query(ctypes.Structure):
@@ -581,7 +581,7 @@ def topk_noalloc(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=
 # ---------------------------------------------------------------------------
 
 def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_ker_ms, t_post_ms,
-                   margin_ms: float = 0.0, weighting: int = FIT_ORDINARY) -> olap_gate_model:
+                   margin_ms: float = 0.0, weighting: int = FIT_ORDINARY, topk_cpu: int = 0) -> olap_gate_model:
     """olap_gate_calibrate over equal-length sample sequences (times in ms)."""
     lib = load()
     cols = [np.ascontiguousarray(np.asarray(c, dtype=np.float64)) for c in
@@ -589,7 +589,7 @@ def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_
     cnt = cols[0].shape[0]
     assert all(c.shape[0] == cnt for c in cols)
     ptrs = [c.ctypes.data_as(_dp) for c in cols]
-    smp = olap_gate_samples(op, weighting, cnt, *ptrs)
+    smp = olap_gate_samples(op, weighting, cnt, *ptrs, topk_cpu, 0)
     m = olap_gate_model()
     st = lib.olap_gate_calibrate(ctypes.byref(smp), float(margin_ms), ctypes.byref(m))
     if st != OK:
@@ -669,11 +669,12 @@ class HostEngine:
 
 def serve(requests, policy: int, topk_model=None, probe_model=None, host: HostEngine | None = None,
           gpu_slots: int = 4, cpu_workers: int = 8, mem_budget_bytes: int = 0, closed_loop: bool = False,
-          device: int = 0) -> olap_serve_stats:
-    """olap_serve over a ctypes array (or list) of olap_serve_request."""
+          device: int = 0, host_access: int = HOST_AUTO) -> olap_serve_stats:
+    """olap_serve over a ctypes array (or list) of olap_serve_request; the
+    slot contexts are created with the given host_access."""
     lib = load()
     arr = requests if isinstance(requests, ctypes.Array) else (olap_serve_request * len(requests))(*requests)
-    co = olap_opts(device, None, 0, 0.0, 0, 0.0, 0, 0, 0, 0, 0)
+    co = olap_opts(device=device, host_access=host_access)
     o = olap_serve_opts(policy, gpu_slots, cpu_workers, mem_budget_bytes,
                         ctypes.addressof(topk_model) if topk_model is not None else None,
                         ctypes.addressof(probe_model) if probe_model is not None else None,

@@ -40,18 +40,19 @@ def _noisy_samples(rng, op, form, count=24):
     return n, km, tx, out, t_cpu, t_tx, t_ker, t_post
 
 
-@pytest.mark.parametrize("op,form", [(gate.TOPK, gate.CPU_NLOGN), (gate.TOPK, gate.CPU_NK),
-                                     (gate.PROBE, gate.CPU_NM)])
+@pytest.mark.parametrize("op,form,topk_cpu", [(gate.TOPK, gate.CPU_NLOGN, 0), (gate.TOPK, gate.CPU_NK, 0),
+                                              (gate.PROBE, gate.CPU_NM, 0), (gate.TOPK, gate.CPU_NLOGN, gate.CPU_MAX),
+                                              (gate.TOPK, gate.CPU_NK, gate.CPU_MAX)])
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("weighting", [gate.ORDINARY, gate.RELATIVE])
-def test_calibrate_and_decide_match_oracle(op, form, seed, weighting):
+def test_calibrate_and_decide_match_oracle(op, form, topk_cpu, seed, weighting):
     rng = np.random.default_rng(seed)
     smp = _noisy_samples(rng, op, form)
     for margin in (0.0, 5.0, 10.0):
-        want = gate.calibrate(op, *smp, margin_ms=margin, weighting=weighting)
-        got = olap.gate_calibrate(op, *smp, margin_ms=margin, weighting=weighting)
+        want = gate.calibrate(op, *smp, margin_ms=margin, weighting=weighting, topk_cpu=topk_cpu)
+        got = olap.gate_calibrate(op, *smp, margin_ms=margin, weighting=weighting, topk_cpu=topk_cpu)
         assert got.cpu_form == want.cpu_form
-        for nm in "abcdefgh":
+        for nm in ("a", "b", "c", "d", "e", "f", "g", "h", "a2", "b2"):
             assert math.isclose(getattr(got, nm), getattr(want, nm), rel_tol=1e-9, abs_tol=1e-15), nm
         qn = np.floor(np.exp(rng.uniform(np.log(1e2), np.log(1e9), 50))).astype(np.int64)
         for nq in qn:
@@ -71,7 +72,8 @@ def test_exact_knife_edge_is_not_offloaded():
     # dyadic constants: C_cpu - C_gpu equals the margin exactly (the paper's
     # "exceeds" is strict).  n=8, M=2: C_cpu = 0.5*16 + 1 = 9; C_tx = 0.25*8 +
     # 0.5 = 2.5; C_ker = 0.125*8 = 1; C_post = 0 -> gain 5.5.
-    model = olap.olap_gate_model(gate.PROBE, gate.CPU_NM, 0.5, 1.0, 0.25, 0.5, 0.125, 0.0, 0.0, 0.0, 5.5, 0.0, 0.0)
+    model = olap.olap_gate_model(gate.PROBE, gate.CPU_NM, 0.5, 1.0, 0.25, 0.5, 0.125, 0.0, 0.0, 0.0, 5.5, 0.0, 0.0,
+                                 0.0, 0.0)
     d = olap.gate_estimate(model, gate.PROBE, 8, 2.0, 8.0, 0.0)
     assert d.gain_ms == 5.5 and d.offload == 0
     model.margin_ms = 5.25

@@ -105,3 +105,23 @@ def test_relative_weighting_recovers_exact_data_and_favours_small_points():
     # weights 1/y^2 by hand on two points reduce to the line through them
     s2, i2 = gate.ols([1.0, 3.0], [2.0, 4.0], gate.RELATIVE)
     assert math.isclose(s2, 1.0) and math.isclose(i2, 1.0)
+
+
+def test_max_form_keeps_both_fits_and_takes_the_larger():
+    """CPU_MAX: each form's coefficients are that form's own least-squares
+    fit (checked against numpy.polyfit, a different routine), and the CPU
+    estimate is the larger of the two, at every (N, K)."""
+    rng = np.random.default_rng(11)
+    n = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(1e8), 30)))
+    k = np.minimum(np.floor(np.exp(rng.uniform(0, np.log(1e5), 30))), n)
+    t_cpu = (3e-9 * n * np.log2(n) + 1e-9 * n * k + 0.02) * (1.0 + rng.normal(0, 0.02, 30))
+    z = np.zeros(30)
+    m = gate.calibrate(gate.TOPK, n, k, 8 * n, k, t_cpu, z + 0.1, z + 0.1, z + 0.1, topk_cpu=gate.CPU_MAX)
+    assert m.cpu_form == gate.CPU_MAX
+    a1, b1 = np.polyfit(n * np.log2(n), t_cpu, 1)
+    a2, b2 = np.polyfit(n * k, t_cpu, 1)
+    for got, want in ((m.a, a1), (m.b, b1), (m.a2, a2), (m.b2, b2)):
+        assert math.isclose(got, want, rel_tol=1e-7, abs_tol=1e-12)
+    for ni, ki in ((1e3, 1.0), (1e6, 1e5), (1e8, 10.0), (5e4, 5e4)):
+        c_cpu = gate.costs(m, ni, ki, 8 * ni, ki)[0]
+        assert math.isclose(c_cpu, max(m.a * ni * math.log2(ni) + m.b, m.a2 * ni * ki + m.b2), rel_tol=1e-14)
