@@ -134,6 +134,14 @@ olap_status olap_ctx_sync(olap_ctx* ctx);
  * directly (OLAP_HOST_AUTO on a device with host-page-table access), else 0;
  * 0 for NULL. */
 int olap_ctx_host_direct(const olap_ctx* ctx);
+/* Self-test of the bounded device-side waits (every spin in the library
+ * gives up after a limit and reports OLAP_E_TIMEOUT instead of hanging): one
+ * thread runs the grid barriers' wait on a device word that nothing writes,
+ * for at most limit_cycles (1 .. 2^31) SM clock cycles, then returns.
+ * *out_status receives the device status the wait recorded -- OLAP_E_TIMEOUT
+ * when the bound works.  Returns OLAP_E_INVALID for a bad limit, else OLAP_OK
+ * (or E_CUDA).  The context stays usable. */
+olap_status olap_selftest_wait(olap_ctx* ctx, uint64_t limit_cycles, int32_t* out_status);
 
 /* ------------------------------------------------------------------------
  * Top-K selection, ORDER BY key {ASC|DESC} LIMIT k (Sec. III-A; Sec. V-B

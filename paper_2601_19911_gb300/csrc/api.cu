@@ -134,6 +134,12 @@ static olap_status direct_copy(olap_ctx* ctx, void* dst, const void* src, size_t
     return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, what);
 }
 
+// Self-test of the bounded device waits: one thread waits, with the wait
+// the grid barriers use, on a word that nothing writes.
+__global__ void wait_selftest_kernel(const unsigned* word, int* err, long long limit) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) wait_changed(word, 0u, err, limit);
+}
+
 olap_status copy_h2d(olap_ctx* ctx, void* dst, const void* src, size_t bytes, olap_mem where) {
     if (bytes == 0) return OLAP_OK;
     cudaError_t e;
@@ -370,6 +376,26 @@ const char* olap_last_error(const olap_ctx* ctx) { return ctx ? ctx->last_error.
 void* olap_ctx_stream(const olap_ctx* ctx) { return ctx ? static_cast<void*>(ctx->stream) : nullptr; }
 
 int olap_ctx_host_direct(const olap_ctx* ctx) { return ctx && ctx->host_direct ? 1 : 0; }
+
+olap_status olap_selftest_wait(olap_ctx* ctx, uint64_t limit_cycles, int32_t* out_status) {
+    if (!ctx || !out_status) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (limit_cycles == 0 || limit_cycles > (1ull << 31)) return fail(ctx, OLAP_E_INVALID, "limit out of range");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
+    // aux: [word nobody writes][status], in the context's small device area
+    unsigned* word = static_cast<unsigned*>(ctx->aux) + 512;
+    int* err = reinterpret_cast<int*>(static_cast<unsigned*>(ctx->aux) + 520);
+    if ((e = cudaMemsetAsync(word, 0, 64, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "self-test reset");
+    wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(word, err, static_cast<long long>(limit_cycles));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "self-test launch");
+    if ((e = cudaMemcpyAsync(ctx->host_status, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "self-test wait");
+    *out_status = *ctx->host_status;
+    return OLAP_OK;
+}
 
 olap_status olap_ctx_sync(olap_ctx* ctx) {
     if (!ctx) return OLAP_E_INVALID;

@@ -190,6 +190,20 @@ struct GridBar {
     unsigned gen;
 };
 
+// Wait until *word differs from `old`, at most `limit` clock cycles; on
+// expiry record OLAP_E_TIMEOUT in *err (first error wins) and return false.
+__device__ __forceinline__ bool wait_changed(const unsigned* word, unsigned old, int* err, long long limit) {
+    const long long t0 = clock64();
+    while (ld_acquire_u32(word) == old) {
+        if (clock64() - t0 > limit) {
+            atomicCAS(err, 0, static_cast<int>(OLAP_E_TIMEOUT));
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
 __device__ __forceinline__ bool grid_sync(GridBar* bar, int* err) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -201,14 +215,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, int* err) {
             __threadfence();
             st_release_u32(&bar->gen, g + 1);
         } else {
-            const long long t0 = clock64();
-            while (ld_acquire_u32(&bar->gen) == g) {
-                if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
-                    atomicCAS(err, 0, static_cast<int>(OLAP_E_TIMEOUT));
-                    break;
-                }
-                __nanosleep(64);
-            }
+            wait_changed(&bar->gen, g, err, WAIT_LIMIT_CYCLES);
         }
         __threadfence();
     }

@@ -29,7 +29,7 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 # Every symbol include/olap.h declares, checked by the ABI tests.
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
-    "olap_ctx_host_direct",
+    "olap_ctx_host_direct", "olap_selftest_wait",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last", "olap_topk_rows",
     "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_autotune",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
@@ -196,6 +196,8 @@ def load(path: str | None = None):
         lib.olap_ctx_sync.argtypes = [vp]
         lib.olap_ctx_host_direct.restype = i32
         lib.olap_ctx_host_direct.argtypes = [vp]
+        lib.olap_selftest_wait.restype = i32
+        lib.olap_selftest_wait.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int32)]
         lib.olap_topk.restype = i32
         lib.olap_topk.argtypes = [vp, vp, i32, vp, i32, u64, u64, i32, vp, vp, i32, ctypes.POINTER(u64)]
         lib.olap_topk_async.restype = i32
@@ -468,6 +470,13 @@ class Context:
         res = olap_tune_result()
         self.check(self.lib.olap_autotune(self.h, ctypes.byref(req), ctypes.byref(res)))
         return {nm: getattr(res, nm) for nm, _ in olap_tune_result._fields_ if nm != "pad"}
+
+    def selftest_wait(self, limit_cycles: int) -> int:
+        """olap_selftest_wait: the device status a bounded wait on a word that
+        nothing writes records (OLAP_E_TIMEOUT expected)."""
+        st = ctypes.c_int32(-1)
+        self.check(self.lib.olap_selftest_wait(self.h, int(limit_cycles), ctypes.byref(st)))
+        return st.value
 
     @property
     def host_direct(self) -> bool:

@@ -60,3 +60,23 @@ def test_empty_and_tiny(hctx):
         gk, gr = hctx.topk(keys, 10, olap.ASC)
         wk, wr = oracle.topk(keys, 10, olap.ASC)
         np.testing.assert_array_equal(gr, wr)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """Every device-side spin in the library is bounded: the self-test runs the
+    grid barriers' wait on a word that nothing writes, with a short limit
+    (about 1 ms of SM clock), and the wait must expire with OLAP_E_TIMEOUT.
+    The context keeps working afterwards."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0)
+    try:
+        assert c.selftest_wait(2_000_000) == olap.E_TIMEOUT
+        assert c.selftest_wait(50_000) == olap.E_TIMEOUT
+        keys = datagen.topk_keys(100_000, "uniform", "i64", seed=99)
+        gk, gr = c.topk(keys, 10, olap.DESC)
+        np.testing.assert_array_equal(gr, oracle.topk(keys, 10, olap.DESC)[1])
+        with pytest.raises(olap.OlapError):
+            c.selftest_wait(0)
+    finally:
+        c.close()
