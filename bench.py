@@ -124,26 +124,18 @@ class ClockSampler:
 
 
 def _dist():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2601_19911_gb300 import replicas
+    return replicas.env()
 
 
 def _max_over_ranks(x: float, world: int) -> float:
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2601_19911_gb300 import replicas
+    return replicas.max_over_ranks(x, world, device="cuda")
 
 
 def _barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2601_19911_gb300 import replicas
+    replicas.barrier(world)
 
 
 def cpu_baseline(n_full: int, k: int, seconds: float = 12.0):
@@ -803,7 +795,8 @@ def run_ours(args):
     phases = ctx.topk_info()
     total_ms = _max_over_ranks(total_ms, world)
     ms = total_ms / args.steps
-    value = world * n / (ms * 1e-3) / 1e9
+    from paper_2601_19911_gb300 import replicas
+    value = replicas.whole_job_rate(n, world, ms * 1e-3) / 1e9
 
     # -- end to end through the public blocking call, pinned host keys -----------
     hk = torch.from_numpy(keys).pin_memory()
@@ -818,7 +811,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         ctx.topk(hk, k, olap.DESC, rowids=hr, out_keys=hok, out_rowids=horow)
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
-    e2e_value = world * n / e2e_s / 1e9
+    e2e_value = replicas.whole_job_rate(n, world, e2e_s) / 1e9
 
     # -- per-kernel device time (events around each kernel), same workload ----
     kms = _kernel_pass(ctx, args.steps, lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr))
@@ -892,7 +885,7 @@ def run_ours(args):
     return 0
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -945,7 +938,11 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="resident CTAs per SM (0 = default)")
     ap.add_argument("--filter", default="regs", choices=["bulk", "regs"],
                     help="Top-K streaming pass: register loads (default) or bulk-copy ring")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
