@@ -278,7 +278,8 @@ def batched_leg(args, ctx, torch):
     # autotuned digit width, filter block size and load factor, on a context
     # of its own: a 2^20-key Top-K (the large queries dominate the batch) and
     # the batch's table shape
-    ctx = olap.Context(torch.cuda.current_device())
+    ctx = olap.Context(torch.cuda.current_device(), batch_overlap=args.batch_overlap,
+                       batch_topk_ctas_per_sm=args.batch_topk_ctas)
     tune = ctx.autotune(topk_n=1 << 20, topk_k=500, join_build_n=1 << 22, join_probe_n=1 << 20,
                         join_hit_rate=0.5, reps=5)
     ns, ks = datagen.batched_topk_queries(args.batch_topk, 1e3, 4e6, 1000, seed=3)
@@ -912,6 +913,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--join-traffic", type=float, default=None)
     ap.add_argument("--gate-points", type=int, default=16, help="N grid points of the gate leg (1e3..1e8)")
     ap.add_argument("--fullrow-payload", type=int, default=100, help="payload bytes per row of the full-row leg")
+    ap.add_argument("--batch-overlap", type=int, default=0, help="0: Top-K then probe kernel; 1: side by side")
+    ap.add_argument("--batch-topk-ctas", type=int, default=0, help="batched Top-K CTAs per SM (0 = 2)")
     ap.add_argument("--fullrow-reps", type=int, default=11)
     ap.add_argument("--gate-reps", type=int, default=5)
     ap.add_argument("--join-partitions", type=int, default=0,

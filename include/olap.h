@@ -96,6 +96,10 @@ typedef struct {
     int topk_digit_bits;        /* radix digit width of the Top-K selects (8..12; 0 => 12), also
                                    for batches created on this context */
     int host_access;            /* olap_host_access: how pageable host memory is copied */
+    int batch_overlap;          /* batches: 0 => the Top-K and probe kernels run one after the
+                                   other, 1 => side by side (two branches of the graph); each
+                                   already fills the GPU, and side by side measured no faster */
+    int batch_topk_ctas_per_sm; /* batches: resident Top-K CTAs per SM (1 or 2; 0 => 2) */
 } olap_opts;
 
 /* How pageable host inputs and outputs (OLAP_MEM_HOST) cross the host link. */

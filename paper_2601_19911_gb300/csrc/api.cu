@@ -292,6 +292,8 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
         ctx->opts.join_bucket_loads < OLAP_LOADS_AUTO || ctx->opts.join_bucket_loads > OLAP_LOADS_L2_ONLY ||
         (ctx->opts.topk_digit_bits != 0 && (ctx->opts.topk_digit_bits < 8 || ctx->opts.topk_digit_bits > 12)) ||
         ctx->opts.host_access < OLAP_HOST_AUTO || ctx->opts.host_access > OLAP_HOST_STAGED ||
+        ctx->opts.batch_overlap < 0 || ctx->opts.batch_overlap > 1 || ctx->opts.batch_topk_ctas_per_sm < 0 ||
+        ctx->opts.batch_topk_ctas_per_sm > 2 ||
         (ctx->opts.block_threads != 0 && ctx->opts.block_threads != 256 && ctx->opts.block_threads != 512 &&
          ctx->opts.block_threads != 1024) ||
         (ctx->opts.l2_fetch_bytes != 0 && ctx->opts.l2_fetch_bytes != 32 && ctx->opts.l2_fetch_bytes != 64 &&

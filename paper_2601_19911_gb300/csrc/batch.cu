@@ -484,6 +484,11 @@ struct olap_batch {
     uint64_t* cand_r = nullptr;
     uint32_t* cand_rid = nullptr;
     int grid_topk = 0, grid_probe = 0;
+    // Overlap: the probe branch runs on a second stream forked from the
+    // launch stream inside the graph (the two kernels are independent).
+    bool overlap = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int digit = 12;                       // radix digit width of the per-CTA Top-K
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -495,25 +500,39 @@ olap_status enqueue_batch(olap_batch* b, cudaStream_t s) {
     // queue heads and the error count live in one 256-byte block
     cudaError_t e = cudaMemsetAsync(b->d_next, 0, 256, s);
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "batch reset");
+    cudaStream_t ps = s;                      // stream of the probe branch
+    if (b->overlap) {
+        if ((e = cudaEventRecord(b->ev_fork, s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(b->side, b->ev_fork, 0)) != cudaSuccess)
+            return cuda_fail(b->ctx, e, "batch fork");
+        ps = b->side;
+    }
+    if (b->n_probe) {
+        const Item* probe_items = b->d_items + b->n_topk;
+        batch_probe_reset_kernel<<<static_cast<unsigned>((b->n_probe + 255) / 256), 256, 0, ps>>>(
+            probe_items, b->n_probe, b->d_errors);
+        if (b->n_chunks)
+            batch_probe_kernel<<<b->grid_probe, JP_TPB, JP_SMEM, ps>>>(probe_items, b->d_chunks, b->n_chunks,
+                                                                       b->d_next + 1);
+    }
     if (b->n_topk)
         batch_topk_kernel<<<b->grid_topk, BT_TPB, BT_SMEM, s>>>(b->d_items, b->n_topk, b->d_next, b->cand_r,
                                                                 b->cand_rid, b->d_errors, b->digit);
-    if (b->n_probe) {
-        const Item* probe_items = b->d_items + b->n_topk;
-        batch_probe_reset_kernel<<<static_cast<unsigned>((b->n_probe + 255) / 256), 256, 0, s>>>(
-            probe_items, b->n_probe, b->d_errors);
-        if (b->n_chunks)
-            batch_probe_kernel<<<b->grid_probe, JP_TPB, JP_SMEM, s>>>(probe_items, b->d_chunks, b->n_chunks,
-                                                                      b->d_next + 1);
-    }
-    e = cudaGetLastError();
-    return e == cudaSuccess ? OLAP_OK : cuda_fail(b->ctx, e, "batch launch");
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(b->ctx, e, "batch launch");
+    if (b->overlap &&
+        ((e = cudaEventRecord(b->ev_join, b->side)) != cudaSuccess || (e = cudaStreamWaitEvent(s, b->ev_join, 0)) !=
+                                                                         cudaSuccess))
+        return cuda_fail(b->ctx, e, "batch join");
+    return OLAP_OK;
 }
 
 void batch_release(olap_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_chunks) cudaFree(b->d_chunks);
     if (b->d_next) cudaFree(b->d_next);
@@ -616,7 +635,17 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
         batch_release(b);
         return cuda_fail(ctx, e, "batch kernel set-up");
     }
-    b->grid_topk = ctx->sm_count * std::max(1, std::min(per_t, 2));
+    const int topk_per_sm = ctx->opts.batch_topk_ctas_per_sm > 0 ? ctx->opts.batch_topk_ctas_per_sm : 2;
+    b->grid_topk = ctx->sm_count * std::max(1, std::min(per_t, topk_per_sm));
+    b->overlap = ctx->opts.batch_overlap == 1 && n_topk > 0 && n_items > n_topk;
+    if (b->overlap &&
+        ((e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess ||
+         (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+         (e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming)) != cudaSuccess)) {
+        cudaGetLastError();
+        batch_release(b);
+        return cuda_fail(ctx, e, "batch streams");
+    }
     b->grid_probe = ctx->sm_count * std::max(1, per_p);
     if ((e = cudaMalloc(&b->d_items, std::max<uint64_t>(1, n_items) * sizeof(Item))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_chunks, std::max<size_t>(1, chunks.size()) * sizeof(ProbeChunk))) != cudaSuccess ||

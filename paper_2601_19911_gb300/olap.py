@@ -72,6 +72,8 @@ class olap_opts(ctypes.Structure):
         ("l2_fetch_bytes", ctypes.c_int),
         ("topk_digit_bits", ctypes.c_int),
         ("host_access", ctypes.c_int),
+        ("batch_overlap", ctypes.c_int),
+        ("batch_topk_ctas_per_sm", ctypes.c_int),
     ]
 
 
@@ -320,11 +322,12 @@ class Context:
                  topk_filter: int = FILTER_AUTO, topk_tile_bytes: int = 0, topk_stages: int = 0,
                  topk_ctas_per_sm: int = 0, join_partitions: int = 0, join_bucket_loads: int = 0,
                  l2_fetch_bytes: int = 0, topk_digit_bits: int = 0, block_threads: int = 0,
-                 host_access: int = 0):
+                 host_access: int = 0, batch_overlap: int = 0, batch_topk_ctas_per_sm: int = 0):
         self.lib = load()
         opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, block_threads, load_factor, staging_bytes,
                          topk_filter, topk_tile_bytes, topk_stages, topk_ctas_per_sm, join_partitions,
-                         join_bucket_loads, l2_fetch_bytes, topk_digit_bits, host_access)
+                         join_bucket_loads, l2_fetch_bytes, topk_digit_bits, host_access, batch_overlap,
+                         batch_topk_ctas_per_sm)
         h = ctypes.c_void_p()
         st = self.lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h))
         if st != OK:

@@ -46,7 +46,8 @@ def test_no_cpu_fallback_without_gpu(lib):
 @pytest.mark.parametrize("field,value", [("join_partitions", 3), ("join_partitions", 512), ("join_partitions", -1),
                                          ("load_factor", 0.95), ("topk_filter", 7), ("join_bucket_loads", 3),
                                          ("l2_fetch_bytes", 48), ("topk_digit_bits", 7), ("topk_digit_bits", 13),
-                                         ("block_threads", 384), ("host_access", 2)])
+                                         ("block_threads", 384), ("host_access", 2), ("batch_overlap", 2),
+                                         ("batch_topk_ctas_per_sm", 3)])
 def test_bad_options_are_rejected_before_any_device_call(lib, field, value):
     opts = olap.olap_opts()
     setattr(opts, field, value)

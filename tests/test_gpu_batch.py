@@ -161,3 +161,22 @@ def test_host_rejects_k_above_limit(ctx):
     with pytest.raises(olap.OlapError) as ei:
         ctx.batch([olap.topk_item(keys, 4097, olap.DESC, out, out, c)])
     assert ei.value.status == olap.E_INVALID
+
+
+def test_side_by_side_branches_match_oracle():
+    """The graph with the Top-K and probe kernels on two branches gives the
+    same results as the serial graph."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0, batch_overlap=1)
+    try:
+        items, q, b, table = _make(c, n_topk=60, n_probe=12, seed=21)
+        batch = c.batch(items)
+        batch.run()
+        c.sync()
+        assert batch.errors() == 0
+        _verify(q, b)
+        batch.free()
+        table.free()
+    finally:
+        c.close()
