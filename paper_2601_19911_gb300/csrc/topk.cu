@@ -773,12 +773,32 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
                 a.out_rid1[pos] = erid;
             }
             if (!grid_sync(a.bar, &ctl->err)) return report(a);
-            // Rank every bucket in shared memory: one CTA per bucket.
+            // Buckets of at most 32 entries: one warp each, ranked in
+            // registers (lane i holds entry i; the others come by shuffle).
+            for (int b = gw; b < TK_BINS; b += nwarps) {
+                const unsigned m = hv[b];
+                if (m == 0 || m > 32) continue;
+                const unsigned o = off[b];
+                uint64_t er = 0;
+                uint32_t erid = 0;
+                if (lane < m) {
+                    er = __ldcg(a.out_r1 + o + lane);
+                    erid = __ldcg(a.out_rid1 + o + lane);
+                }
+                unsigned c = 0;
+                for (unsigned j = 0; j < m; ++j) {
+                    const uint64_t jr = __shfl_sync(0xFFFFFFFFu, er, j);
+                    const uint32_t jrid = __shfl_sync(0xFFFFFFFFu, erid, j);
+                    c += (jr < er || (jr == er && (jrid < erid || (jrid == erid && j < lane)))) ? 1u : 0u;
+                }
+                if (lane < m) write_result(a, o + c, er, erid);
+            }
+            // Larger buckets: one CTA each, ranked in shared memory.
             uint64_t* br = reinterpret_cast<uint64_t*>(smem + TK_BINS * 4);
             uint32_t* brid = reinterpret_cast<uint32_t*>(smem + TK_BINS * 4 + TK_SMALL * 8);
             for (int b = blockIdx.x; b < TK_BINS; b += gridDim.x) {
                 const unsigned m = hv[b];
-                if (m == 0) continue;
+                if (m <= 32) continue;
                 const unsigned o = off[b];
                 for (unsigned i = threadIdx.x; i < m; i += TK_TPB) {
                     br[i] = __ldcg(a.out_r1 + o + i);
