@@ -24,8 +24,11 @@
  *     context, its device scratch, its pinned staging buffers and join tables.
  *   - Pointers tagged OLAP_MEM_DEVICE must be device memory of the context's
  *     device; OLAP_MEM_HOST_PINNED must be page-locked host memory;
- *     OLAP_MEM_HOST may be any host memory (staged through pinned buffers).
- *   - Keys must be naturally aligned (8 bytes for int64, 4 for float32).
+ *     OLAP_MEM_HOST may be any host memory (read by a copy kernel where the
+ *     device accesses pageable memory through the host page tables, else
+ *     staged through pinned buffers; see olap_host_access).
+ *   - Keys must be naturally aligned (8 bytes for 8-byte key types, 4 for
+ *     4-byte ones).
  *   - Blocking calls return after the result is in the output buffers.
  *     Calls suffixed _async only enqueue work on the given stream, take device
  *     pointers only, and report device-side status through a device word.
