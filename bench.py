@@ -38,7 +38,7 @@ METRIC = "Top-K Gkeys/s & join probes/s (% HBM peak); batched vs per-query; gate
 # 2^26 uniform keys, K = 1000, register filter; the traffic of a full launch
 # is this figure times n (the reads are the keys, the writes the candidates,
 # both in proportion to n).  Valid only for that configuration.
-FILTER_DRAM_BYTES_PER_KEY = {"i64": 540_177_408 / 2**26, "f32": 271_681_792 / 2**26}
+FILTER_DRAM_BYTES_PER_KEY = {"i64": 540_344_320 / 2**26, "f32": 271_533_824 / 2**26}
 
 
 def _kernel_pass(ctx, steps, launch):

@@ -113,8 +113,13 @@ __device__ __forceinline__ void and_or(uint64_t w0, uint64_t w1, uint64_t* ao) {
     ao[3] |= w1;
 }
 
-// Warp-reduce running AND / OR words and merge them into `dst` (lane 0).
+// Reduce the running AND / OR words over the CTA (warp shuffles, then the
+// warps' results in shared memory) and merge them into `dst` with four
+// atomics per CTA: same-address atomics serialise in L2, so one per warp
+// would cost thousands of serial updates over the grid.  Whole CTA calls.
+template <int TPB>
 __device__ __forceinline__ void and_or_merge(uint64_t* ao, unsigned long long* dst) {
+    __shared__ unsigned long long s_ao[TPB / 32][4];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ao[0] &= __shfl_xor_sync(0xFFFFFFFFu, ao[0], o);
@@ -122,12 +127,23 @@ __device__ __forceinline__ void and_or_merge(uint64_t* ao, unsigned long long* d
         ao[2] |= __shfl_xor_sync(0xFFFFFFFFu, ao[2], o);
         ao[3] |= __shfl_xor_sync(0xFFFFFFFFu, ao[3], o);
     }
-    if ((threadIdx.x & 31u) == 0) {
-        atomicAnd(dst + 0, static_cast<unsigned long long>(ao[0]));
-        atomicAnd(dst + 1, static_cast<unsigned long long>(ao[1]));
-        atomicOr(dst + 2, static_cast<unsigned long long>(ao[2]));
-        atomicOr(dst + 3, static_cast<unsigned long long>(ao[3]));
+    if ((threadIdx.x & 31u) == 0)
+        for (int j = 0; j < 4; ++j) s_ao[threadIdx.x >> 5][j] = ao[j];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t r[4] = {~0ull, ~0ull, 0ull, 0ull};
+        for (int w = 0; w < TPB / 32; ++w) {
+            r[0] &= s_ao[w][0];
+            r[1] &= s_ao[w][1];
+            r[2] |= s_ao[w][2];
+            r[3] |= s_ao[w][3];
+        }
+        atomicAnd(dst + 0, static_cast<unsigned long long>(r[0]));
+        atomicAnd(dst + 1, static_cast<unsigned long long>(r[1]));
+        atomicOr(dst + 2, static_cast<unsigned long long>(r[2]));
+        atomicOr(dst + 3, static_cast<unsigned long long>(r[3]));
     }
+    __syncthreads();
 }
 
 // First bit position (0 = MSB of w0) where the entries behind merged AND / OR

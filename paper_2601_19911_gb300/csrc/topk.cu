@@ -408,8 +408,7 @@ __device__ void hist_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_t
         if (dig != 0xFFFFFFFFu && lane == static_cast<unsigned>(__ffs(peers) - 1))
             atomicAdd(&sh[dig], static_cast<unsigned>(__popc(peers)));
     }
-    and_or_merge(acc, ao);
-    __syncthreads();
+    and_or_merge<TK_TPB>(acc, ao);
     for (int b = threadIdx.x; b < TK_BINS; b += TK_TPB)
         if (sh[b]) atomicAdd(&gh[b], sh[b]);
 }
@@ -708,7 +707,7 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
                     and_or(w0, w1, acc);
                 }
             }
-            and_or_merge(acc, ctl->fin);
+            and_or_merge<TK_TPB>(acc, ctl->fin);
         }
         if (!grid_sync(a.bar, &ctl->err)) return report(a);
         const int L0 = min(first_diff(ctl->fin, TB), TB - 1);
