@@ -709,6 +709,13 @@ def _gpu_cpu_affinity(index: int):
         out = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True, timeout=30).stdout
     except Exception:
         return None
+    return _parse_topo_affinity(out, index)
+
+
+def _parse_topo_affinity(out: str, index: int):
+    """The "CPU Affinity" cell of row GPU`index` in `nvidia-smi topo -m`
+    output (tab-separated; ranges like "0-71,144-215") as a set of core
+    numbers, or None when the table, the row or the column is missing."""
     lines = [ln for ln in out.splitlines() if ln.strip()]
     if not lines:
         return None
@@ -854,7 +861,8 @@ def run_ours(args):
                      "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w + (4 * n if hr is not None else 0),
                 "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
-        "gpu_launches": args.steps * (3 if (n > (1 << 21) and k <= n // 256) else 2),
+        # kernels one Top-K call launched (each reported its own event time)
+        "gpu_launches": args.steps * len(kms),
         "clocks": clk.summary(),
     }
     if "join" in workloads:
@@ -904,6 +912,7 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="topk,join,batched,fullrow,gate,serving",
                     help="comma list: topk (the headline value), join (probe sub-object), batched (executor), "
+                         "fullrow (full-row vs key-only transfer), gate (break-even validation), "
                          "serving (gated vs always-on stream)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",
                     help="build multiplicity (unique|mult14), probe distribution (uniform|zipf), hit rate")
