@@ -82,16 +82,31 @@ olap_status ensure_part(olap_ctx* ctx, size_t bytes) {
 }
 
 olap_status ensure_pinned(olap_ctx* ctx) {
-    if (ctx->pinned[0]) return OLAP_OK;
+    if (ctx->pinned_bytes) return OLAP_OK;
     const size_t b = ctx->opts.staging_bytes ? ctx->opts.staging_bytes : (64ull << 20);
+    // All or nothing: a partial set (one buffer, or a buffer without its
+    // event) would make the staged copies spin on zero-length chunks.
+    auto undo = [&](cudaError_t e, const char* what) {
+        cudaGetLastError();
+        for (int i = 0; i < 2; ++i) {
+            if (ctx->pinned[i]) cudaFreeHost(ctx->pinned[i]);
+            if (ctx->pinned_ev[i]) cudaEventDestroy(ctx->pinned_ev[i]);
+            ctx->pinned[i] = nullptr;
+            ctx->pinned_ev[i] = nullptr;
+        }
+        return cuda_fail(ctx, e, what);
+    };
     for (int i = 0; i < 2; ++i) {
         cudaError_t e = cudaMallocHost(&ctx->pinned[i], b);
         if (e != cudaSuccess) {
-            cudaGetLastError();
-            return cuda_fail(ctx, e, "pinned staging allocation");
+            ctx->pinned[i] = nullptr;
+            return undo(e, "pinned staging allocation");
         }
         e = cudaEventCreateWithFlags(&ctx->pinned_ev[i], cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "staging event");
+        if (e != cudaSuccess) {
+            ctx->pinned_ev[i] = nullptr;
+            return undo(e, "staging event");
+        }
     }
     ctx->pinned_bytes = b;
     return OLAP_OK;
