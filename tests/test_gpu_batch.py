@@ -180,3 +180,91 @@ def test_side_by_side_branches_match_oracle():
         table.free()
     finally:
         c.close()
+
+
+@pytest.mark.slow
+def test_full_size_batch_sampled():
+    """The batched workload at full size, in the configuration the benchmark
+    times: 4096 Top-K queries (N ~ logU[1e3, 4e6), K ~ U{1..1000}, int64
+    uniform keys drawn on the device, DESC) and 1024 probe batches
+    (n ~ logU[1e3, 1e6), hit rate 0.5) against one 2^22-key unique table, on
+    an autotuned context, one graph launch.  Every item: status OK and the
+    exact count; every Top-K output: sorted, ties by row-id, and each key the
+    key of its row; a sample of items (the largest and a random draw) against
+    the oracle bit for bit."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0)
+    try:
+        c.autotune(topk_n=1 << 20, topk_k=500, join_build_n=1 << 22, join_probe_n=1 << 20,
+                   join_hit_rate=0.5, reps=3)
+        n_topk, n_probe = 4096, 1024
+        ns, ks = datagen.batched_topk_queries(n_topk, 1e3, 4e6, 1000, seed=3)
+        offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        kseed = datagen.stream_seed(3, 0)
+        keys = datagen.splitmix64_torch(kseed, int(offs[-1]), device="cuda")
+        cnt = np.minimum(ks, ns)
+        koffs = np.concatenate([[0], np.cumsum(ks)]).astype(np.int64)
+        out_k = torch.empty(int(koffs[-1]), dtype=torch.int64, device="cuda")
+        out_r = torch.empty(int(koffs[-1]), dtype=torch.int32, device="cuda")
+        counts = torch.zeros(n_topk + n_probe, dtype=torch.int64, device="cuda")
+        status = torch.full((n_topk + n_probe,), -1, dtype=torch.int32, device="cuda")
+        items = []
+        for i in range(n_topk):
+            a, e = int(koffs[i]), int(koffs[i + 1])
+            items.append(olap.topk_item(keys[int(offs[i]):int(offs[i + 1])], int(ks[i]), olap.DESC,
+                                        out_k[a:e], out_r[a:e], counts[i:i + 1], d_status=status[i:i + 1]))
+        b = datagen.join_build(1 << 22, "unique", seed=3)
+        table = c.join_build(torch.from_numpy(b.keys).cuda())
+        pns = datagen.batched_probe_sizes(n_probe, 1e3, 1e6, seed=3)
+        poffs = np.concatenate([[0], np.cumsum(pns)]).astype(np.int64)
+        p = datagen.join_probe(int(poffs[-1]), b, 0.5, "uniform", seed=3)
+        hits = np.concatenate([[0], np.cumsum(p.hit)]).astype(np.int64)
+        pk = torch.from_numpy(p.keys).cuda()
+        pairs = torch.empty((int(hits[-1]) + 1, 2), dtype=torch.int32, device="cuda")
+        for j in range(n_probe):
+            a, e = int(poffs[j]), int(poffs[j + 1])
+            h0, h1 = int(hits[a]), int(hits[e])
+            items.append(olap.probe_item(table, pk[a:e], pairs[h0:h1 + 1], h1 - h0,
+                                         counts[n_topk + j:n_topk + j + 1],
+                                         d_status=status[n_topk + j:n_topk + j + 1]))
+        batch = c.batch(items)
+        batch.run()
+        c.sync()
+        assert batch.errors() == 0
+        assert int((status != olap.OK).sum().item()) == 0
+        got_counts = counts.cpu().numpy()
+        np.testing.assert_array_equal(got_counts[:n_topk], cnt)
+        np.testing.assert_array_equal(got_counts[n_topk:], np.diff(hits[poffs]))
+
+        # every Top-K output: a real row, in order (rank DESC, row-id ASC on ties)
+        valid = torch.from_numpy(np.concatenate([np.arange(koffs[i], koffs[i] + cnt[i]) for i in range(n_topk)])).cuda()
+        seg = torch.from_numpy(np.repeat(np.arange(n_topk), cnt)).cuda()
+        ok_k, ok_r = out_k[valid], out_r[valid].to(torch.int64)
+        assert int(((ok_r < 0) | (ok_r >= torch.from_numpy(ns).cuda()[seg])).sum().item()) == 0
+        src = torch.from_numpy(offs[:-1]).cuda()[seg] + ok_r
+        assert torch.equal(keys[src], ok_k)
+        same = seg[1:] == seg[:-1]
+        desc = (ok_k[:-1] > ok_k[1:]) | ((ok_k[:-1] == ok_k[1:]) & (ok_r[:-1] < ok_r[1:]))
+        assert int((same & ~desc).sum().item()) == 0
+
+        # a sample against the oracle: the largest items and a seeded draw
+        rng = np.random.default_rng(7)
+        t_pick = np.unique(np.concatenate([np.argsort(ns)[-6:], rng.choice(n_topk, 20, replace=False)]))
+        hk, hr = out_k.cpu().numpy(), out_r.cpu().numpy().view(np.uint32)
+        for i in t_pick:
+            host = datagen.splitmix64(kseed, int(ns[i]), start=int(offs[i])).view(np.int64)
+            wk, wr = oracle.topk(host, int(ks[i]), olap.DESC)
+            a = int(koffs[i])
+            np.testing.assert_array_equal(hr[a:a + len(wr)], wr)
+            np.testing.assert_array_equal(hk[a:a + len(wr)], wk)
+        p_pick = np.unique(np.concatenate([np.argsort(pns)[-3:], rng.choice(n_probe, 9, replace=False)]))
+        hp = pairs.cpu().numpy().view(np.uint32)
+        for j in p_pick:
+            a, e = int(poffs[j]), int(poffs[j + 1])
+            h0, h1 = int(hits[a]), int(hits[e])
+            np.testing.assert_array_equal(_packed(hp[h0:h1]), oracle.join(b.keys, p.keys[a:e]))
+        batch.free()
+        table.free()
+    finally:
+        c.close()
