@@ -213,7 +213,7 @@ def test_full_size(ctx, mult, dist, hit):
     ctx.join_probe_async(t, dk, out, need, cnt)
     ctx.sync()
     assert int(cnt.item()) == need
-    pairs = out.view(torch.int64) if False else out
+    pairs = out
     pr = pairs[:, 0].to(torch.int64) & 0xFFFFFFFF
     br = pairs[:, 1].to(torch.int64) & 0xFFFFFFFF
     bkd = torch.from_numpy(b.keys).cuda()
