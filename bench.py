@@ -55,6 +55,11 @@ def _kernel_pass(ctx, steps, launch):
     return {nm: float(np.mean(v)) for nm, v in acc.items()}
 
 
+def _topk_kernels(kms) -> int:
+    """Kernels one Top-K call launched: those that reported an event time."""
+    return sum(1 for nm in kms if nm.startswith("topk_"))
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -182,7 +187,8 @@ def run_reference(args):
             "config": {"workload": f"topk_i64_uniform_n{ns}_k{k}_desc (bounded sample of the 2^28 workload)",
                        "n": ns, "k": k},
             "cpu_baseline": {"value": v, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed steps of the oracle on {ns} keys"},
+                             "sample": f"{args.steps} timed steps of the oracle on {ns} keys",
+                             "host": _host_info()},
             "e2e": {"value": v, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -701,6 +707,129 @@ def serving_leg(args, ctx, torch):
                      "topk_n_star_k100": int(nstar), "calibration_points": len(cal_n)}}
 
 
+def _median_p95(xs):
+    """Median and 95th percentile (linear interpolation) of a list of times."""
+    a = np.asarray(xs, dtype=np.float64)
+    return float(np.median(a)), float(np.percentile(a, 95))
+
+
+def single_leg(args, ctx, torch):
+    """The single Top-K query: 2^20 int64 keys drawn uniformly over the full
+    range (seed 0), explicit row-ids 0..N-1, K = 100, DESC.  The keys fit in
+    L2, so this is a latency figure: one query at a time, 31 warmed runs,
+    median and P95, kernel-only (device-resident keys and row-ids, CUDA
+    events around each call) and end to end through the blocking call (keys
+    and row-ids, 12 MiB, from pinned host memory, and again from pageable
+    host memory; K results back to the same kind of memory)."""
+    from paper_2601_19911_gb300 import datagen, olap
+    n, k, reps = 1 << 20, 100, 31
+    keys = datagen.topk_keys(n, "uniform", "i64", seed=0)
+    rid = datagen.identity_rowids(n)
+    dk = torch.from_numpy(keys).cuda()
+    dr = torch.from_numpy(rid.view(np.int32)).cuda()
+    ok = torch.empty(k, dtype=torch.int64, device="cuda")
+    orow = torch.empty(k, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    per_call = _topk_kernels(_kernel_pass(ctx, 1, lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)))
+    for _ in range(5):
+        ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
+    ctx.sync()
+    kern = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
+        b.record(stream)
+        ctx.sync()
+        kern.append(a.elapsed_time(b))
+
+    def e2e(kk, rr, o1, o2):
+        for _ in range(3):
+            ctx.topk(kk, k, olap.DESC, rowids=rr, out_keys=o1, out_rowids=o2)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            ctx.topk(kk, k, olap.DESC, rowids=rr, out_keys=o1, out_rowids=o2)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        return ts
+
+    pinned = e2e(torch.from_numpy(keys).pin_memory(), torch.from_numpy(rid.view(np.int32)).pin_memory(),
+                 torch.empty(k, dtype=torch.int64).pin_memory(), torch.empty(k, dtype=torch.int32).pin_memory())
+    pageable = e2e(keys, rid, np.empty(k, dtype=np.int64), np.empty(k, dtype=np.uint32))
+    km, kp = _median_p95(kern)
+    pm, pp = _median_p95(pinned)
+    gm, gp = _median_p95(pageable)
+    # kernels per call, plus the copy kernels of pageable memory where the
+    # device reads it directly (keys, row-ids in; keys, row-ids out)
+    launches = reps * per_call * 3 + (reps * 4 if ctx.host_direct else 0)
+    return {"metric": "single Top-K query latency", "unit": "ms (median, p95 of 31)",
+            "config": {"n": n, "k": k, "order": "desc", "key_type": "i64", "rowids": "explicit", "seed": 0},
+            "kernel": {"median_ms": km, "p95_ms": kp, "gkeys_s": n / (km * 1e-3) / 1e9},
+            "e2e_pinned": {"median_ms": pm, "p95_ms": pp, "gkeys_s": n / (pm * 1e-3) / 1e9,
+                           "h2d_bytes": n * 12, "d2h_bytes": k * 12},
+            "e2e_pageable": {"median_ms": gm, "p95_ms": gp, "gkeys_s": n / (gm * 1e-3) / 1e9,
+                             "host_access": "direct" if ctx.host_direct else "staged"},
+            "gpu_launches": launches}
+
+
+def link_leg(torch, nbytes: int = 1 << 30, reps: int = 10):
+    """The host link every offload crosses: pinned host <-> device copy
+    bandwidth (cudaMemcpyAsync through torch) of `nbytes`, CUDA events,
+    median of `reps`."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+
+    def rate(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return nbytes / (float(np.median(ts)) * 1e-3) / 1e9
+
+    h2d = rate(lambda: d.copy_(h, non_blocking=True))
+    d2h = rate(lambda: h.copy_(d, non_blocking=True))
+    del h, d
+    torch.cuda.empty_cache()
+    return {"h2d_gbs": h2d, "d2h_gbs": d2h, "bytes": nbytes, "reps": reps,
+            "memory": "pinned host <-> device, cudaMemcpyAsync"}
+
+
+def _parse_cpu_model(lscpu: str, cpuinfo: str):
+    """CPU model name from `lscpu` output ("Model name:"), else from
+    /proc/cpuinfo ("model name"), else None."""
+    for text, key in ((lscpu, "model name:"), (cpuinfo, "model name")):
+        for ln in text.splitlines():
+            if ln.strip().lower().startswith(key):
+                v = ln.split(":", 1)[1].strip() if ":" in ln else ""
+                if v and v != "-":
+                    return v
+    return None
+
+
+def _host_info():
+    """Cores and CPU model of the machine the CPU baseline runs on."""
+    import platform
+    lscpu = cpuinfo = ""
+    try:
+        lscpu = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            cpuinfo = f.read()
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(),
+            "cpu_model": _parse_cpu_model(lscpu, cpuinfo)}
+
+
 def _gpu_cpu_affinity(index: int):
     """CPU cores local to GPU `index` from `nvidia-smi topo -m` (its "CPU
     Affinity" column), as a set, or None when unknown."""
@@ -854,6 +983,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": algo_bytes,
                      "bytes_per_unit": f"{w} per key read once", "kernel_ms": kern_ms,
                      "kernel_ms_all": kms, "call_ms": call_ms,
+                     "call_ms_median": _median_p95(per_launch)[0], "call_ms_p95": _median_p95(per_launch)[1],
                      "call_frac": algo_bytes / (call_ms * 1e-3) / 1e9 / peak,
                      "timing": "CUDA events around each kernel on the library stream, "
                                f"{args.steps} further steps after the timed region",
@@ -862,9 +992,14 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w + (4 * n if hr is not None else 0),
                 "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
         # kernels one Top-K call launched (each reported its own event time)
-        "gpu_launches": args.steps * len(kms),
+        "gpu_launches": args.steps * _topk_kernels(kms),
         "clocks": clk.summary(),
     }
+    if "single" in workloads:
+        line["single"] = single_leg(args, ctx, torch)
+        line["gpu_launches"] += line["single"]["gpu_launches"]
+    if "link" in workloads:
+        line["link"] = link_leg(torch)
     if "join" in workloads:
         del dk, hk, dr, hr
         torch.cuda.empty_cache()
@@ -885,6 +1020,7 @@ def run_ours(args):
         line["serving"] = serving_leg(args, ctx, torch)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n, k)
+        line["cpu_baseline"]["host"] = _host_info()
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -910,8 +1046,9 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,join,batched,fullrow,gate,serving",
-                    help="comma list: topk (the headline value), join (probe sub-object), batched (executor), "
+    ap.add_argument("--workload", default="topk,single,link,join,batched,fullrow,gate,serving",
+                    help="comma list: topk (the headline value), single (2^20-key query latency), link (pinned "
+                         "copy bandwidth), join (probe sub-object), batched (executor), "
                          "fullrow (full-row vs key-only transfer), gate (break-even validation), "
                          "serving (gated vs always-on stream)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",

@@ -96,7 +96,7 @@ def test_parser_defaults_follow_the_timing_rules():
     assert a.dist == "uniform"
     legs = a.workload.split(",")
     assert legs[0] == "topk"
-    assert set(legs) == {"topk", "join", "batched", "fullrow", "gate", "serving"}
+    assert set(legs) == {"topk", "single", "link", "join", "batched", "fullrow", "gate", "serving"}
     # the keys at the default size exceed L2 (129 MB), so no flush is needed
     assert (1 << a.log2n) * 8 > 129 * 10**6
 
@@ -108,3 +108,32 @@ def test_filter_traffic_constants_cover_the_algorithmic_bytes():
     for kt, width in (("i64", 8), ("f32", 4)):
         per_key = bench.FILTER_DRAM_BYTES_PER_KEY[kt]
         assert width <= per_key < 1.05 * width
+
+
+# -- latency statistics, launch counts and host description ------------------
+
+def test_median_p95():
+    m, p = bench._median_p95(list(range(1, 101)))          # 1..100
+    assert m == 50.5
+    assert math.isclose(p, 95.05)                          # linear interpolation
+    assert bench._median_p95([3.0]) == (3.0, 3.0)
+
+
+def test_topk_kernel_count():
+    assert bench._topk_kernels({"topk_prepare_ms": 0.01, "topk_filter_ms": 0.3, "topk_select_ms": 0.03}) == 3
+    assert bench._topk_kernels({"topk_prepare_ms": 0.01, "topk_select_ms": 0.03, "join_probe_ms": 4.0}) == 2
+    assert bench._topk_kernels({}) == 0
+
+
+def test_cpu_model_from_lscpu_then_cpuinfo():
+    lscpu = "Architecture:  aarch64\nVendor ID:  ARM\nModel name:  Neoverse-V2\nCPU(s): 72\n"
+    assert bench._parse_cpu_model(lscpu, "") == "Neoverse-V2"
+    cpuinfo = "processor\t: 0\nmodel name\t: Intel(R) Xeon(R) Platinum\nflags\t: fpu\n"
+    assert bench._parse_cpu_model("", cpuinfo) == "Intel(R) Xeon(R) Platinum"
+    assert bench._parse_cpu_model("Model name: -\n", cpuinfo) == "Intel(R) Xeon(R) Platinum"
+    assert bench._parse_cpu_model("", "CPU part\t: 0xd4f\n") is None
+
+
+def test_host_info_here():
+    h = bench._host_info()
+    assert h["nproc"] >= 1 and h["machine"]
