@@ -284,10 +284,28 @@ def ptr(buf) -> int | None:
     if buf is None:
         return None
     if isinstance(buf, np.ndarray):
-        assert buf.flags["C_CONTIGUOUS"]
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffers must be C-contiguous")
         return buf.ctypes.data
-    assert buf.is_contiguous()
+    if not buf.is_contiguous():
+        raise ValueError("tensors must be contiguous")
     return buf.data_ptr()
+
+
+def _check_rowids(rowids, where: int, n: int) -> None:
+    """Explicit row-ids must sit in the same kind of memory as the keys and
+    hold one entry per key."""
+    if rowids is None:
+        return
+    if mem_kind(rowids) != where:
+        raise ValueError("row-ids must be in the same kind of memory as the keys")
+    if numel(rowids) != n:
+        raise ValueError(f"{numel(rowids)} row-ids for {n} keys")
+
+
+def _check_count(got: int, want: int) -> None:
+    if got != want:
+        raise RuntimeError(f"the library returned {got} results where {want} were due")
 
 
 def key_type_of(buf) -> int:
@@ -378,14 +396,13 @@ class Context:
             out_keys = np.empty(max(cnt, 1), dtype=KEY_NUMPY[kt])
             out_rowids = np.empty(max(cnt, 1), dtype=np.uint32)
         where = mem_kind(keys)
-        if rowids is not None:
-            assert mem_kind(rowids) == where and numel(rowids) == n
+        _check_rowids(rowids, where, n)
         ow = mem_kind(out_keys)
         got = ctypes.c_uint64()
         st = self.lib.olap_topk(self.h, ptr(keys), kt, ptr(rowids), where, n, int(k), int(order),
                                 ptr(out_keys), ptr(out_rowids), ow, ctypes.byref(got))
         self.check(st)
-        assert got.value == cnt
+        _check_count(got.value, cnt)
         return out_keys[:cnt], out_rowids[:cnt]
 
     def topk_rows(self, rows, row_bytes: int, key_offset: int, key_type: int, k: int, order: int = DESC,
@@ -394,7 +411,8 @@ class Context:
         bytes (numpy, pinned or CUDA tensor); returns (rows, row-ids) of the
         min(k, n) selected rows, whole."""
         nbytes = rows.nbytes if isinstance(rows, np.ndarray) else rows.numel() * rows.element_size()
-        assert nbytes % row_bytes == 0
+        if row_bytes <= 0 or nbytes % row_bytes:
+            raise ValueError("the row buffer must hold a whole number of rows")
         n = nbytes // row_bytes
         cnt = min(int(k), n)
         if out_rows is None:
@@ -404,15 +422,14 @@ class Context:
         self.check(self.lib.olap_topk_rows(self.h, ptr(rows), mem_kind(rows), n, row_bytes, key_offset, key_type,
                                            int(k), int(order), ptr(out_rows), ptr(out_rowids), mem_kind(out_rows),
                                            ctypes.byref(got)))
-        assert got.value == cnt
+        _check_count(got.value, cnt)
         return out_rows, (None if out_rowids is None else out_rowids[:cnt])
 
     # -- Join ----------------------------------------------------------------
     def join_build(self, keys, rowids=None, load_factor: float = 0.0) -> "JoinTable":
         """olap_join_build over int64 keys (numpy, pinned or CUDA tensor)."""
         where = mem_kind(keys)
-        if rowids is not None:
-            assert mem_kind(rowids) == where and numel(rowids) == numel(keys)
+        _check_rowids(rowids, where, numel(keys))
         h = ctypes.c_void_p()
         self.check(self.lib.olap_join_build(self.h, ptr(keys), ptr(rowids), where, numel(keys),
                                             float(load_factor), ctypes.byref(h)))
@@ -425,8 +442,7 @@ class Context:
         the first guess overflows."""
         where = mem_kind(keys)
         n = numel(keys)
-        if rowids is not None:
-            assert mem_kind(rowids) == where and numel(rowids) == n
+        _check_rowids(rowids, where, n)
         own = out is None
         if own:
             capacity = capacity if capacity is not None else max(16, 2 * n)
@@ -599,7 +615,8 @@ def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_
     cols = [np.ascontiguousarray(np.asarray(c, dtype=np.float64)) for c in
             (n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_ker_ms, t_post_ms)]
     cnt = cols[0].shape[0]
-    assert all(c.shape[0] == cnt for c in cols)
+    if any(c.shape[0] != cnt for c in cols):
+        raise ValueError("every sample sequence must have the same length")
     ptrs = [c.ctypes.data_as(_dp) for c in cols]
     smp = olap_gate_samples(op, weighting, cnt, *ptrs, topk_cpu, 0)
     m = olap_gate_model()

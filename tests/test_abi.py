@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2601_19911_gb300 import build, olap
@@ -90,3 +91,22 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for f in cls._fields_:
             assert int(got[f"{name}.{f[0]}"]) == getattr(cls, f[0]).offset, (name, f[0])
+
+
+def test_binding_rejects_bad_buffers_without_asserts():
+    """Argument checks of the binding raise real exceptions (they survive
+    python -O), before any call crosses the ABI."""
+    a = np.arange(20, dtype=np.int64)
+    with pytest.raises(ValueError):
+        olap.ptr(a[::2])                                   # not contiguous
+    olap._check_rowids(None, olap.MEM_HOST, 5)
+    olap._check_rowids(np.arange(5, dtype=np.uint32), olap.MEM_HOST, 5)
+    with pytest.raises(ValueError):
+        olap._check_rowids(np.arange(4, dtype=np.uint32), olap.MEM_HOST, 5)
+    with pytest.raises(ValueError):
+        olap._check_rowids(np.arange(5, dtype=np.uint32), olap.MEM_DEVICE, 5)
+    with pytest.raises(RuntimeError):
+        olap._check_count(3, 4)
+    with pytest.raises(ValueError):
+        olap.gate_calibrate(olap.OP_TOPK, [1e3, 1e4], [10, 10], [8e3, 8e4], [10, 10], [1.0, 2.0],
+                            [0.1, 0.2], [0.1, 0.1], [0.01])
