@@ -323,6 +323,14 @@ olap_status olap_join_probe_async(olap_ctx* ctx, const olap_join_table* table, c
                                   const uint32_t* d_rowids, uint64_t n, olap_pair* d_out, uint64_t capacity,
                                   uint64_t* d_count, void* stream);
 
+/* How a probe of n rows against `table` runs on this context (Sec. III-B,
+ * parallel probing): *parts = 1 for the direct probe (one kernel), else the
+ * number of radix partitions of the partitioned probe (a count, a scatter and
+ * a probe kernel).  Decided by the context's join_partitions option and, when
+ * automatic, by the table's size against the device's L2.  Host arithmetic
+ * only; OLAP_E_INVALID for a NULL or freed table or a NULL *parts. */
+olap_status olap_join_probe_partitions(olap_ctx* ctx, const olap_join_table* table, uint64_t n, int* parts);
+
 /* Table facts: build rows, buckets (2 slots each), rows in the side list. */
 olap_status olap_join_table_info(const olap_join_table* table, uint64_t* n_build, uint64_t* n_buckets,
                                  uint64_t* n_side);

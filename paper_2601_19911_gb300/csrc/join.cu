@@ -553,6 +553,16 @@ olap_status olap_join_probe(olap_ctx* ctx, const olap_join_table* table, const i
     return OLAP_OK;
 }
 
+olap_status olap_join_probe_partitions(olap_ctx* ctx, const olap_join_table* table, uint64_t n, int* parts) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (!parts) return fail(ctx, OLAP_E_INVALID, "parts is NULL");
+    olap_status st = check_join_table(ctx, table);
+    if (st != OLAP_OK) return st;
+    *parts = probe_parts(ctx, table, n);
+    return OLAP_OK;
+}
+
 olap_status olap_join_table_info(const olap_join_table* t, uint64_t* n_build, uint64_t* n_buckets, uint64_t* n_side) {
     if (!t || !t->slots) return OLAP_E_INVALID;
     if (n_build) *n_build = t->n_build;

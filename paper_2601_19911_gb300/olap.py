@@ -32,7 +32,8 @@ EXPORTS = [
     "olap_ctx_host_direct", "olap_selftest_wait",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last", "olap_topk_rows",
     "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_autotune",
-    "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_table_info", "olap_join_free",
+    "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_probe_partitions",
+    "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
     "olap_batch_create", "olap_batch_run", "olap_batch_run_per_query", "olap_batch_errors", "olap_batch_free",
     "olap_serve",
@@ -221,6 +222,8 @@ def load(path: str | None = None):
         lib.olap_join_probe.argtypes = [vp, vp, vp, vp, i32, u64, vp, i32, u64, ctypes.POINTER(u64)]
         lib.olap_join_probe_async.restype = i32
         lib.olap_join_probe_async.argtypes = [vp, vp, vp, vp, u64, vp, u64, vp, vp]
+        lib.olap_join_probe_partitions.restype = i32
+        lib.olap_join_probe_partitions.argtypes = [vp, vp, u64, ctypes.POINTER(ctypes.c_int)]
         lib.olap_join_table_info.restype = i32
         lib.olap_join_table_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
         lib.olap_join_free.restype = None
@@ -466,6 +469,13 @@ class Context:
                                                   ptr(d_out), int(capacity), ptr(d_count), stream))
 
     # -- Batched executor ----------------------------------------------------
+    def join_probe_partitions(self, table: "JoinTable", n: int) -> int:
+        """olap_join_probe_partitions: 1 for the direct probe, else the radix
+        partitions a probe of n rows against `table` uses on this context."""
+        parts = ctypes.c_int()
+        self.check(self.lib.olap_join_probe_partitions(self.h, table.h, int(n), ctypes.byref(parts)))
+        return parts.value
+
     def batch(self, items) -> "Batch":
         """olap_batch_create from a list of olap_batch_item."""
         arr = (olap_batch_item * max(1, len(items)))(*items)

@@ -228,3 +228,35 @@ def test_full_size(ctx, mult, dist, hit):
     t.free()
     del dk, out, bkd
     torch.cuda.empty_cache()
+
+
+def test_probe_partitions_query():
+    """olap_join_probe_partitions reports the probe's mode: direct for a small
+    probe, a power of two above 1 for a table well above L2 with a large
+    probe side, the forced count when the option sets one."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    b = datagen.join_build(1 << 22, "unique", seed=61)          # 2^22 buckets x 32 B = 128 MiB, above L2
+    c = olap.Context(0)
+    try:
+        t = c.join_build(torch.from_numpy(b.keys).cuda())
+        assert c.join_probe_partitions(t, 1000) == 1           # too few rows to pay for partitioning
+        parts = c.join_probe_partitions(t, 1 << 24)
+        assert parts > 1 and parts & (parts - 1) == 0
+        small = c.join_build(b.keys[:1000])
+        assert c.join_probe_partitions(small, 1 << 24) == 1     # the table fits in L2
+        small.free()
+        with pytest.raises(olap.OlapError) as ei:
+            c.join_probe_partitions(small, 10)                  # freed
+        assert ei.value.status == olap.E_INVALID
+        t.free()
+    finally:
+        c.close()
+    for opt, want in ((1, 1), (16, 16)):
+        c = olap.Context(0, join_partitions=opt)
+        try:
+            t = c.join_build(b.keys[:100_000])
+            assert c.join_probe_partitions(t, 5000) == want
+            t.free()
+        finally:
+            c.close()
