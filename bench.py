@@ -55,11 +55,6 @@ def _kernel_pass(ctx, steps, launch):
     return {nm: float(np.mean(v)) for nm, v in acc.items()}
 
 
-def _topk_kernels(kms) -> int:
-    """Kernels one Top-K call launched: those that reported an event time."""
-    return sum(1 for nm in kms if nm.startswith("topk_"))
-
-
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -224,10 +219,12 @@ def join_leg(args, ctx, torch, world):
     _barrier(world)
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
+        l0 = ctx.launches()
         for i in range(steps):
             evs[i][0].record(stream)
             ctx.join_probe_async(table, dk, out, need, cnt)
             evs[i][1].record(stream)
+        launches = ctx.launches() - l0
         ctx.sync()
         torch.cuda.synchronize()
     per = [a.elapsed_time(b_) for a, b_ in evs]
@@ -237,10 +234,12 @@ def join_leg(args, ctx, torch, world):
     hout = torch.empty((need, 2), dtype=torch.int32).pin_memory()
     ctx.join_probe(table, hk, out=hout)
     e2e_steps = max(2, min(5, args.e2e_steps))
+    l0 = ctx.launches()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.join_probe(table, hk, out=hout)
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    launches += ctx.launches() - l0
     kms = _kernel_pass(ctx, min(steps, 10), lambda: ctx.join_probe_async(table, dk, out, need, cnt))
     kern_ms = kms["join_probe_ms"]
     # the partitioned probe is three launches (count, scatter, probe), the
@@ -274,7 +273,7 @@ def join_leg(args, ctx, torch, world):
                      "traffic": args.join_traffic},
         "e2e": {"value": world * npr / e2e_s / 1e9, "unit": "Gprobes/s", "ms_per_step": e2e_s * 1e3,
                 "h2d_bytes_per_step": npr * 8, "d2h_bytes_per_step": need * 8 + 8},
-        "gpu_launches": steps * len(kernels),
+        "gpu_launches": launches,
         "clocks": clk.summary(),
     }
 
@@ -330,19 +329,21 @@ def batched_leg(args, ctx, torch):
             fn()
         ctx.sync()
         a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ctx.launches()
         a_.record(stream)
         for _ in range(reps):
             fn()
         b_.record(stream)
+        n_launch = ctx.launches() - l0
         ctx.sync()
         torch.cuda.synchronize()
-        return a_.elapsed_time(b_) / reps
+        return a_.elapsed_time(b_) / reps, n_launch
 
     with ClockSampler(torch.cuda.current_device()) as clk:
-        ms_graph = timed(batch.run, args.batch_reps)
+        ms_graph, launch_graph = timed(batch.run, args.batch_reps)
     errors = batch.errors()
     ok = int((status != olap.OK).sum().item()) == 0
-    ms_per_query = timed(batch.run_per_query, max(1, args.batch_reps // 5))
+    ms_per_query, launch_pq = timed(batch.run_per_query, max(1, args.batch_reps // 5))
     peak, peak_kind = _peaks()
     algo = float(offs[-1]) * 8 + float(ks.sum()) * 24 + float(poffs[-1]) * 40 + float(hits[-1]) * 8
     batch.free()
@@ -356,7 +357,9 @@ def batched_leg(args, ctx, torch):
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": algo / (ms_graph * 1e-3) / 1e9 / peak,
                          "bytes": "8 per Top-K key + 24 per selected row + 40 per probe + 8 per pair"},
-            "gpu_launches_graph": (1 if args.batch_topk else 0) + (2 if args.batch_probe else 0),
+            "gpu_launches": launch_graph + launch_pq,
+            "gpu_launches_per_graph_run": launch_graph // args.batch_reps,
+            "gpu_launches_per_query_run": launch_pq // max(1, args.batch_reps // 5),
             "autotune": tune, "clocks": clk.summary()}
 
 
@@ -736,11 +739,11 @@ def single_leg(args, ctx, torch):
     ok = torch.empty(k, dtype=torch.int64, device="cuda")
     orow = torch.empty(k, dtype=torch.int32, device="cuda")
     stream = torch.cuda.ExternalStream(ctx.stream)
-    per_call = _topk_kernels(_kernel_pass(ctx, 1, lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)))
     for _ in range(5):
         ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
     ctx.sync()
     kern = []
+    l0 = ctx.launches()
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -748,15 +751,19 @@ def single_leg(args, ctx, torch):
         b.record(stream)
         ctx.sync()
         kern.append(a.elapsed_time(b))
+    launches = ctx.launches() - l0
 
     def e2e(kk, rr, o1, o2):
+        nonlocal launches
         for _ in range(3):
             ctx.topk(kk, k, olap.DESC, rowids=rr, out_keys=o1, out_rowids=o2)
         ts = []
+        c0 = ctx.launches()
         for _ in range(reps):
             t0 = time.perf_counter()
             ctx.topk(kk, k, olap.DESC, rowids=rr, out_keys=o1, out_rowids=o2)
             ts.append((time.perf_counter() - t0) * 1e3)
+        launches += ctx.launches() - c0
         return ts
 
     pinned = e2e(torch.from_numpy(keys).pin_memory(), torch.from_numpy(rid.view(np.int32)).pin_memory(),
@@ -765,9 +772,6 @@ def single_leg(args, ctx, torch):
     km, kp = _median_p95(kern)
     pm, pp = _median_p95(pinned)
     gm, gp = _median_p95(pageable)
-    # kernels per call, plus the copy kernels of pageable memory where the
-    # device reads it directly (keys, row-ids in; keys, row-ids out)
-    launches = reps * per_call * 3 + (reps * 4 if ctx.host_direct else 0)
     return {"metric": "single Top-K query latency", "unit": "ms (median, p95 of 31)",
             "config": {"n": n, "k": k, "order": "desc", "key_type": "i64", "rowids": "explicit", "seed": 0},
             "kernel": {"median_ms": km, "p95_ms": kp, "gkeys_s": n / (km * 1e-3) / 1e9},
@@ -925,12 +929,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         start = torch.cuda.Event(enable_timing=True)
         end = torch.cuda.Event(enable_timing=True)
+        l0 = ctx.launches()
         start.record(stream)
         for i in range(args.steps):
             evs[i][0].record(stream)
             ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
             evs[i][1].record(stream)
         end.record(stream)
+        launches = ctx.launches() - l0
         ctx.sync()
         torch.cuda.synchronize()
     total_ms = start.elapsed_time(end)
@@ -950,10 +956,12 @@ def run_ours(args):
         ctx.topk(hk, k, olap.DESC, rowids=hr, out_keys=hok, out_rowids=horow)
     _barrier(world)
     e2e_steps = max(3, min(args.steps, args.e2e_steps))
+    l0 = ctx.launches()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.topk(hk, k, olap.DESC, rowids=hr, out_keys=hok, out_rowids=horow)
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    launches += ctx.launches() - l0
     e2e_value = replicas.whole_job_rate(n, world, e2e_s) / 1e9
 
     # -- per-kernel device time (events around each kernel), same workload ----
@@ -997,24 +1005,21 @@ def run_ours(args):
                      "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w + (4 * n if hr is not None else 0),
                 "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
-        # kernels one Top-K call launched (each reported its own event time)
-        "gpu_launches": args.steps * _topk_kernels(kms),
+        # the library's own count over the timed regions of `value` and `e2e`
+        "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     if "single" in workloads:
         line["single"] = single_leg(args, ctx, torch)
-        line["gpu_launches"] += line["single"]["gpu_launches"]
     if "link" in workloads:
         line["link"] = link_leg(torch)
     if "join" in workloads:
         del dk, hk, dr, hr
         torch.cuda.empty_cache()
         line["join"] = join_leg(args, ctx, torch, world)
-        line["gpu_launches"] += line["join"]["gpu_launches"]
     if "batched" in workloads:
         torch.cuda.empty_cache()
         line["batched"] = batched_leg(args, ctx, torch)
-        line["gpu_launches"] += line["batched"]["gpu_launches_graph"] * args.batch_reps
     if "fullrow" in workloads:
         torch.cuda.empty_cache()
         line["fullrow"] = fullrow_leg(args, ctx, torch)

@@ -207,11 +207,19 @@ typedef struct {
     float topk_prepare_ms;           /* sample threshold kernel */
     float topk_filter_ms;            /* streaming filter (-1: the plan had none) */
     float topk_select_ms;            /* cooperative select kernel */
-    float join_probe_ms;             /* probe kernel */
+    float join_probe_ms;             /* the whole probe: its one kernel, or the count, scatter and
+                                        probe kernels of the partitioned probe */
 } olap_kernel_ms;
 /* Times of the last timed Top-K and join probe on this context (waits for
  * them); -1 for a kernel that was not timed. */
 olap_status olap_kernel_ms_last(olap_ctx* ctx, olap_kernel_ms* out);
+
+/* Kernels this context has launched since it was created: every launch of
+ * the library's own kernels made for it (Top-K, join build and probe, copy
+ * kernels of pageable memory, full-row extraction and gather, tuning inputs),
+ * and each replay of a batch graph counted as the kernels inside it.  Copies
+ * and memsets are not kernels.  Host bookkeeping only. */
+olap_status olap_ctx_launches(const olap_ctx* ctx, uint64_t* count);
 
 /* ------------------------------------------------------------------------
  * Autotuner.  The paper fixes no kernel parameters; this picks them by

@@ -146,7 +146,9 @@ static olap_status direct_copy(olap_ctx* ctx, void* dst, const void* src, size_t
     else if (u == 2) direct_copy_kernel<uint16_t><<<grid, 256, 0, ctx->stream>>>(dp, sp, head, units, tail);
     else direct_copy_kernel<uint8_t><<<grid, 256, 0, ctx->stream>>>(dp, sp, head, units, tail);
     const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, what);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    ctx->launches += 1;
+    return OLAP_OK;
 }
 
 // Self-test of the bounded device waits: one thread waits, with the wait
@@ -273,6 +275,7 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
         cudaGetLastError();
         return cuda_fail(ctx, e, "Top-K launch");
     }
+    ctx->launches += plan.use_sample ? 3 : 2;           // prepare, [filter,] select
     if (ctl_out) *ctl_out = a.ctl;
     return OLAP_OK;
 }
@@ -406,6 +409,7 @@ olap_status olap_selftest_wait(olap_ctx* ctx, uint64_t limit_cycles, int32_t* ou
     if ((e = cudaMemsetAsync(word, 0, 64, ctx->stream)) != cudaSuccess) return cuda_fail(ctx, e, "self-test reset");
     wait_selftest_kernel<<<1, 32, 0, ctx->stream>>>(word, err, static_cast<long long>(limit_cycles));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "self-test launch");
+    ctx->launches += 1;
     if ((e = cudaMemcpyAsync(ctx->host_status, err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream)) !=
             cudaSuccess ||
         (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
@@ -459,6 +463,7 @@ olap_status olap_topk_rows(olap_ctx* ctx, const void* rows, olap_mem in_where, u
     if ((e = rows_extract(dr, n, row_bytes, key_offset, static_cast<int>(w), b + o_keys, grid, ctx->stream)) !=
         cudaSuccess)
         return cuda_fail(ctx, e, "key extraction");
+    ctx->launches += 1;
     TopkCtl* ctl = nullptr;
     uint32_t* drid = reinterpret_cast<uint32_t*>(b + o_rid);
     if ((st = topk_enqueue(ctx, b + o_keys, type, nullptr, n, kk, order, b + o_sel, drid, nullptr, ctx->stream,
@@ -466,6 +471,7 @@ olap_status olap_topk_rows(olap_ctx* ctx, const void* rows, olap_mem in_where, u
         return st;
     if ((e = rows_gather(dr, row_bytes, drid, kk, b + o_rows, grid, ctx->stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "row gather");
+    ctx->launches += 1;
     e = cudaMemcpyAsync(ctx->host_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
     if ((st = copy_d2h(ctx, out_rows, b + o_rows, kk * row_bytes, out_where)) != OLAP_OK) return st;
@@ -574,6 +580,12 @@ extern "C" olap_status olap_ctx_time_kernels(olap_ctx* ctx, int on) {
         if (e != cudaSuccess) return cuda_fail(ctx, e, "timing events");
     }
     ctx->time_kernels = on != 0;
+    return OLAP_OK;
+}
+
+extern "C" olap_status olap_ctx_launches(const olap_ctx* ctx, uint64_t* count) {
+    if (!ctx || !count) return OLAP_E_INVALID;
+    *count = ctx->launches;
     return OLAP_OK;
 }
 

@@ -490,6 +490,7 @@ struct olap_batch {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int digit = 12;                       // radix digit width of the per-CTA Top-K
+    int graph_kernels = 0;                // kernels in the captured graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -507,17 +508,23 @@ olap_status enqueue_batch(olap_batch* b, cudaStream_t s) {
             return cuda_fail(b->ctx, e, "batch fork");
         ps = b->side;
     }
+    b->graph_kernels = 0;
     if (b->n_probe) {
         const Item* probe_items = b->d_items + b->n_topk;
         batch_probe_reset_kernel<<<static_cast<unsigned>((b->n_probe + 255) / 256), 256, 0, ps>>>(
             probe_items, b->n_probe, b->d_errors);
-        if (b->n_chunks)
+        ++b->graph_kernels;
+        if (b->n_chunks) {
             batch_probe_kernel<<<b->grid_probe, JP_TPB, JP_SMEM, ps>>>(probe_items, b->d_chunks, b->n_chunks,
                                                                        b->d_next + 1);
+            ++b->graph_kernels;
+        }
     }
-    if (b->n_topk)
+    if (b->n_topk) {
         batch_topk_kernel<<<b->grid_topk, BT_TPB, BT_SMEM, s>>>(b->d_items, b->n_topk, b->d_next, b->cand_r,
                                                                 b->cand_rid, b->d_errors, b->digit);
+        ++b->graph_kernels;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(b->ctx, e, "batch launch");
     if (b->overlap &&
         ((e = cudaEventRecord(b->ev_join, b->side)) != cudaSuccess || (e = cudaStreamWaitEvent(s, b->ev_join, 0)) !=
@@ -696,7 +703,9 @@ olap_status olap_batch_run(olap_batch* b, void* stream) {
     if (!b) return OLAP_E_INVALID;
     cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : b->ctx->stream;
     cudaError_t e = cudaGraphLaunch(b->exec, s);
-    return e == cudaSuccess ? OLAP_OK : cuda_fail(b->ctx, e, "batch graph launch");
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "batch graph launch");
+    b->ctx->launches += static_cast<uint64_t>(b->graph_kernels);
+    return OLAP_OK;
 }
 
 olap_status olap_batch_run_per_query(olap_batch* b, void* stream) {

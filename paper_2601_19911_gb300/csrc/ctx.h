@@ -44,6 +44,10 @@ struct olap_ctx {
     // Control block of the last Top-K launched (diagnostics).
     void* last_topk_ctl = nullptr;
 
+    // Kernels launched for this context (a batch replay counts its graph's
+    // kernels).
+    uint64_t launches = 0;
+
     // Optional per-kernel timing: events around the kernels of the last Top-K
     // (4) and of the last join probe (2) launched while timing is on.
     bool time_kernels = false;

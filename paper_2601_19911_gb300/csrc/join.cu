@@ -363,6 +363,7 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
             join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(a);
     }
     e = cudaGetLastError();
+    if (e == cudaSuccess) ctx->launches += parts > 1 ? 3 : 1;    // [count, scatter,] probe
     if (e == cudaSuccess && ctx->time_kernels) e = cudaEventRecord(ctx->kev[5], s);
     return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "probe launch");
 }
@@ -444,6 +445,7 @@ olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* 
         join_build_kernel<<<grid, JB_TPB, 0, ctx->stream>>>(dk, dr, n, t->slots, buckets - 1, jc);
         e = cudaGetLastError();
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build launch"));
+        ctx->launches += 1;
     }
     JoinCtl hc;
     e = cudaMemcpyAsync(&hc, jc, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream);
@@ -458,6 +460,7 @@ olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* 
         }
         join_side_kernel<<<ctx->sm_count * 4, JB_TPB, 0, ctx->stream>>>(dk, dr, n, t->side, jc);
         e = cudaGetLastError();
+        if (e == cudaSuccess) ctx->launches += 1;
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) {
             cudaFree(t->side);

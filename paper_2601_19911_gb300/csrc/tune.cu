@@ -140,6 +140,7 @@ extern "C" olap_status olap_autotune(olap_ctx* ctx, const olap_tune_request* req
         }
         gen_topk_keys<<<ctx->sm_count * 4, 256, 0, s>>>(keys.p, n, w4 ? 1 : 0, req->seed);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "tuning input");
+        ctx->launches += 1;
         const olap_key_type kt = static_cast<olap_key_type>(req->topk_key_type);
         auto run = [&]() {
             return olap_topk_async(ctx, keys.p, kt, nullptr, n, kk, OLAP_DESC, ok.p, static_cast<uint32_t*>(orow.p),
@@ -195,6 +196,7 @@ extern "C" olap_status olap_autotune(olap_ctx* ctx, const olap_tune_request* req
         gen_join_keys<<<ctx->sm_count * 4, 256, 0, s>>>(static_cast<int64_t*>(bk.p), nb, static_cast<int64_t*>(pk.p),
                                                        np, req->join_hit_rate, req->seed + 16);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "tuning input");
+        ctx->launches += 1;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(ctx, e, "tuning input");
         const olap_opts saved = ctx->opts;
         double best = -1.0, t = 0.0;

@@ -31,7 +31,7 @@ EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
     "olap_ctx_host_direct", "olap_selftest_wait",
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last", "olap_topk_rows",
-    "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_autotune",
+    "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_ctx_launches", "olap_autotune",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_probe_partitions",
     "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
@@ -216,6 +216,8 @@ def load(path: str | None = None):
         lib.olap_ctx_time_kernels.argtypes = [vp, i32]
         lib.olap_kernel_ms_last.restype = i32
         lib.olap_kernel_ms_last.argtypes = [vp, ctypes.POINTER(olap_kernel_ms)]
+        lib.olap_ctx_launches.restype = i32
+        lib.olap_ctx_launches.argtypes = [vp, ctypes.POINTER(u64)]
         lib.olap_join_build.restype = i32
         lib.olap_join_build.argtypes = [vp, vp, vp, i32, u64, ctypes.c_double, ctypes.POINTER(vp)]
         lib.olap_join_probe.restype = i32
@@ -515,6 +517,12 @@ class Context:
     def time_kernels(self, on: bool = True):
         """olap_ctx_time_kernels: record CUDA events around each kernel."""
         self.check(self.lib.olap_ctx_time_kernels(self.h, 1 if on else 0))
+
+    def launches(self) -> int:
+        """olap_ctx_launches: kernels launched for this context so far."""
+        c = ctypes.c_uint64()
+        self.check(self.lib.olap_ctx_launches(self.h, ctypes.byref(c)))
+        return c.value
 
     def kernel_ms(self) -> dict:
         """olap_kernel_ms_last as a dict (milliseconds; -1 = not timed)."""

@@ -119,12 +119,6 @@ def test_median_p95():
     assert bench._median_p95([3.0]) == (3.0, 3.0)
 
 
-def test_topk_kernel_count():
-    assert bench._topk_kernels({"topk_prepare_ms": 0.01, "topk_filter_ms": 0.3, "topk_select_ms": 0.03}) == 3
-    assert bench._topk_kernels({"topk_prepare_ms": 0.01, "topk_select_ms": 0.03, "join_probe_ms": 4.0}) == 2
-    assert bench._topk_kernels({}) == 0
-
-
 def test_cpu_model_from_lscpu_then_cpuinfo():
     lscpu = "Architecture:  aarch64\nVendor ID:  ARM\nModel name:  Neoverse-V2\nCPU(s): 72\n"
     assert bench._parse_cpu_model(lscpu, "") == "Neoverse-V2"

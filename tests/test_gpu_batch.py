@@ -268,3 +268,58 @@ def test_full_size_batch_sampled():
         table.free()
     finally:
         c.close()
+
+
+def test_launch_counter_counts_every_kernel():
+    """olap_ctx_launches: the direct Top-K is two kernels (prepare, select),
+    the sampled one three (prepare, filter, select); a build without key -1
+    one; a direct probe one, a partitioned probe three; a batch replay the
+    kernels of its graph (probe reset, probe, Top-K); the per-query run the
+    sum of its calls.  A staged context launches no copy kernels."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0, host_access=olap.HOST_STAGED)
+    try:
+        def delta(fn):
+            c0 = c.launches()
+            fn()
+            c.sync()
+            return c.launches() - c0
+        small = torch.from_numpy(datagen.topk_keys(1 << 20, "uniform", "i64", seed=70)).cuda()
+        big = torch.from_numpy(datagen.topk_keys(1 << 22, "uniform", "i64", seed=71)).cuda()
+        ok = torch.empty(100, dtype=torch.int64, device="cuda")
+        orow = torch.empty(100, dtype=torch.int32, device="cuda")
+        assert delta(lambda: c.topk_async(small, 100, olap.DESC, ok, orow)) == 2
+        assert delta(lambda: c.topk_async(big, 100, olap.DESC, ok, orow)) == 3
+        assert delta(lambda: c.topk(small.cpu().numpy(), 100, olap.DESC)) == 2      # staged copies are not kernels
+        b = datagen.join_build(50_000, "unique", seed=72)
+        holder = []
+        assert delta(lambda: holder.append(c.join_build(torch.from_numpy(b.keys).cuda()))) == 1
+        t = holder[0]
+        p = datagen.join_probe(40_000, b, 0.5, "uniform", seed=72)
+        pk = torch.from_numpy(p.keys).cuda()
+        need = p.expected_pairs(b)
+        out = torch.empty((need, 2), dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        assert c.join_probe_partitions(t, 40_000) == 1
+        assert delta(lambda: c.join_probe_async(t, pk, out, need, cnt)) == 1
+        cnt2 = torch.zeros(2, dtype=torch.int64, device="cuda")
+        items = [olap.topk_item(small, 100, olap.DESC, ok, orow, cnt2[0:1]),
+                 olap.probe_item(t, pk, out, need, cnt2[1:2])]
+        bt = c.batch(items)
+        assert delta(bt.run) == 3
+        assert delta(bt.run_per_query) == 3
+        bt.free()
+        t.free()
+    finally:
+        c.close()
+    cp = olap.Context(0, join_partitions=4, host_access=olap.HOST_STAGED)
+    try:
+        t = cp.join_build(b.keys)
+        c0 = cp.launches()
+        got = cp.join_probe(t, p.keys)
+        assert cp.launches() - c0 == 3                          # count, scatter, probe
+        assert got.shape[0] == need
+        t.free()
+    finally:
+        cp.close()
