@@ -269,6 +269,22 @@ int probe_grid(int device) {
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// Grid of the two partition passes.  Both take the same one (the scatter
+// reads the count pass's per-CTA counts), at most JQ_CTAS_PER_SM per SM and no
+// more than the heavier scatter kernel keeps resident: every CTA owns a fixed
+// set of tiles, so CTAs beyond one wave would run their whole share late.
+int part_grid(int device, int sms) {
+    static int cached[64] = {};
+    if (device < 0 || device >= 64) return 0;
+    if (cached[device]) return cached[device];
+    int per_s = 0, per_c = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_s, join_part_scatter_kernel, JQ_TPB, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_c, join_part_count_kernel, JQ_TPB, 0) != cudaSuccess)
+        return 0;
+    cached[device] = sms * std::max(1, std::min(JQ_CTAS_PER_SM, std::min(per_s, per_c)));
+    return cached[device];
+}
+
 }  // namespace
 
 // Partitions the probe of `n` rows against `t` uses (1 = direct probe).
@@ -292,6 +308,7 @@ int probe_parts(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
 size_t probe_scratch_bytes(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
     const int parts = probe_parts(ctx, t, n);
     if (parts <= 1) return 0;
+    // room for the largest grid the partition passes can take
     const uint64_t grid = static_cast<uint64_t>(ctx->sm_count) * JQ_CTAS_PER_SM;
     return align256(n * 8) + align256(n * 4) + align256(grid * parts * 8) + align256((parts + 1) * 8);
 }
@@ -323,11 +340,13 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     a.count = reinterpret_cast<unsigned long long*>(d_count);
     const int parts = probe_parts(ctx, t, n);
     PartArgs q{};
+    unsigned qgrid = 0;
     if (parts > 1) {
         olap_status st = ensure_part(ctx, probe_scratch_bytes(ctx, t, n));
         if (st != OLAP_OK) return st;
         unsigned char* m = static_cast<unsigned char*>(ctx->part);
-        const uint64_t qgrid = static_cast<uint64_t>(ctx->sm_count) * JQ_CTAS_PER_SM;
+        qgrid = static_cast<unsigned>(part_grid(ctx->device, ctx->sm_count));
+        if (qgrid == 0) return fail(ctx, OLAP_E_CUDA, "partition kernel occupancy query failed");
         q.keys = d_keys;
         q.rowids = d_rowids;
         q.n = n;
@@ -338,7 +357,7 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
         q.out_keys = reinterpret_cast<int64_t*>(m);
         q.out_rowids = reinterpret_cast<uint32_t*>(m + align256(n * 8));
         q.cnt = reinterpret_cast<unsigned long long*>(m + align256(n * 8) + align256(n * 4));
-        q.pstart = q.cnt + qgrid * parts;
+        q.pstart = q.cnt + static_cast<uint64_t>(qgrid) * parts;
         if (q.pstart + parts + 1 > reinterpret_cast<unsigned long long*>(m + ctx->part_bytes))
             return fail(ctx, OLAP_E_INVALID, "probe partition scratch too small");
     }
@@ -346,7 +365,6 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     if (ctx->time_kernels && (e = cudaEventRecord(ctx->kev[4], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "timing event");
     if (parts > 1) {
-        const unsigned qgrid = static_cast<unsigned>(ctx->sm_count * JQ_CTAS_PER_SM);
         join_part_count_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
         join_part_scatter_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
         ProbeArgs pa = a;
