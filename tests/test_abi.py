@@ -110,3 +110,23 @@ def test_binding_rejects_bad_buffers_without_asserts():
     with pytest.raises(ValueError):
         olap.gate_calibrate(olap.OP_TOPK, [1e3, 1e4], [10, 10], [8e3, 8e4], [10, 10], [1.0, 2.0],
                             [0.1, 0.2], [0.1, 0.1], [0.01])
+
+
+def test_noalloc_refuses_bad_arguments_before_any_device_call():
+    """olap_topk_noalloc checks every argument before it touches the device,
+    so the refusals hold without a GPU; the addresses below are never read."""
+    lib = olap.load()
+    fake, odd = 0x10000, 0x10004                     # 16- and 4-byte aligned placeholders
+    call = lambda keys, kt, n, k, order, ok=fake, orow=fake: lib.olap_topk_noalloc(
+        keys, kt, None, n, k, order, ok, orow, None, None)
+    assert call(fake, 9, 100, 10, olap.DESC) == olap.E_INVALID                   # no such key type
+    assert call(fake, olap.KEY_I64, 100, 10, 7) == olap.E_INVALID               # no such order
+    assert call(fake, olap.KEY_I64, olap.NOALLOC_MAX_N + 1, 10, olap.DESC) == olap.E_INVALID
+    assert call(fake, olap.KEY_I64, 100, olap.NOALLOC_MAX_K + 1, olap.DESC) == olap.E_INVALID
+    assert call(None, olap.KEY_I64, 100, 10, olap.DESC) == olap.E_INVALID       # keys missing
+    assert call(fake, olap.KEY_I64, 100, 10, olap.DESC, ok=None) == olap.E_INVALID
+    assert call(odd, olap.KEY_I64, 100, 10, olap.DESC) == olap.E_INVALID        # int64 keys 4-byte aligned
+    assert call(odd + 1, olap.KEY_F32, 100, 10, olap.DESC) == olap.E_INVALID    # float32 keys misaligned
+    # nothing to select and no status word: done without the device
+    assert call(fake, olap.KEY_I64, 0, 10, olap.DESC) == olap.OK
+    assert call(fake, olap.KEY_I64, 100, 0, olap.DESC, ok=None, orow=None) == olap.OK
