@@ -555,15 +555,24 @@ olap_status olap_serve(olap_serve_request* reqs, uint64_t n, const olap_serve_op
  * cudaFree may cause).
  *
  * Same arguments and result as olap_topk_async, but without a context: the
- * working memory is a fixed array of about 2 MiB built into the library,
- * resident on every GPU the library is loaded on until the process exits.
- * The call makes no cudaMalloc/cudaFree and no other allocation.
- *   - Limits: n <= OLAP_NOALLOC_MAX_N and k <= OLAP_NOALLOC_MAX_K; larger
- *     sizes return OLAP_E_INVALID before anything is launched.
+ * working memory is a fixed 2 MiB array built into the library, which stays
+ * on every GPU that has loaded it until the process exits.  Apart from the
+ * first call on a device (below), a call makes no cudaMalloc/cudaFree and no
+ * other allocation.
+ *   - Limits: n <= OLAP_NOALLOC_MAX_N and k <= OLAP_NOALLOC_MAX_K.
+ *   - OLAP_E_INVALID, returned before anything is launched, means one of:
+ *     n or k above those limits; an unknown key type or order; d_keys NULL
+ *     with n > 0; an output pointer NULL with min(k, n) > 0; d_keys not
+ *     aligned to its key width.  OLAP_E_CUDA means a CUDA call failed (no
+ *     current device, the set-up below, or the launch).
  *   - Runs on the current CUDA device, on `stream` (NULL = legacy default).
- *   - The first call on a device looks up the array's device address with
- *     that device current (one-time set-up); make that first call before any
- *     stream capture.
+ *   - The first call on a device does a one-time set-up with that device
+ *     current: it looks up the array's device address, which makes CUDA load
+ *     the array's code module on that device if it is not loaded yet (lazy
+ *     module loading is CUDA's default).  That load takes the array's 2 MiB of
+ *     device memory and may synchronise the device, so make the first call on
+ *     each device during start-up, before any stream capture; later calls
+ *     allocate nothing.
  *   - All calls on a device share the one array and it keeps the previous
  *     call's contents (the library clears what must start at zero).  Calls
  *     whose work overlaps on the GPU race on it: order them on one stream.

@@ -9,23 +9,31 @@
 // with all bits set; build rows carrying that key value live in a side list.
 // Hash: the 64-bit finalizer of MurmurHash3 (fmix64, A. Appleby).
 //
-// Probe: the rows are split evenly over all warps of the grid.  Each lane
-// runs two independent probe streams and walks their chains one bucket per
-// step; a stream whose chain ends starts its next row at once (its key is
-// already loaded), so lanes do not wait for the longest chain of the warp.
-// Matches are staged per warp in shared memory and appended to the output
-// with one atomic on the global count per flush.
+// Build: one CAS pass, then a pass that records in every occupied slot how
+// many further copies of its key follow it along the chain, so a probe can
+// stop at a key's last copy instead of walking on to the chain's end.
+//
+// Probe: every warp takes chunks of consecutive rows from a global counter
+// and hands them to its lanes in order (the loads of keys and row-ids
+// coalesce; no lane waits at a partition or range boundary).  Each lane runs
+// two independent probe streams and walks their chains one bucket per step; a
+// stream whose chain ends starts its next row at once (its key is already
+// loaded), so lanes do not wait for the longest chain of the warp.  Matches
+// are staged per warp in shared memory and appended to the output with one
+// atomic on the global count per flush.
 //
 // Partitioned probe (table much larger than L2, many probe rows): a table
-// larger than L2 turns every probe into a random DRAM sector read.  Instead
-// the probe rows are first radix-partitioned by the top bits of their home
-// bucket into P partitions (a counting pass and a scatter pass, both
-// streaming, with the same CTA-to-tile assignment so every CTA's output
-// ranges come from the count matrix without global atomics), then all CTAs
-// probe partition 0, then 1, ...: the buckets a partition can touch are one
-// 1/P slice of the table, sized to stay resident in L2, so the table is read
-// from DRAM about once.
+// larger than L2 turns every probe into a random DRAM sector read, and those
+// run at a small fraction of the streaming rate.  Instead the probe rows are
+// first radix-partitioned by the top bits of their home bucket into P
+// partitions (a counting pass and a scatter pass, both streaming, with the
+// same CTA-to-tile assignment so every CTA's output ranges come from the
+// count matrix without global atomics).  The probe then takes the reordered
+// rows chunk by chunk in partition order, so the whole grid works on one
+// 1/P slice of the table at a time, sized to stay resident in L2: the table
+// is read from DRAM about once.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 
@@ -65,6 +73,33 @@ __global__ void __launch_bounds__(JB_TPB) join_build_kernel(const int64_t* keys,
     }
 }
 
+// After the build: every occupied slot records, in the high half of its
+// row-id word, how many further copies of its key follow it along the chain
+// (up to the first bucket with a free slot, where every chain through it
+// ends).  Copies of a key all sit between its home bucket and that end, in
+// the order a probe walks them, so a probe that meets a copy with no further
+// copies has seen them all and stops there instead of walking to the chain's
+// end: for a unique build a hit stops at its key.
+__global__ void __launch_bounds__(JB_TPB) join_chain_kernel(ulonglong2* slots, uint64_t mask) {
+    const uint64_t n_slots = (mask + 1) * 2;
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * JB_TPB;
+    for (uint64_t j = static_cast<uint64_t>(blockIdx.x) * JB_TPB + threadIdx.x; j < n_slots; j += stride) {
+        const uint64_t key = slots[j].x;
+        if (key == JN_EMPTY) continue;
+        uint64_t b = j >> 1;
+        uint32_t further = 0;
+        uint64_t k1 = slots[b * 2 + 1].x;
+        if ((j & 1) == 0 && k1 == key) ++further;
+        for (uint64_t step = 0; k1 != JN_EMPTY && step < mask; ++step) {   // bucket b full: the chain goes on
+            b = (b + 1) & mask;
+            const uint64_t k0 = slots[b * 2].x;
+            k1 = slots[b * 2 + 1].x;
+            further += (k0 == key) + (k1 == key);
+        }
+        slots[j].y = (slots[j].y & 0xFFFFFFFFull) | (static_cast<uint64_t>(further) << 32);
+    }
+}
+
 __global__ void __launch_bounds__(JB_TPB) join_side_kernel(const int64_t* keys, const uint32_t* rowids,
                                                            uint64_t n, uint32_t* side, JoinCtl* ctl) {
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * JB_TPB;
@@ -76,14 +111,19 @@ __global__ void __launch_bounds__(JB_TPB) join_side_kernel(const int64_t* keys, 
     }
 }
 
+// The probe: rows [0, a.n) handed out in chunks by a row queue (see
+// probe_queue).  Used on the input (direct probe) and on the rows reordered
+// by partition (pass 3 of the partitioned probe): there the chunks come out in
+// partition order, so the warps of the whole grid work on one partition's
+// table slice at a time and that slice stays in L2.
 template <bool L2_ONLY>
-__global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs a) {
+__global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs a, unsigned long long* next_row) {
     extern __shared__ __align__(16) uint2 stage[];
     const unsigned warp = threadIdx.x >> 5;
-    uint64_t b, e;
-    warp_share(0, a.n, static_cast<uint64_t>(blockIdx.x) * JP_WARPS + warp,
-               static_cast<uint64_t>(gridDim.x) * JP_WARPS, &b, &e);
-    probe_warp<L2_ONLY>(a, b, e, stage + warp * JP_WCAP);
+    RowQueue q;
+    q.counter = next_row;
+    q.n = a.n;
+    probe_queue<L2_ONLY>(a, q, stage + warp * JP_WCAP);
 }
 
 // ---- partitioned probe ------------------------------------------------------
@@ -202,7 +242,7 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
                 const unsigned q = pr[j] & 0xFFu;
                 const unsigned pos = off[q] + (pr[j] >> 8);
                 sk[pos] = static_cast<int64_t>(kc[j]);
-                sr[pos] = a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx);
+                sr[pos] = a.rowids ? ld_stream_u32(a.rowids + idx) : static_cast<uint32_t>(idx);
                 sp[pos] = static_cast<uint8_t>(q);
             }
         }
@@ -218,22 +258,6 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
         if (p < a.parts) base[p] += hv;
 #pragma unroll
         for (int j = 0; j < JQ_PER; ++j) kc[j] = kn[j];
-    }
-}
-
-// Pass 3: all CTAs probe partition 0, then 1, ...  `a` points at the
-// partitioned keys and row-ids; partition q is rows [pstart[q], pstart[q+1]).
-template <bool L2_ONLY>
-__global__ void __launch_bounds__(JP_TPB, 4) join_probe_part_kernel(ProbeArgs a, const unsigned long long* pstart,
-                                                                    int parts) {
-    extern __shared__ __align__(16) uint2 stage[];
-    const unsigned warp = threadIdx.x >> 5;
-    const uint64_t w = static_cast<uint64_t>(blockIdx.x) * JP_WARPS + warp;
-    const uint64_t warps = static_cast<uint64_t>(gridDim.x) * JP_WARPS;
-    for (int q = 0; q < parts; ++q) {
-        uint64_t b, e;
-        warp_share(__ldcg(pstart + q), __ldcg(pstart + q + 1), w, warps, &b, &e);
-        probe_warp<L2_ONLY>(a, b, e, stage + warp * JP_WCAP);
     }
 }
 
@@ -254,17 +278,15 @@ bool probe_kernel_setup(K kernel, int* per_sm) {
 }
 
 int probe_grid(int device) {
-    static int cached[64] = {};
+    static std::atomic<int> cached[64] = {};
     if (device < 0 || device >= 64) return 0;
-    if (cached[device]) return cached[device];
+    if (const int c = cached[device].load()) return c;
     int sms = 0, per = 1 << 20;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-    if (!probe_kernel_setup(join_probe_kernel<false>, &per) || !probe_kernel_setup(join_probe_kernel<true>, &per) ||
-        !probe_kernel_setup(join_probe_part_kernel<false>, &per) ||
-        !probe_kernel_setup(join_probe_part_kernel<true>, &per))
+    if (!probe_kernel_setup(join_probe_kernel<false>, &per) || !probe_kernel_setup(join_probe_kernel<true>, &per))
         return 0;
-    cached[device] = sms * std::max(1, per);
-    return cached[device];
+    cached[device].store(sms * std::max(1, per));
+    return cached[device].load();
 }
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -274,15 +296,15 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 // more than the heavier scatter kernel keeps resident: every CTA owns a fixed
 // set of tiles, so CTAs beyond one wave would run their whole share late.
 int part_grid(int device, int sms) {
-    static int cached[64] = {};
+    static std::atomic<int> cached[64] = {};
     if (device < 0 || device >= 64) return 0;
-    if (cached[device]) return cached[device];
+    if (const int c = cached[device].load()) return c;
     int per_s = 0, per_c = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_s, join_part_scatter_kernel, JQ_TPB, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_c, join_part_count_kernel, JQ_TPB, 0) != cudaSuccess)
         return 0;
-    cached[device] = sms * std::max(1, std::min(JQ_CTAS_PER_SM, std::min(per_s, per_c)));
-    return cached[device];
+    cached[device].store(sms * std::max(1, std::min(JQ_CTAS_PER_SM, std::min(per_s, per_c))));
+    return cached[device].load();
 }
 
 }  // namespace
@@ -364,22 +386,21 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     ctx->probe_timed = ctx->time_kernels;
     if (ctx->time_kernels && (e = cudaEventRecord(ctx->kev[4], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "timing event");
+    // the row queue's counter, in the context's small device area
+    unsigned long long* next_row = reinterpret_cast<unsigned long long*>(static_cast<unsigned char*>(ctx->aux) + 256);
+    if ((e = cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+        return cuda_fail(ctx, e, "probe queue reset");
+    ProbeArgs pa = a;
     if (parts > 1) {
         join_part_count_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
         join_part_scatter_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
-        ProbeArgs pa = a;
         pa.keys = q.out_keys;
         pa.rowids = q.out_rowids;
-        if (ctx->opts.join_bucket_loads == OLAP_LOADS_L1)
-            join_probe_part_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(pa, q.pstart, parts);
-        else
-            join_probe_part_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(pa, q.pstart, parts);
-    } else {
-        if (ctx->opts.join_bucket_loads == OLAP_LOADS_L1)
-            join_probe_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(a);
-        else
-            join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(a);
     }
+    if (ctx->opts.join_bucket_loads == OLAP_LOADS_L1)
+        join_probe_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row);
+    else
+        join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row);
     e = cudaGetLastError();
     if (e == cudaSuccess) ctx->launches += parts > 1 ? 3 : 1;    // [count, scatter,] probe
     if (e == cudaSuccess && ctx->time_kernels) e = cudaEventRecord(ctx->kev[5], s);
@@ -463,7 +484,10 @@ olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* 
         join_build_kernel<<<grid, JB_TPB, 0, ctx->stream>>>(dk, dr, n, t->slots, buckets - 1, jc);
         e = cudaGetLastError();
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build launch"));
-        ctx->launches += 1;
+        join_chain_kernel<<<grid, JB_TPB, 0, ctx->stream>>>(t->slots, buckets - 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build launch"));
+        ctx->launches += 2;
     }
     JoinCtl hc;
     e = cudaMemcpyAsync(&hc, jc, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream);

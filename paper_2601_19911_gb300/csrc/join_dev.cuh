@@ -43,10 +43,21 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t h) {
     return h;
 }
 
+// Streaming probe-side traffic (keys, row-ids, pairs) is read or written
+// once: the .cs forms allocate its L2 lines evict-first, so the table's lines
+// are what L2 keeps.
 __device__ __forceinline__ uint64_t ld_stream_u64(const void* p) {
     uint64_t v;
     asm volatile("ld.global.cs.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u32(const void* p) {
+    uint32_t v;
+    asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_stream_pair(uint2* p, uint2 v) {
+    asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(v.x), "r"(v.y) : "memory");
 }
 
 struct ProbeArgs {
@@ -66,7 +77,7 @@ struct ProbeArgs {
 // 256-bit load; L2_ONLY bypasses L1 (ld.global.cg), else the read-only path
 // through L1 (ld.global.nc).
 struct Bucket {
-    uint64_t k0, w0, k1, w1;          // w: row-id in the low 32 bits
+    uint64_t k0, w0, k1, w1;          // w: row-id in the low 32 bits, further copies in the high 32
 };
 
 template <bool L2_ONLY>
@@ -94,7 +105,7 @@ __device__ __forceinline__ void warp_flush(const ProbeArgs& a, uint2* ws, unsign
     if (lane == 0) g = atomicAdd(a.count, static_cast<unsigned long long>(cnt));
     g = __shfl_sync(0xFFFFFFFFu, g, 0);
     for (unsigned i = lane; i < cnt; i += 32)
-        if (g + i < a.cap) a.out[g + i] = ws[i];
+        if (g + i < a.cap) st_stream_pair(a.out + g + i, ws[i]);
     __syncwarp();
     cnt = 0;
 }
@@ -132,11 +143,11 @@ __device__ __forceinline__ void probe_warp(const ProbeArgs& a, uint64_t begin, u
         const uint64_t i = begin + lane + 32ull * s;
         live[s] = i < end;
         key[s] = live[s] ? ld_stream_u64(a.keys + i) : JN_EMPTY;
-        rid[s] = live[s] ? (a.rowids ? a.rowids[i] : static_cast<uint32_t>(i)) : 0u;
+        rid[s] = live[s] ? (a.rowids ? ld_stream_u32(a.rowids + i) : static_cast<uint32_t>(i)) : 0u;
         nxt[s] = i + STEP;
         plive[s] = nxt[s] < end;
         pkey[s] = plive[s] ? ld_stream_u64(a.keys + nxt[s]) : JN_EMPTY;
-        prid[s] = plive[s] ? (a.rowids ? a.rowids[nxt[s]] : static_cast<uint32_t>(nxt[s])) : 0u;
+        prid[s] = plive[s] ? (a.rowids ? ld_stream_u32(a.rowids + nxt[s]) : static_cast<uint32_t>(nxt[s])) : 0u;
     }
 #pragma unroll
     for (int s = 0; s < JP_S; ++s) {
@@ -166,18 +177,23 @@ __device__ __forceinline__ void probe_warp(const ProbeArgs& a, uint64_t begin, u
                 }
             }
         }
-        // Matches in the current bucket of every stream.
+        // Matches in the current bucket of every stream.  A match whose slot
+        // counts no further copies of its key is the chain's last copy: the
+        // stream's walk for this row ends there.
+        bool last[JP_S];
 #pragma unroll
         for (int s = 0; s < JP_S; ++s) {
             const bool real = live[s] && key[s] != JN_EMPTY;
-            warp_put(a, ws, cnt, real && v[s].k0 == key[s], make_uint2(rid[s], static_cast<uint32_t>(v[s].w0)));
-            warp_put(a, ws, cnt, real && v[s].k1 == key[s], make_uint2(rid[s], static_cast<uint32_t>(v[s].w1)));
+            const bool m0 = real && v[s].k0 == key[s], m1 = real && v[s].k1 == key[s];
+            warp_put(a, ws, cnt, m0, make_uint2(rid[s], static_cast<uint32_t>(v[s].w0)));
+            warp_put(a, ws, cnt, m1, make_uint2(rid[s], static_cast<uint32_t>(v[s].w1)));
+            last[s] = (m0 && (v[s].w0 >> 32) == 0) || (m1 && (v[s].w1 >> 32) == 0);
         }
         // Next bucket of the chain, or the stream's next row.
 #pragma unroll
         for (int s = 0; s < JP_S; ++s) {
             if (!live[s]) continue;
-            if (key[s] != JN_EMPTY && v[s].k0 != JN_EMPTY && v[s].k1 != JN_EMPTY) {
+            if (key[s] != JN_EMPTY && !last[s] && v[s].k0 != JN_EMPTY && v[s].k1 != JN_EMPTY) {
                 bk[s] = (bk[s] + 1u) & mask;
             } else {
                 live[s] = plive[s];
@@ -189,7 +205,7 @@ __device__ __forceinline__ void probe_warp(const ProbeArgs& a, uint64_t begin, u
                 plive[s] = nxt[s] < end;
                 if (plive[s]) {
                     pkey[s] = ld_stream_u64(a.keys + nxt[s]);
-                    prid[s] = a.rowids ? a.rowids[nxt[s]] : static_cast<uint32_t>(nxt[s]);
+                    prid[s] = a.rowids ? ld_stream_u32(a.rowids + nxt[s]) : static_cast<uint32_t>(nxt[s]);
                 }
                 if (key[s] == JN_EMPTY) {
                     v[s] = Bucket{JN_EMPTY, 0, JN_EMPTY, 0};
@@ -197,6 +213,151 @@ __device__ __forceinline__ void probe_warp(const ProbeArgs& a, uint64_t begin, u
                 }
             }
             v[s] = ld_bucket<L2_ONLY>(a.slots, bk[s]);
+        }
+    }
+    warp_flush(a, ws, cnt);
+}
+
+// Rows handed to the lanes of one warp.  The warp takes chunks of JQ_CHUNK
+// consecutive rows from a global counter and gives them out in order, the
+// lanes that need a row in one step getting consecutive rows, so the loads of
+// their keys and row-ids coalesce.  Every field is warp-uniform: `cur` is the
+// chunk being handed out, `nxt` the one taken after it (empty: b == e).
+constexpr uint64_t JQ_CHUNK = 512;
+
+struct RowRange {
+    uint64_t b, e;
+};
+
+struct RowQueue {
+    RowRange cur, nxt;
+    unsigned long long* counter;  // next unclaimed row (zeroed before the launch)
+    uint64_t n;
+};
+
+__device__ __forceinline__ RowRange take_chunk(RowQueue& q) {
+    unsigned long long g = 0;
+    if ((threadIdx.x & 31u) == 0) g = atomicAdd(q.counter, static_cast<unsigned long long>(JQ_CHUNK));
+    g = __shfl_sync(0xFFFFFFFFu, g, 0);
+    return RowRange{min(static_cast<uint64_t>(g), q.n), min(static_cast<uint64_t>(g) + JQ_CHUNK, q.n)};
+}
+
+// The next row of every lane in `need` (a ballot; whole warp calls): row
+// index, or false when the rows are exhausted.
+__device__ __forceinline__ bool queue_next(RowQueue& q, unsigned need, uint64_t* row) {
+    const unsigned c = __popc(need);
+    if (c == 0) return false;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned r = __popc(need & ((1u << lane) - 1u));
+    uint64_t avail = q.cur.e - q.cur.b;
+    if (avail < c && q.nxt.b == q.nxt.e) q.nxt = take_chunk(q);
+    bool ok;
+    if (r < avail) {
+        *row = q.cur.b + r;
+        ok = true;
+    } else {
+        *row = q.nxt.b + (r - avail);
+        ok = *row < q.nxt.e;
+    }
+    if (c <= avail) {
+        q.cur.b += c;
+    } else {
+        const uint64_t used = min(static_cast<uint64_t>(c) - avail, q.nxt.e - q.nxt.b);
+        q.cur = RowRange{q.nxt.b + used, q.nxt.e};
+        q.nxt = RowRange{0, 0};
+    }
+    return ok && ((need >> lane) & 1u);
+}
+
+// One warp probes rows from the queue until the rows run out.  Each lane runs
+// JP_S independent streams.  A stream walks its row's chain one bucket per
+// step and, when the chain ends, switches at once to the row it has already
+// loaded and asks the queue for the next one.  Matches go to the warp's own
+// stage `ws`, flushed to the output whenever it could overflow and at the end.
+template <bool L2_ONLY>
+__device__ __forceinline__ void probe_queue(const ProbeArgs& a, RowQueue& q, uint2* ws) {
+    const unsigned lane = threadIdx.x & 31u;
+    const uint32_t mask = static_cast<uint32_t>(a.mask);
+    unsigned cnt = 0;
+    uint64_t key[JP_S], pkey[JP_S];
+    uint32_t rid[JP_S], prid[JP_S], bk[JP_S];
+    bool live[JP_S], plive[JP_S];
+    Bucket v[JP_S];
+    q.cur = take_chunk(q);
+    q.nxt = RowRange{0, 0};
+    // current rows, then the rows loaded ahead
+#pragma unroll
+    for (int s = 0; s < JP_S; ++s) {
+        uint64_t i = 0;
+        live[s] = queue_next(q, 0xFFFFFFFFu, &i);
+        key[s] = live[s] ? ld_stream_u64(a.keys + i) : JN_EMPTY;
+        rid[s] = live[s] ? (a.rowids ? ld_stream_u32(a.rowids + i) : static_cast<uint32_t>(i)) : 0u;
+    }
+#pragma unroll
+    for (int s = 0; s < JP_S; ++s) {
+        uint64_t i = 0;
+        plive[s] = queue_next(q, 0xFFFFFFFFu, &i);
+        pkey[s] = plive[s] ? ld_stream_u64(a.keys + i) : JN_EMPTY;
+        prid[s] = plive[s] ? (a.rowids ? ld_stream_u32(a.rowids + i) : static_cast<uint32_t>(i)) : 0u;
+    }
+#pragma unroll
+    for (int s = 0; s < JP_S; ++s) {
+        bk[s] = static_cast<uint32_t>(fmix64(key[s])) & mask;
+        v[s] = (live[s] && key[s] != JN_EMPTY) ? ld_bucket<L2_ONLY>(a.slots, bk[s]) : Bucket{JN_EMPTY, 0, JN_EMPTY, 0};
+    }
+    while (true) {
+        bool any = false;
+#pragma unroll
+        for (int s = 0; s < JP_S; ++s) any = any || live[s];
+        if (!__any_sync(0xFFFFFFFFu, any)) break;
+        // Probe keys equal to the empty marker pair with every side-list row;
+        // the warp emits them together, one such key at a time (rare).
+#pragma unroll
+        for (int s = 0; s < JP_S; ++s) {
+            unsigned sb = __ballot_sync(0xFFFFFFFFu, live[s] && key[s] == JN_EMPTY);
+            while (sb) {
+                const int src = __ffs(sb) - 1;
+                sb &= sb - 1;
+                const uint32_t r = __shfl_sync(0xFFFFFFFFu, rid[s], src);
+                for (uint64_t o0 = 0; o0 < a.n_side; o0 += 32) {
+                    const bool m = o0 + lane < a.n_side;
+                    warp_put(a, ws, cnt, m, make_uint2(r, m ? a.side[o0 + lane] : 0u));
+                }
+            }
+        }
+        // Matches in the current bucket of every stream; a match whose slot
+        // counts no further copies of its key ends the row's walk.
+        bool go[JP_S];
+#pragma unroll
+        for (int s = 0; s < JP_S; ++s) {
+            const bool real = live[s] && key[s] != JN_EMPTY;
+            const bool m0 = real && v[s].k0 == key[s], m1 = real && v[s].k1 == key[s];
+            warp_put(a, ws, cnt, m0, make_uint2(rid[s], static_cast<uint32_t>(v[s].w0)));
+            warp_put(a, ws, cnt, m1, make_uint2(rid[s], static_cast<uint32_t>(v[s].w1)));
+            const bool last = (m0 && (v[s].w0 >> 32) == 0) || (m1 && (v[s].w1 >> 32) == 0);
+            go[s] = real && !last && v[s].k1 != JN_EMPTY;     // slot 1 taken: the bucket is full
+        }
+        // Each stream steps along its chain, or takes the row it loaded ahead
+        // and loads the queue's next row in its place.
+#pragma unroll
+        for (int s = 0; s < JP_S; ++s) {
+            const bool swap = live[s] && !go[s];
+            uint64_t i = 0;
+            const bool got = queue_next(q, __ballot_sync(0xFFFFFFFFu, swap && plive[s]), &i);
+            if (go[s]) {
+                bk[s] = (bk[s] + 1u) & mask;
+            } else if (swap) {
+                live[s] = plive[s];
+                key[s] = pkey[s];
+                rid[s] = prid[s];
+                bk[s] = static_cast<uint32_t>(fmix64(key[s])) & mask;
+                plive[s] = got;
+                if (got) {
+                    pkey[s] = ld_stream_u64(a.keys + i);
+                    prid[s] = a.rowids ? ld_stream_u32(a.rowids + i) : static_cast<uint32_t>(i);
+                }
+            }
+            if (live[s] && key[s] != JN_EMPTY) v[s] = ld_bucket<L2_ONLY>(a.slots, bk[s]);
         }
     }
     warp_flush(a, ws, cnt);

@@ -10,10 +10,13 @@
 // file, so the call itself allocates nothing.  The caller still provides the
 // input and output buffers.
 //
-// The array below lives in every GPU's memory once this library is loaded on
-// it and stays there until the process exits.  Its address is looked up once
-// per device (cudaGetSymbolAddress, with that device current) on the first
-// call made on that device; make that first call before any stream capture.
+// The array below lives in the memory of every GPU that has loaded this
+// file's code module and stays there until the process exits.  Its address is
+// looked up once per device (cudaGetSymbolAddress, with that device current)
+// on the first call made on that device.  With lazy module loading (CUDA's
+// default) that lookup is also what loads the module, so the first call on a
+// device takes the array's 2 MiB of device memory and may synchronise; make
+// it during start-up, before any stream capture.  Later calls allocate nothing.
 // All calls on one device share the array and it keeps the previous call's
 // contents: the grid barrier at its start is cleared before every launch, and
 // the kernel clears its own counters and histograms.  Calls whose work

@@ -29,7 +29,9 @@
 //      K <= 4096, else tile sorts plus merge-path rounds across the grid --
 //      and write keys (original bits, by the inverse transform) and row-ids.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "block.cuh"
 #include "topk.cuh"
@@ -995,10 +997,15 @@ void topk_carve(TopkArgs& a, const TopkPlan& p, void* base) {
     a.filter = TK_FILTER_BULK;
 }
 
-static int g_smem_limit[64] = {};   // dynamic shared bytes the filter kernel may use, per device
+// Dynamic shared bytes the filter kernel may use, per device; set once, under
+// g_attr_lock, by the first thread that needs the kernels' attributes there.
+static std::atomic<int> g_smem_limit[64] = {};
+static std::mutex g_attr_lock;
 
 static bool set_kernel_attrs(int device) {
-    if (g_smem_limit[device]) return true;
+    if (g_smem_limit[device].load()) return true;
+    std::lock_guard<std::mutex> guard(g_attr_lock);
+    if (g_smem_limit[device].load()) return true;
     // Opt-in limit per block, less the filter kernel's static shared memory.
     int optin = 0;
     cudaFuncAttributes fa;
@@ -1017,7 +1024,7 @@ static bool set_kernel_attrs(int device) {
         cudaFuncSetAttribute(topk_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TK_SORT_SMEM) != cudaSuccess)
         return false;
-    g_smem_limit[device] = lim;
+    g_smem_limit[device].store(lim);
     return true;
 }
 
@@ -1036,7 +1043,7 @@ bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, int 
     int sms = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return false;
     if (!set_kernel_attrs(device)) return false;
-    if (g.smem_bytes > g_smem_limit[device]) return false;
+    if (g.smem_bytes > g_smem_limit[device].load()) return false;
     // Streaming filter: independent CTAs, capped at ctas_per_sm per SM.
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, topk_filter_bulk_kernel<false>, TKF_TPB,
                                                       g.smem_bytes) != cudaSuccess)

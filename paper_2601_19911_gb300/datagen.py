@@ -54,6 +54,37 @@ def _threads() -> int:
     return max(1, min(16, os.cpu_count() or 1))
 
 
+def _par_chunks(count: int, fn) -> None:
+    """Call ``fn(a, b)`` over [0, count) in chunks, on a thread pool for large
+    counts (numpy's searches and gathers release the interpreter lock)."""
+    count = int(count)
+    if count <= _CHUNK:
+        if count:
+            fn(0, count)
+        return
+    spans = [(a, min(a + _CHUNK, count)) for a in range(0, count, _CHUNK)]
+    with _cf.ThreadPoolExecutor(_threads()) as ex:
+        list(ex.map(lambda ab: fn(*ab), spans))
+
+
+def _searchsorted(sorted_a: np.ndarray, v: np.ndarray, side: str = "left") -> np.ndarray:
+    out = np.empty(v.shape[0], dtype=np.int64)
+
+    def part(a, b):
+        out[a:b] = np.searchsorted(sorted_a, v[a:b], side=side)
+    _par_chunks(v.shape[0], part)
+    return out
+
+
+def _take(src: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    out = np.empty(idx.shape[0], dtype=src.dtype)
+
+    def part(a, b):
+        out[a:b] = src[idx[a:b]]
+    _par_chunks(idx.shape[0], part)
+    return out
+
+
 def splitmix64(seed: int, count: int, start: int = 0) -> np.ndarray:
     """``count`` uint64 draws x_start .. x_{start+count-1} of stream ``seed``."""
     out = np.empty(int(count), dtype=np.uint64)
@@ -95,7 +126,14 @@ def splitmix64_torch(seed: int, count: int, start: int = 0, device="cuda", chunk
 
 def unit_f64(seed: int, count: int, start: int = 0) -> np.ndarray:
     """Uniform doubles in [0, 1) from the top 53 bits of each draw."""
-    return (splitmix64(seed, count, start) >> _U64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    out = np.empty(int(count), dtype=np.float64)
+
+    def part(a, b):
+        raw = np.empty(b - a, dtype=np.uint64)
+        _fill(raw, seed, start + a)
+        out[a:b] = (raw >> _U64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    _par_chunks(count, part)
+    return out
 
 
 def log_uniform(lo: float, hi: float, seed: int, count: int) -> np.ndarray:
@@ -251,7 +289,7 @@ def _zipf_ranks(u: np.ndarray, d: int, s: float) -> np.ndarray:
     w = np.power(np.arange(1, d + 1, dtype=np.float64), -s)
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
-    r = np.searchsorted(cdf, u, side="right")
+    r = _searchsorted(cdf, u, side="right")
     return np.minimum(r, d - 1)
 
 
@@ -278,21 +316,25 @@ def join_probe(n: int, build: JoinBuild, hit_rate: float = 0.9, dist: str = "uni
     hit = unit_f64(stream_seed(seed, 3), n) < hit_rate
     u = unit_f64(stream_seed(seed, 4), n)
     if dist == "uniform":
-        idx = np.minimum(np.floor(u * d).astype(np.int64), d - 1)
+        idx = np.empty(n, dtype=np.int64)
+
+        def part(a, b):
+            idx[a:b] = np.minimum(np.floor(u[a:b] * d).astype(np.int64), d - 1)
+        _par_chunks(n, part)
     elif dist == "zipf":
         ranks = _zipf_ranks(u, d, zipf_s)
         perm = np.argsort(splitmix64(stream_seed(seed, 6), d), kind="stable")
-        idx = perm[ranks]
+        idx = _take(perm, ranks)
     else:
         raise ValueError(dist)
-    keys = build.distinct[idx]
+    keys = _take(build.distinct, idx)
     nm = int(n - int(hit.sum()))
     miss = splitmix64(stream_seed(seed, 5), nm).view(np.int64)
     sorted_build = np.sort(build.distinct)
     nxt = nm
     while nm:
-        pos = np.minimum(np.searchsorted(sorted_build, miss), d - 1)
-        bad = np.flatnonzero(sorted_build[pos] == miss)
+        pos = np.minimum(_searchsorted(sorted_build, miss), d - 1)
+        bad = np.flatnonzero(_take(sorted_build, pos) == miss)
         if bad.shape[0] == 0:
             break
         miss[bad] = splitmix64(stream_seed(seed, 5), bad.shape[0], start=nxt).view(np.int64)

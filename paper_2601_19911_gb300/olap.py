@@ -616,6 +616,19 @@ def topk_noalloc(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=
     if n > NOALLOC_MAX_N or int(k) > NOALLOC_MAX_K:
         raise ValueError(f"olap_topk_noalloc handles n <= {NOALLOC_MAX_N} and k <= {NOALLOC_MAX_K}; "
                          f"got n={n}, k={k}")
+    if int(k) < 0 or int(order) not in (ASC, DESC):
+        raise ValueError(f"bad k={k} or order={order}")
+    cnt = min(int(k), n)
+    for nm, buf in (("d_keys", d_keys), ("d_out_keys", d_out_keys), ("d_out_rowids", d_out_rowids),
+                    ("d_rowids", d_rowids), ("dev_status", dev_status)):
+        if buf is not None and mem_kind(buf) != MEM_DEVICE:
+            raise ValueError(f"{nm} must be a CUDA tensor")
+    if cnt and (d_out_keys is None or d_out_rowids is None):
+        raise ValueError("output buffers are required when min(k, n) > 0")
+    if cnt and (numel(d_out_keys) < cnt or numel(d_out_rowids) < cnt):
+        raise ValueError(f"outputs must hold min(k, n) = {cnt} entries")
+    if d_rowids is not None and numel(d_rowids) != n:
+        raise ValueError(f"{numel(d_rowids)} row-ids for {n} keys")
     st = lib.olap_topk_noalloc(ptr(d_keys), key_type_of(d_keys), ptr(d_rowids), n, int(k), int(order),
                                ptr(d_out_keys), ptr(d_out_rowids), ptr(dev_status), stream)
     if st != OK:

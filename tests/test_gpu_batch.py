@@ -273,7 +273,7 @@ def test_full_size_batch_sampled():
 def test_launch_counter_counts_every_kernel():
     """olap_ctx_launches: the direct Top-K is two kernels (prepare, select),
     the sampled one three (prepare, filter, select); a build without key -1
-    one; a direct probe one, a partitioned probe three; a batch replay the
+    two (insert, chain counts); a direct probe one, a partitioned probe three; a batch replay the
     kernels of its graph (probe reset, probe, Top-K); the per-query run the
     sum of its calls.  A staged context launches no copy kernels."""
     if not torch.cuda.is_available():
@@ -294,7 +294,7 @@ def test_launch_counter_counts_every_kernel():
         assert delta(lambda: c.topk(small.cpu().numpy(), 100, olap.DESC)) == 2      # staged copies are not kernels
         b = datagen.join_build(50_000, "unique", seed=72)
         holder = []
-        assert delta(lambda: holder.append(c.join_build(torch.from_numpy(b.keys).cuda()))) == 1
+        assert delta(lambda: holder.append(c.join_build(torch.from_numpy(b.keys).cuda()))) == 2
         t = holder[0]
         p = datagen.join_probe(40_000, b, 0.5, "uniform", seed=72)
         pk = torch.from_numpy(p.keys).cuda()

@@ -3,9 +3,10 @@ set of matched (probe, build) row pointers) against the CPU oracle: the pair
 multiset, compared sorted, bit-exact.
 
 Small and medium sizes compare every pair.  The full-size workload (2^24
-build rows, 2^28 probes) checks the exact pair count the generator fixes
-(sum of build multiplicities over the hits), key equality of every pair, and
-the exact pairs of a sample of probe rows against the oracle.
+build rows, 2^28 probes, all eight cells) checks the exact pair count the
+generator fixes (sum of build multiplicities over the hits), key equality and
+distinctness of every pair, and the exact pairs of a sample of probe rows
+against the oracle.
 """
 import numpy as np
 import pytest
@@ -199,11 +200,31 @@ def test_bucket_load_paths(loads, parts):
         c.close()
 
 
-@pytest.mark.parametrize("mult,dist,hit", [("mult14", "zipf", 0.9), ("unique", "uniform", 0.1)])
+_BUILDS = {}
+
+
+def _full_build(mult):
+    """The 2^24-row build side of a full-size cell, generated once per
+    multiplicity for the whole module."""
+    if mult not in _BUILDS:
+        _BUILDS.clear()
+        _BUILDS[mult] = datagen.join_build(1 << 24, mult, seed=2)
+    return _BUILDS[mult]
+
+
+@pytest.mark.parametrize("hit", [0.1, 0.9])
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+@pytest.mark.parametrize("mult", ["unique", "mult14"])
 def test_full_size(ctx, mult, dist, hit):
-    """2^24 build rows, 2^28 probe keys, device resident (the benchmark's call;
-    the table is 8x L2, so the automatic mode takes the partitioned probe)."""
-    b = datagen.join_build(1 << 24, mult, seed=2)
+    """Every join cell at full size: 2^24 build rows, 2^28 probe keys, device
+    resident, the benchmark's call (the table is 8x L2, so the automatic mode
+    takes the partitioned probe).  The pair set is fixed by four checks:
+    the exact count the generator implies (the sum of build multiplicities
+    over the hits), every pair joining equal keys, every pair distinct
+    (sorted on the device, strictly increasing), and the exact pairs of 4096
+    sampled probe rows against the oracle.  Distinct valid pairs as many as
+    the join has are the join."""
+    b = _full_build(mult)
     p = datagen.join_probe(1 << 28, b, hit, dist, seed=2)
     need = p.expected_pairs(b)
     t = ctx.join_build(torch.from_numpy(b.keys).cuda())
@@ -212,21 +233,26 @@ def test_full_size(ctx, mult, dist, hit):
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
     ctx.join_probe_async(t, dk, out, need, cnt)
     ctx.sync()
+    t.free()
     assert int(cnt.item()) == need
-    pairs = out
-    pr = pairs[:, 0].to(torch.int64) & 0xFFFFFFFF
-    br = pairs[:, 1].to(torch.int64) & 0xFFFFFFFF
+    pr = out[:, 0].to(torch.int64) & 0xFFFFFFFF
+    br = out[:, 1].to(torch.int64) & 0xFFFFFFFF
+    assert bool((pr < (1 << 28)).all()) and bool((br < (1 << 24)).all())
     bkd = torch.from_numpy(b.keys).cuda()
     assert torch.equal(dk[pr], bkd[br])                       # every pair joins equal keys
+    del bkd
+    packed_d = torch.sort((pr << 32) | br).values
+    del br
+    assert bool((packed_d[1:] > packed_d[:-1]).all())          # no pair twice
+    del packed_d
     # exact pairs of a sample of probe rows against the oracle
     rng = np.random.default_rng(0)
     rows = np.sort(rng.choice(1 << 28, 4096, replace=False))
     sel = torch.isin(pr, torch.from_numpy(rows).cuda())
-    got = packed(pairs[sel].cpu().numpy().view(np.uint32))
+    got = packed(out[sel].cpu().numpy().view(np.uint32))
     want = oracle.join(b.keys, p.keys[rows], None, rows.astype(np.uint32))
     np.testing.assert_array_equal(got, want)
-    t.free()
-    del dk, out, bkd
+    del dk, out, pr, sel
     torch.cuda.empty_cache()
 
 

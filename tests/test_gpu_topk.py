@@ -247,59 +247,79 @@ def test_total_order_key_matches_fixture():
     assert np.all(k[1:] > k[:-1])
 
 
-def _full_size_properties(keys, k, order, gk, gr):
-    n = keys.shape[0]
-    assert gr.shape[0] == k
-    idx = gr.astype(np.int64)
-    assert np.all(idx < n)
-    assert np.unique(idx).shape[0] == k                               # distinct rows
-    np.testing.assert_array_equal(_bits(keys[idx]), _bits(gk))        # real input rows
-    if keys.dtype == np.int64:
-        sk = keys.astype(np.int64)
-        ko = gk.astype(np.int64)
-    else:
-        sk = _total_order_i32(keys.view(np.uint32)).astype(np.int64)
-        ko = _total_order_i32(gk.view(np.uint32)).astype(np.int64)
-    sgn = -1 if order == olap.DESC else 1
-    # sorted by (key in the requested order, row-id ascending)
-    a = ko[:-1] * 0
-    prev_k, next_k = ko[:-1], ko[1:]
-    if sgn < 0:
-        ok_order = (prev_k > next_k) | ((prev_k == next_k) & (idx[:-1] < idx[1:]))
-    else:
-        ok_order = (prev_k < next_k) | ((prev_k == next_k) & (idx[:-1] < idx[1:]))
-    assert np.all(ok_order), a
-    lk, lr = ko[-1], idx[-1]
+def _rank_dev(t):
+    """A signed integer per key, in the keys' total order, on the device:
+    int64 as is; float32 bits mapped like ``_total_order_i32``."""
+    if t.dtype == torch.int64:
+        return t
+    x = t.view(torch.int32)
+    return (x ^ ((x >> 31) & 0x7FFFFFFF)).to(torch.int64)
+
+
+def _full_size_properties(dk, k, order, ok, orow, reversed_rowids=False):
+    """Properties that fix the Top-K of a full-size column uniquely (checked
+    on the device): K distinct real input rows with their own key bits, in
+    (key, row-id) order, and exactly K-1 rows of the whole column strictly
+    ahead of the last one.  Row-ids are the index, or n-1-index when the
+    caller passed reversed row-ids."""
+    n = dk.numel()
+    rid = orow.to(torch.int64) & 0xFFFFFFFF
+    assert rid.numel() == k and bool((rid < n).all())
+    idx = (n - 1 - rid) if reversed_rowids else rid
+    assert torch.unique(idx).numel() == k                                   # distinct rows
+    ibits = torch.int64 if dk.dtype == torch.int64 else torch.int32
+    assert torch.equal(dk[idx].view(ibits), ok.view(ibits))                 # real input rows
+    ko = _rank_dev(ok)
+    pk, nk, pr, nr = ko[:-1], ko[1:], rid[:-1], rid[1:]
+    better = (pk > nk) if order == olap.DESC else (pk < nk)
+    assert bool((better | ((pk == nk) & (pr < nr))).all())                  # sorted, ties by row-id
+    lk, lr = ko[-1], rid[-1]
     ahead = 0
-    step = 1 << 25
-    for s in range(0, n, step):
-        blk = sk[s:s + step]
-        rows = np.arange(s, min(n, s + step), dtype=np.int64)
-        better = (blk > lk) if sgn < 0 else (blk < lk)
-        ahead += int(np.count_nonzero(better | ((blk == lk) & (rows < lr))))
+    step = 1 << 26
+    for s0 in range(0, n, step):
+        blk = _rank_dev(dk[s0:s0 + step])
+        rows = torch.arange(s0, min(n, s0 + step), dtype=torch.int64, device=dk.device)
+        if reversed_rowids:
+            rows = n - 1 - rows
+        b = (blk > lk) if order == olap.DESC else (blk < lk)
+        ahead += int((b | ((blk == lk) & (rows < lr))).sum().item())
     assert ahead == k - 1
 
 
-FULL = [("i64", "uniform", 10), ("i64", "uniform", 1000), ("i64", "uniform", 100_000),
-        ("i64", "ascending", 1000), ("i64", "dup1024", 1000), ("i64", "dup1024", 100_000),
-        ("f32", "uniform", 10), ("f32", "uniform", 100_000), ("f32", "ascending", 1000),
-        ("f32", "dup1024", 1000)]
+FULL_CELLS = [(kt, dist) for kt in ("i64", "f32") for dist in ("uniform", "ascending", "dup1024")]
 
 
-@pytest.mark.parametrize("kt,dist,k", FULL)
-def test_full_size_2p28(ctx, kt, dist, k):
+@pytest.mark.parametrize("kt,dist", FULL_CELLS)
+def test_full_size_2p28(ctx, kt, dist):
+    """Every Top-K-at-scale cell: N = 2^28 keys of {int64, float32} x
+    {uniform, ascending, 1024 distinct} x K in {10, 1000, 100000}, DESC (and
+    ASC at K = 1000), device resident, the call the benchmark times."""
     n = 1 << 28
-    keys = datagen.topk_keys(n, dist, kt, seed=1)
-    dk = torch.from_numpy(keys).cuda()
-    ok = torch.empty(k, dtype=dk.dtype, device="cuda")
-    orow = torch.empty(k, dtype=torch.int32, device="cuda")
-    for order in (olap.DESC, olap.ASC) if k == 1000 else (olap.DESC,):
-        ctx.topk(dk, k, order, out_keys=ok, out_rowids=orow)
-        gk = ok.cpu().numpy()
-        gr = orow.cpu().numpy().view(np.uint32)
-        _full_size_properties(keys, k, order, gk, gr)
-        if dist == "ascending":                                        # closed form
-            want = np.arange(n - 1, n - 1 - k, -1) if order == olap.DESC else np.arange(k)
-            np.testing.assert_array_equal(gr.astype(np.int64), want)
+    dk = torch.from_numpy(datagen.topk_keys(n, dist, kt, seed=1)).cuda()
+    for k in (10, 1000, 100_000):
+        ok = torch.empty(k, dtype=dk.dtype, device="cuda")
+        orow = torch.empty(k, dtype=torch.int32, device="cuda")
+        for order in (olap.DESC, olap.ASC) if k == 1000 else (olap.DESC,):
+            ctx.topk(dk, k, order, out_keys=ok, out_rowids=orow)
+            _full_size_properties(dk, k, order, ok, orow)
+            if dist == "ascending":                                        # closed form
+                want = np.arange(n - 1, n - 1 - k, -1) if order == olap.DESC else np.arange(k)
+                np.testing.assert_array_equal(orow.cpu().numpy().view(np.uint32).astype(np.int64), want)
     del dk
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kt", ["i64", "f32"])
+def test_full_size_explicit_rowids(ctx, kt):
+    """2^28 keys with 1024 distinct values and explicit u32 row-ids n-1..0, so
+    the row-id tie-break runs against the index order inside every tie group."""
+    n = 1 << 28
+    dk = torch.from_numpy(datagen.topk_keys(n, "dup1024", kt, seed=1)).cuda()
+    dr = torch.arange(n - 1, -1, -1, dtype=torch.int64, device="cuda").to(torch.int32)
+    for k, order in ((1000, olap.DESC), (1000, olap.ASC), (100_000, olap.DESC)):
+        ok = torch.empty(k, dtype=dk.dtype, device="cuda")
+        orow = torch.empty(k, dtype=torch.int32, device="cuda")
+        ctx.topk(dk, k, order, rowids=dr, out_keys=ok, out_rowids=orow)
+        _full_size_properties(dk, k, order, ok, orow, reversed_rowids=True)
+    del dk, dr
     torch.cuda.empty_cache()

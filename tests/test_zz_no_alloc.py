@@ -5,15 +5,16 @@ whose device memory belongs to their own pool, operator hosts that forbid
 allocation, paths that cannot take cudaMalloc's synchronisation); its working
 memory is a fixed array inside the library.  This test calls it through the C
 ABI twice in a row -- the second call reusing the array the first one left
-behind -- and checks each result against olap_topk on the same input.  The
-results are integers and row-ids, so the comparison is exact.  This file is
-collected last so that a failure here comes after every other test has run.
+behind -- and once more at the size limits, where its working set is largest,
+and checks each result against the CPU oracle and against olap_topk on the
+same input.  The results are integers and row-ids, so the comparison is
+exact.  This file is collected last so that a failure here comes after every
+other test has run.
 """
-import ctypes
-
 import numpy as np
 import pytest
 
+import oracle
 from paper_2601_19911_gb300 import datagen, olap
 
 torch = pytest.importorskip("torch")
@@ -44,20 +45,30 @@ def _noalloc(keys_np, k, order):
     return ok.cpu().numpy(), orow.cpu().numpy().view(np.uint32)
 
 
-def _reference(ctx, keys_np, k, order):
-    return ctx.topk(keys_np, k, order)
+def _same(keys, k, order, ctx):
+    gk, gr = _noalloc(keys, k, order)
+    ok, orow = oracle.topk(keys, k, order)
+    np.testing.assert_array_equal(gr, orow)
+    np.testing.assert_array_equal(gk.view(np.uint8), ok.view(np.uint8))
+    wk, wr = ctx.topk(keys, k, order)
+    np.testing.assert_array_equal(gr, wr)
+    np.testing.assert_array_equal(gk.view(np.uint8), wk.view(np.uint8))
 
 
-def test_two_calls_in_a_row_match_olap_topk(ctx):
+def test_two_calls_in_a_row_match_oracle_and_olap_topk(ctx):
     # First call: sampled single-pass path (n > 2^21), int64, DESC.
     a = datagen.topk_keys(3_000_001, "uniform", "i64", seed=31)
     # Second call: direct path, float32 with duplicates, ASC, the largest k.
     b = datagen.topk_keys(200_003, "dup1024", "f32", seed=32)
-    for keys, k, order in ((a, 1000, olap.DESC), (b, olap.NOALLOC_MAX_K, olap.ASC)):
-        gk, gr = _noalloc(keys, k, order)
-        wk, wr = _reference(ctx, keys, k, order)
-        np.testing.assert_array_equal(gr, wr)
-        np.testing.assert_array_equal(gk.view(np.uint8), wk.view(np.uint8))
+    _same(a, 1000, olap.DESC, ctx)
+    _same(b, olap.NOALLOC_MAX_K, olap.ASC, ctx)
+
+
+def test_at_the_size_limits(ctx):
+    # n and k at their maxima on the sampled path: the largest candidate
+    # buffer the fixed array has to hold.
+    keys = datagen.topk_keys(olap.NOALLOC_MAX_N, "uniform", "i64", seed=33)
+    _same(keys, olap.NOALLOC_MAX_K, olap.DESC, ctx)
 
 
 def test_sizes_beyond_the_array_are_refused():
