@@ -103,7 +103,25 @@ typedef struct {
                                    other, 1 => side by side (two branches of the graph); each
                                    already fills the GPU, and side by side measured no faster */
     int batch_topk_ctas_per_sm; /* batches: resident Top-K CTAs per SM (1 or 2; 0 => 2) */
+    int join_prefilter;         /* olap_prefilter: Bloom pre-probe of the join (Sec. III-B) */
+    int staging_threads;        /* host threads that copy pageable data into and out of the
+                                   pinned staging buffers (1..64; 0 => 4) */
 } olap_opts;
+
+/* Bloom pre-probe of the join ("bloom-filter/partitioned hash", Sec. III-B).
+ * A table far above L2 gets a blocked Bloom filter over its keys (about 16
+ * bits per build row, one 32-byte block per key) when it is built.  Before a
+ * probe, a sample of the probe keys is tested on the device; when few pass,
+ * one streaming pass drops every probe row the filter rules out and only the
+ * rest is probed (partitioned or direct).  No host synchronisation: the
+ * decision and the surviving row count stay on the device. */
+typedef enum {
+    OLAP_PREFILTER_AUTO = 0,    /* filter built for tables above half of L2; used when at most
+                                   60 % of a 4096-key sample of a probe of >= 2^20 rows passes */
+    OLAP_PREFILTER_OFF = 1,     /* no filter built, none used */
+    OLAP_PREFILTER_ON = 2       /* filter built for every table (with rows) and used for every
+                                   probe */
+} olap_prefilter;
 
 /* How pageable host inputs and outputs (OLAP_MEM_HOST) cross the host link. */
 typedef enum {
@@ -290,13 +308,16 @@ olap_status olap_topk_rows(olap_ctx* ctx, const void* rows, olap_mem in_where, u
  * key-only hash table", pointers returned for late materialization, Sec. II-C).
  *
  * The table is an open-addressing table of 16-byte slots {int64 key, uint32
- * row-id}, two slots per 32-byte bucket, with linear probing over buckets
- * (a bucket with a free slot ends every chain).  Capacity is the power of two
- * of buckets that keeps n / (2 * buckets) at or below the load factor.  Build
- * rows whose key equals the table's empty marker (all bits set, i.e. -1) are
- * kept in a side list, so every int64 key value joins correctly.  The table
- * stays resident on the device until olap_join_free; it may be probed any
- * number of times, from any context on the same device.
+ * row-id, uint32 count of further copies of the key along its chain}, two
+ * slots per 32-byte bucket, with linear probing over buckets (a bucket with a
+ * free slot ends every chain; a probe also stops at its key's last copy).
+ * Capacity is the power of two of buckets that keeps n / (2 * buckets) at or
+ * below the load factor.  Build rows whose key equals the table's empty
+ * marker (all bits set, i.e. -1) are kept in a side list, so every int64 key
+ * value joins correctly.  A table far above L2 also carries a blocked Bloom
+ * filter for the pre-probe (see olap_prefilter).  The table stays resident on
+ * the device until olap_join_free; it may be probed any number of times, from
+ * any context on the same device.
  *
  * Result: every (probe row-id, build row-id) pair whose keys are equal, as a
  * multiset (duplicate keys on either side multiply), in no particular order.
@@ -338,6 +359,14 @@ olap_status olap_join_probe_async(olap_ctx* ctx, const olap_join_table* table, c
  * automatic, by the table's size against the device's L2.  Host arithmetic
  * only; OLAP_E_INVALID for a NULL or freed table or a NULL *parts. */
 olap_status olap_join_probe_partitions(olap_ctx* ctx, const olap_join_table* table, uint64_t n, int* parts);
+
+/* How the last probe enqueued on this context ran: *parts as
+ * olap_join_probe_partitions; *prefiltered = 1 when the Bloom pre-probe
+ * dropped rows before the probe (0 when it was not used or the sample said
+ * not to); *rows_probed = the probe rows left after it (n when not used).
+ * Waits for the context's stream.  OLAP_E_INVALID for NULL outputs or when no
+ * probe has run on the context. */
+olap_status olap_join_probe_info_last(olap_ctx* ctx, int* parts, int* prefiltered, uint64_t* rows_probed);
 
 /* Table facts: build rows, buckets (2 slots each), rows in the side list. */
 olap_status olap_join_table_info(const olap_join_table* table, uint64_t* n_build, uint64_t* n_buckets,

@@ -109,6 +109,10 @@ olap_status ensure_pinned(olap_ctx* ctx) {
         }
     }
     ctx->pinned_bytes = b;
+    if (!ctx->copy_pool) {
+        const int threads = ctx->opts.staging_threads ? ctx->opts.staging_threads : 4;
+        ctx->copy_pool = new HostCopyPool(threads - 1);
+    }
     return OLAP_OK;
 }
 
@@ -180,7 +184,7 @@ olap_status copy_h2d(olap_ctx* ctx, void* dst, const void* src, size_t bytes, ol
         const size_t len = std::min(ctx->pinned_bytes, bytes - off);
         e = cudaEventSynchronize(ctx->pinned_ev[slot]);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "staging wait");
-        std::memcpy(ctx->pinned[slot], s + off, len);
+        ctx->copy_pool->copy(ctx->pinned[slot], s + off, len);
         e = cudaMemcpyAsync(d + off, ctx->pinned[slot], len, cudaMemcpyHostToDevice, ctx->stream);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "staged H2D copy");
         e = cudaEventRecord(ctx->pinned_ev[slot], ctx->stream);
@@ -222,7 +226,7 @@ olap_status copy_d2h(olap_ctx* ctx, void* dst, const void* src, size_t bytes, ol
             if (pend_slot >= 0) {
                 e = cudaEventSynchronize(ctx->pinned_ev[pend_slot]);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "staging wait");
-                std::memcpy(d + pend_off, ctx->pinned[pend_slot], pend_len);
+                ctx->copy_pool->copy(d + pend_off, ctx->pinned[pend_slot], pend_len);
             }
             pend_slot = slot;
             pend_off = off;
@@ -232,7 +236,7 @@ olap_status copy_d2h(olap_ctx* ctx, void* dst, const void* src, size_t bytes, ol
         } else {
             e = cudaEventSynchronize(ctx->pinned_ev[pend_slot]);
             if (e != cudaSuccess) return cuda_fail(ctx, e, "staging wait");
-            std::memcpy(d + pend_off, ctx->pinned[pend_slot], pend_len);
+            ctx->copy_pool->copy(d + pend_off, ctx->pinned[pend_slot], pend_len);
             pend_slot = -1;
         }
     }
@@ -311,7 +315,9 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
         (ctx->opts.topk_digit_bits != 0 && (ctx->opts.topk_digit_bits < 8 || ctx->opts.topk_digit_bits > 12)) ||
         ctx->opts.host_access < OLAP_HOST_AUTO || ctx->opts.host_access > OLAP_HOST_STAGED ||
         ctx->opts.batch_overlap < 0 || ctx->opts.batch_overlap > 1 || ctx->opts.batch_topk_ctas_per_sm < 0 ||
-        ctx->opts.batch_topk_ctas_per_sm > 2 ||
+        ctx->opts.batch_topk_ctas_per_sm > 2 || ctx->opts.join_prefilter < OLAP_PREFILTER_AUTO ||
+        ctx->opts.join_prefilter > OLAP_PREFILTER_ON || ctx->opts.staging_threads < 0 ||
+        ctx->opts.staging_threads > 64 ||
         (ctx->opts.block_threads != 0 && ctx->opts.block_threads != 256 && ctx->opts.block_threads != 512 &&
          ctx->opts.block_threads != 1024) ||
         (ctx->opts.l2_fetch_bytes != 0 && ctx->opts.l2_fetch_bytes != 32 && ctx->opts.l2_fetch_bytes != 64 &&
@@ -382,6 +388,7 @@ void olap_ctx_destroy(olap_ctx* ctx) {
         if (ctx->pinned[i]) cudaFreeHost(ctx->pinned[i]);
         if (ctx->pinned_ev[i]) cudaEventDestroy(ctx->pinned_ev[i]);
     }
+    delete ctx->copy_pool;
     for (cudaEvent_t ev : ctx->kev)
         if (ev) cudaEventDestroy(ev);
     if (ctx->host_status) cudaFreeHost(ctx->host_status);

@@ -8,6 +8,7 @@
 #include <set>
 #include <string>
 
+#include "hostcopy.h"
 #include "olap.h"
 #include "topk.cuh"
 
@@ -35,6 +36,7 @@ struct olap_ctx {
     void* pinned[2] = {nullptr, nullptr};
     size_t pinned_bytes = 0;
     cudaEvent_t pinned_ev[2] = {nullptr, nullptr};
+    olap::HostCopyPool* copy_pool = nullptr;   // host threads of the staging copies
 
     // Small pinned words for device status read-back, and a small device
     // area for counters of blocking calls (4 KiB).
@@ -65,6 +67,12 @@ struct olap_ctx {
     size_t part_bytes = 0;
     uint64_t l2_bytes = 0;            // device L2 size
     bool host_direct = false;         // copy pageable host memory with a kernel (no CPU staging)
+
+    // The last probe enqueued: partitions, rows, and its pre-probe control
+    // block on the device (NULL when it ran none).
+    int last_probe_parts = 0;
+    uint64_t last_probe_n = 0;
+    const void* last_probe_pf = nullptr;
 
     // Device memory held by live join tables built through this context.
     uint64_t table_bytes = 0;

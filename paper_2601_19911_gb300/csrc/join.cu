@@ -116,14 +116,135 @@ __global__ void __launch_bounds__(JB_TPB) join_side_kernel(const int64_t* keys, 
 // by partition (pass 3 of the partitioned probe): there the chunks come out in
 // partition order, so the warps of the whole grid work on one partition's
 // table slice at a time and that slice stays in L2.
+// With the Bloom pre-probe (pf non-NULL and active on the device) the row
+// count is the number of rows it kept, and a direct probe reads those rows
+// (pf_keys non-NULL); a partitioned probe already reads them reordered.
 template <bool L2_ONLY>
-__global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs a, unsigned long long* next_row) {
+__global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs args, unsigned long long* next_row,
+                                                               const PrefilterCtl* pf, const int64_t* pf_keys,
+                                                               const uint32_t* pf_rowids) {
     extern __shared__ __align__(16) uint2 stage[];
     const unsigned warp = threadIdx.x >> 5;
+    ProbeArgs a = args;
+    if (pf && pf->active) {
+        a.n = pf->count;
+        if (pf_keys) {
+            a.keys = pf_keys;
+            a.rowids = pf_rowids;
+        }
+    }
     RowQueue q;
     q.counter = next_row;
     q.n = a.n;
     probe_queue<L2_ONLY>(a, q, stage + warp * JP_WCAP);
+}
+
+// ---- Bloom pre-probe ------------------------------------------------------
+
+// Every build key sets its eight bits in its block (the empty-marker key,
+// kept in the side list, is not entered: the pre-probe keeps such probe rows
+// whatever the filter says).
+__global__ void __launch_bounds__(JB_TPB) join_bloom_kernel(const int64_t* keys, uint64_t n, uint32_t* bloom,
+                                                            uint64_t bmask) {
+    const uint64_t stride = static_cast<uint64_t>(gridDim.x) * JB_TPB;
+    for (uint64_t i = static_cast<uint64_t>(blockIdx.x) * JB_TPB + threadIdx.x; i < n; i += stride) {
+        const uint64_t key = static_cast<uint64_t>(keys[i]);
+        if (key == JN_EMPTY) continue;
+        uint32_t* blk = bloom + bloom_block(key, bmask) * BLOOM_WORDS;
+        const uint64_t g = fmix64(~key);
+#pragma unroll
+        for (int w = 0; w < BLOOM_WORDS; ++w) atomicOr(blk + w, bloom_bit(g, w));
+    }
+}
+
+constexpr int PF_TPB = 256;
+constexpr int PF_SAMPLE = 4096;                // probe keys tested to decide
+constexpr uint64_t PF_MIN_N = 1ull << 20;      // smaller probes skip the pre-probe (automatic mode)
+constexpr int PF_PER = 4;                      // keys per lane per step
+constexpr unsigned PF_WCAP = 256;              // rows staged per warp
+
+// Decide on the device whether the pre-probe runs: a stratified sample of
+// PF_SAMPLE probe keys (n >= PF_SAMPLE) against the filter; it runs when at
+// most 60 % pass (or always when forced).  Also zeroes the kept-row count.
+__global__ void __launch_bounds__(PF_TPB) join_prefilter_sample_kernel(const int64_t* keys, uint64_t n,
+                                                                       const uint32_t* bloom, uint64_t bmask,
+                                                                       int force, PrefilterCtl* ctl) {
+    __shared__ unsigned passes;
+    if (threadIdx.x == 0) passes = 0;
+    __syncthreads();
+    unsigned mine = 0;
+    if (!force) {
+        for (int j = threadIdx.x; j < PF_SAMPLE; j += PF_TPB) {
+            const uint64_t key = static_cast<uint64_t>(keys[(static_cast<uint64_t>(j) * n) / PF_SAMPLE]);
+            const bool maybe = bloom_maybe(bloom, bmask, key);
+            mine += (key == JN_EMPTY || maybe) ? 1u : 0u;
+        }
+    }
+    atomicAdd(&passes, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->active = (force || passes * 10u <= static_cast<unsigned>(PF_SAMPLE) * 6u) ? 1 : 0;
+        ctl->count = 0;
+    }
+}
+
+// The pre-probe: one streaming pass over the probe rows that keeps the rows
+// whose key may be in the table (and every row with the empty-marker key),
+// appended with their row-ids through a per-warp stage, one atomic per flush.
+__global__ void __launch_bounds__(PF_TPB) join_prefilter_kernel(const int64_t* keys, const uint32_t* rowids,
+                                                                uint64_t n, const uint32_t* bloom, uint64_t bmask,
+                                                                PrefilterCtl* ctl, int64_t* out_keys,
+                                                                uint32_t* out_rowids) {
+    if (!ctl->active) return;
+    __shared__ int64_t sk[PF_TPB / 32][PF_WCAP];
+    __shared__ uint32_t sr[PF_TPB / 32][PF_WCAP];
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    int64_t* wk = sk[warp];
+    uint32_t* wr = sr[warp];
+    unsigned cnt = 0;
+    auto flush = [&]() {
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0 && cnt) base = atomicAdd(&ctl->count, static_cast<unsigned long long>(cnt));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        for (unsigned i = lane; i < cnt; i += 32) {
+            out_keys[base + i] = wk[i];
+            out_rowids[base + i] = wr[i];
+        }
+        __syncwarp();
+        cnt = 0;
+    };
+    constexpr uint64_t G = 32ull * PF_PER;
+    const uint64_t groups = (n + G - 1) / G;
+    const uint64_t nw = static_cast<uint64_t>(gridDim.x) * (PF_TPB / 32);
+    for (uint64_t g = static_cast<uint64_t>(blockIdx.x) * (PF_TPB / 32) + warp; g < groups; g += nw) {
+        uint64_t key[PF_PER];
+        bool keep[PF_PER];
+#pragma unroll
+        for (int j = 0; j < PF_PER; ++j) {
+            const uint64_t i = g * G + static_cast<uint64_t>(j) * 32 + lane;
+            key[j] = i < n ? ld_stream_u64(keys + i) : 0ull;
+        }
+#pragma unroll
+        for (int j = 0; j < PF_PER; ++j) {
+            const uint64_t i = g * G + static_cast<uint64_t>(j) * 32 + lane;
+            const bool maybe = bloom_maybe(bloom, bmask, key[j]);
+            keep[j] = i < n && (key[j] == JN_EMPTY || maybe);
+        }
+#pragma unroll
+        for (int j = 0; j < PF_PER; ++j) {
+            const uint64_t i = g * G + static_cast<uint64_t>(j) * 32 + lane;
+            const unsigned b = __ballot_sync(0xFFFFFFFFu, keep[j]);
+            if (cnt + 32 > PF_WCAP) flush();
+            if (keep[j]) {
+                const unsigned pos = cnt + __popc(b & ((1u << lane) - 1u));
+                wk[pos] = static_cast<int64_t>(key[j]);
+                wr[pos] = rowids ? ld_stream_u32(rowids + i) : static_cast<uint32_t>(i);
+            }
+            cnt += __popc(b);
+        }
+    }
+    flush();
 }
 
 // ---- partitioned probe ------------------------------------------------------
@@ -146,7 +267,22 @@ struct PartArgs {
     unsigned long long* pstart;                // [parts + 1] partition offsets (written by CTA 0)
     int64_t* out_keys;
     uint32_t* out_rowids;
+    const PrefilterCtl* pf;                    // non-NULL: rows may come from the Bloom pre-probe
+    const int64_t* pf_keys;                    // its surviving rows, used when pf->active
+    const uint32_t* pf_rowids;
 };
+
+// The rows a partition pass reads: the probe's input, or the rows the Bloom
+// pre-probe kept (decided on the device by the stage before).
+__device__ __forceinline__ PartArgs part_source(const PartArgs& in) {
+    PartArgs a = in;
+    if (a.pf && a.pf->active) {
+        a.keys = a.pf_keys;
+        a.rowids = a.pf_rowids;
+        a.n = a.pf->count;
+    }
+    return a;
+}
 
 __device__ __forceinline__ unsigned part_of(uint64_t key, const PartArgs& a) {
     return static_cast<unsigned>((fmix64(key) & a.mask) >> a.shift);
@@ -154,7 +290,8 @@ __device__ __forceinline__ unsigned part_of(uint64_t key, const PartArgs& a) {
 
 // Pass 1: rows of each partition in the tiles of this CTA (tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...).
-__global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs a) {
+__global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs args) {
+    const PartArgs a = part_source(args);
     __shared__ unsigned h[JQ_PMAX];
     for (int p = threadIdx.x; p < a.parts; p += JQ_TPB) h[p] = 0;
     __syncthreads();
@@ -182,7 +319,8 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs a) {
 // rows already placed), reordered in shared memory so the writes of a
 // partition's run are contiguous.  The keys of the CTA's next tile are loaded
 // while the current one is reordered.
-__global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs a) {
+__global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs args) {
+    const PartArgs a = part_source(args);
     __shared__ unsigned h[JQ_PMAX];
     __shared__ unsigned off[JQ_PMAX];
     __shared__ unsigned long long base[JQ_PMAX];
@@ -327,12 +465,27 @@ int probe_parts(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
     return static_cast<int>(std::max<uint64_t>(parts, 1));
 }
 
-size_t probe_scratch_bytes(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
-    const int parts = probe_parts(ctx, t, n);
+// Whether a probe of n rows against t runs the Bloom pre-probe stage (its
+// sample still decides on the device whether rows are dropped).
+bool probe_prefilter(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
+    if (!t->bloom || n == 0) return false;
+    const int opt = ctx->opts.join_prefilter;
+    return opt == OLAP_PREFILTER_ON || (opt == OLAP_PREFILTER_AUTO && n >= PF_MIN_N);
+}
+
+// Partition scratch: [partitioned keys | row-ids | count matrix | partition
+// starts]; then, with the pre-probe, [kept keys | kept row-ids | control].
+size_t probe_part_bytes(const olap_ctx* ctx, uint64_t n, int parts) {
     if (parts <= 1) return 0;
     // room for the largest grid the partition passes can take
     const uint64_t grid = static_cast<uint64_t>(ctx->sm_count) * JQ_CTAS_PER_SM;
     return align256(n * 8) + align256(n * 4) + align256(grid * parts * 8) + align256((parts + 1) * 8);
+}
+
+size_t probe_scratch_bytes(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
+    const size_t pb = probe_part_bytes(ctx, n, probe_parts(ctx, t, n));
+    if (!probe_prefilter(ctx, t, n)) return pb;
+    return pb + align256(n * 8) + align256(n * 4) + align256(sizeof(PrefilterCtl));
 }
 
 }  // namespace olap
@@ -346,7 +499,12 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
                           uint64_t n, olap_pair* d_out, uint64_t capacity, uint64_t* d_count, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "probe count reset");
-    if (n == 0) return OLAP_OK;
+    if (n == 0) {
+        ctx->last_probe_parts = 1;
+        ctx->last_probe_n = 0;
+        ctx->last_probe_pf = nullptr;
+        return OLAP_OK;
+    }
     const int grid = probe_grid(ctx->device);
     if (grid <= 0) return fail(ctx, OLAP_E_CUDA, "probe kernel occupancy query failed");
     ProbeArgs a;
@@ -361,11 +519,25 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     a.cap = capacity;
     a.count = reinterpret_cast<unsigned long long*>(d_count);
     const int parts = probe_parts(ctx, t, n);
+    const bool pre = probe_prefilter(ctx, t, n);
     PartArgs q{};
     unsigned qgrid = 0;
-    if (parts > 1) {
+    PrefilterCtl* pf = nullptr;
+    int64_t* pf_keys = nullptr;
+    uint32_t* pf_rowids = nullptr;
+    if (parts > 1 || pre) {
         olap_status st = ensure_part(ctx, probe_scratch_bytes(ctx, t, n));
         if (st != OLAP_OK) return st;
+    }
+    if (pre) {
+        unsigned char* m = static_cast<unsigned char*>(ctx->part) + probe_part_bytes(ctx, n, parts);
+        pf_keys = reinterpret_cast<int64_t*>(m);
+        pf_rowids = reinterpret_cast<uint32_t*>(m + align256(n * 8));
+        pf = reinterpret_cast<PrefilterCtl*>(m + align256(n * 8) + align256(n * 4));
+        if (reinterpret_cast<unsigned char*>(pf + 1) > static_cast<unsigned char*>(ctx->part) + ctx->part_bytes)
+            return fail(ctx, OLAP_E_INVALID, "probe pre-filter scratch too small");
+    }
+    if (parts > 1) {
         unsigned char* m = static_cast<unsigned char*>(ctx->part);
         qgrid = static_cast<unsigned>(part_grid(ctx->device, ctx->sm_count));
         if (qgrid == 0) return fail(ctx, OLAP_E_CUDA, "partition kernel occupancy query failed");
@@ -382,7 +554,13 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
         q.pstart = q.cnt + static_cast<uint64_t>(qgrid) * parts;
         if (q.pstart + parts + 1 > reinterpret_cast<unsigned long long*>(m + ctx->part_bytes))
             return fail(ctx, OLAP_E_INVALID, "probe partition scratch too small");
+        q.pf = pf;
+        q.pf_keys = pf_keys;
+        q.pf_rowids = pf_rowids;
     }
+    ctx->last_probe_parts = parts;
+    ctx->last_probe_n = n;
+    ctx->last_probe_pf = pf;
     ctx->probe_timed = ctx->time_kernels;
     if (ctx->time_kernels && (e = cudaEventRecord(ctx->kev[4], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "timing event");
@@ -391,18 +569,29 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     if ((e = cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), s)) != cudaSuccess)
         return cuda_fail(ctx, e, "probe queue reset");
     ProbeArgs pa = a;
+    if (pre) {
+        const uint64_t bmask = t->bloom_blocks - 1;
+        join_prefilter_sample_kernel<<<1, PF_TPB, 0, s>>>(d_keys, n, t->bloom, bmask,
+                                                          ctx->opts.join_prefilter == OLAP_PREFILTER_ON, pf);
+        join_prefilter_kernel<<<ctx->sm_count * 4, PF_TPB, 0, s>>>(d_keys, d_rowids, n, t->bloom, bmask, pf,
+                                                                   pf_keys, pf_rowids);
+    }
+    const int64_t* direct_keys = pre ? pf_keys : nullptr;   // the direct probe reads the kept rows
+    const uint32_t* direct_rowids = pre ? pf_rowids : nullptr;
     if (parts > 1) {
         join_part_count_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
         join_part_scatter_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
         pa.keys = q.out_keys;
         pa.rowids = q.out_rowids;
+        direct_keys = nullptr;
+        direct_rowids = nullptr;
     }
     if (ctx->opts.join_bucket_loads == OLAP_LOADS_L1)
-        join_probe_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row);
+        join_probe_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row, pf, direct_keys, direct_rowids);
     else
-        join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row);
+        join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row, pf, direct_keys, direct_rowids);
     e = cudaGetLastError();
-    if (e == cudaSuccess) ctx->launches += parts > 1 ? 3 : 1;    // [count, scatter,] probe
+    if (e == cudaSuccess) ctx->launches += (parts > 1 ? 3 : 1) + (pre ? 2 : 0);   // [sample, filter,] [count, scatter,] probe
     if (e == cudaSuccess && ctx->time_kernels) e = cudaEventRecord(ctx->kev[5], s);
     return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "probe launch");
 }
@@ -436,7 +625,13 @@ olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* 
     const uint64_t buckets = next_pow2((want_slots + 1) / 2);
     if (buckets > (1ull << 32)) return fail(ctx, OLAP_E_NOMEM, "join table: more than 2^32 buckets");
     const size_t slot_bytes = buckets * 32;
-    const size_t bytes = slot_bytes + 256;
+    // Bloom filter for the pre-probe: about 16 bits per build row, for tables
+    // well above L2 (automatic) or every table with rows (forced on).
+    const uint64_t l2 = ctx->l2_bytes ? ctx->l2_bytes : (64ull << 20);
+    const bool with_bloom = n && (ctx->opts.join_prefilter == OLAP_PREFILTER_ON ||
+                                  (ctx->opts.join_prefilter == OLAP_PREFILTER_AUTO && slot_bytes > l2 / 2));
+    const uint64_t bloom_blocks = with_bloom ? next_pow2((n + 15) / 16) : 0;
+    const size_t bytes = slot_bytes + 256 + bloom_blocks * 32;
     if (!within_budget(ctx, bytes)) return fail(ctx, OLAP_E_NOMEM, "join table: device memory budget exceeded");
 
     // Key-only input: build keys (and row-ids) to the device.
@@ -476,8 +671,13 @@ olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* 
         delete t;
         return st;
     };
+    if (bloom_blocks) {
+        t->bloom = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(mem) + slot_bytes + 256);
+        t->bloom_blocks = bloom_blocks;
+    }
     e = cudaMemsetAsync(mem, 0xFF, slot_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(jc, 0, sizeof(JoinCtl), ctx->stream);
+    if (e == cudaSuccess && bloom_blocks) e = cudaMemsetAsync(t->bloom, 0, bloom_blocks * 32, ctx->stream);
     if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "join table init"));
     if (n) {
         const int grid = ctx->sm_count * 8;
@@ -488,6 +688,12 @@ olap_status olap_join_build(olap_ctx* ctx, const int64_t* keys, const uint32_t* 
         e = cudaGetLastError();
         if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "build launch"));
         ctx->launches += 2;
+        if (bloom_blocks) {
+            join_bloom_kernel<<<grid, JB_TPB, 0, ctx->stream>>>(dk, n, t->bloom, bloom_blocks - 1);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return bail(cuda_fail(ctx, e, "bloom launch"));
+            ctx->launches += 1;
+        }
     }
     JoinCtl hc;
     e = cudaMemcpyAsync(&hc, jc, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stream);
@@ -605,6 +811,28 @@ olap_status olap_join_probe_partitions(olap_ctx* ctx, const olap_join_table* tab
     olap_status st = check_join_table(ctx, table);
     if (st != OLAP_OK) return st;
     *parts = probe_parts(ctx, table, n);
+    return OLAP_OK;
+}
+
+olap_status olap_join_probe_info_last(olap_ctx* ctx, int* parts, int* prefiltered, uint64_t* rows_probed) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (!parts || !prefiltered || !rows_probed) return fail(ctx, OLAP_E_INVALID, "NULL output");
+    if (ctx->last_probe_parts == 0) return fail(ctx, OLAP_E_INVALID, "no probe has run on this context");
+    *parts = ctx->last_probe_parts;
+    *prefiltered = 0;
+    *rows_probed = ctx->last_probe_n;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "probe info");
+    if (ctx->last_probe_pf) {
+        PrefilterCtl c;
+        e = cudaMemcpy(&c, ctx->last_probe_pf, sizeof(c), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "probe info");
+        if (c.active) {
+            *prefiltered = 1;
+            *rows_probed = c.count;
+        }
+    }
     return OLAP_OK;
 }
 

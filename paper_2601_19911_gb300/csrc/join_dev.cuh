@@ -17,6 +17,8 @@ struct olap_join_table {
     uint64_t n_build = 0;
     double load = 0.0;
     size_t bytes = 0;
+    uint32_t* bloom = nullptr;        // blocked Bloom filter over the keys (NULL: none)
+    uint64_t bloom_blocks = 0;        // 32-byte blocks, a power of two
 };
 
 namespace olap {
@@ -59,6 +61,42 @@ __device__ __forceinline__ uint32_t ld_stream_u32(const void* p) {
 __device__ __forceinline__ void st_stream_pair(uint2* p, uint2 v) {
     asm volatile("st.global.cs.v2.u32 [%0], {%1, %2};" ::"l"(p), "r"(v.x), "r"(v.y) : "memory");
 }
+
+// Blocked Bloom filter (Putze, Sanders & Singler, "Cache-, hash- and
+// space-efficient Bloom filters", WEA 2007): every key maps to one 32-byte
+// block (one sector, one load) and sets one bit in each of the block's eight
+// 32-bit words.  The block comes from bits 40..63 of fmix64(key), which the
+// table's bucket index (the low bits) does not use; the eight bit positions
+// come from 40 bits of a second hash, fmix64 of the complemented key.
+constexpr int BLOOM_WORDS = 8;
+
+__device__ __forceinline__ uint64_t bloom_block(uint64_t key, uint64_t bmask) {
+    return (fmix64(key) >> 40) & bmask;
+}
+__device__ __forceinline__ uint32_t bloom_bit(uint64_t g, int w) {
+    return 1u << static_cast<uint32_t>((g >> (5 * w)) & 31u);
+}
+// Whether `key` may be among the filter's keys (no false negatives).
+__device__ __forceinline__ bool bloom_maybe(const uint32_t* bloom, uint64_t bmask, uint64_t key) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(bloom + bloom_block(key, bmask) * BLOOM_WORDS);
+    uint64_t a, b, c, d;
+    asm("ld.global.cg.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+    const uint64_t g = fmix64(~key);
+    const uint64_t want01 = static_cast<uint64_t>(bloom_bit(g, 0)) | (static_cast<uint64_t>(bloom_bit(g, 1)) << 32);
+    const uint64_t want23 = static_cast<uint64_t>(bloom_bit(g, 2)) | (static_cast<uint64_t>(bloom_bit(g, 3)) << 32);
+    const uint64_t want45 = static_cast<uint64_t>(bloom_bit(g, 4)) | (static_cast<uint64_t>(bloom_bit(g, 5)) << 32);
+    const uint64_t want67 = static_cast<uint64_t>(bloom_bit(g, 6)) | (static_cast<uint64_t>(bloom_bit(g, 7)) << 32);
+    return (a & want01) == want01 && (b & want23) == want23 && (c & want45) == want45 && (d & want67) == want67;
+}
+
+// Device-side state of one probe's Bloom pre-probe: whether the rows were
+// filtered, and how many passed.  The stages after the filter read it, so the
+// decision never travels through the host.
+struct PrefilterCtl {
+    int active;
+    int pad;
+    unsigned long long count;
+};
 
 struct ProbeArgs {
     const int64_t* keys;

@@ -33,6 +33,7 @@ EXPORTS = [
     "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last", "olap_topk_rows",
     "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_ctx_launches", "olap_autotune",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_probe_partitions",
+    "olap_join_probe_info_last",
     "olap_join_table_info", "olap_join_free",
     "olap_gate_calibrate", "olap_gate_estimate",
     "olap_batch_create", "olap_batch_run", "olap_batch_run_per_query", "olap_batch_errors", "olap_batch_free",
@@ -45,6 +46,7 @@ FIT_ORDINARY, FIT_RELATIVE = 0, 1
 FILTER_AUTO, FILTER_BULK, FILTER_REGS = 0, 1, 2
 LOADS_AUTO, LOADS_L1, LOADS_L2_ONLY = 0, 1, 2
 HOST_AUTO, HOST_STAGED = 0, 1
+PREFILTER_AUTO, PREFILTER_OFF, PREFILTER_ON = 0, 1, 2
 NOALLOC_MAX_N = 1 << 24
 NOALLOC_MAX_K = 4096
 
@@ -75,6 +77,8 @@ class olap_opts(ctypes.Structure):
         ("host_access", ctypes.c_int),
         ("batch_overlap", ctypes.c_int),
         ("batch_topk_ctas_per_sm", ctypes.c_int),
+        ("join_prefilter", ctypes.c_int),
+        ("staging_threads", ctypes.c_int),
     ]
 
 
@@ -226,6 +230,9 @@ def load(path: str | None = None):
         lib.olap_join_probe_async.argtypes = [vp, vp, vp, vp, u64, vp, u64, vp, vp]
         lib.olap_join_probe_partitions.restype = i32
         lib.olap_join_probe_partitions.argtypes = [vp, vp, u64, ctypes.POINTER(ctypes.c_int)]
+        lib.olap_join_probe_info_last.restype = i32
+        lib.olap_join_probe_info_last.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(u64)]
         lib.olap_join_table_info.restype = i32
         lib.olap_join_table_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
         lib.olap_join_free.restype = None
@@ -345,12 +352,13 @@ class Context:
                  topk_filter: int = FILTER_AUTO, topk_tile_bytes: int = 0, topk_stages: int = 0,
                  topk_ctas_per_sm: int = 0, join_partitions: int = 0, join_bucket_loads: int = 0,
                  l2_fetch_bytes: int = 0, topk_digit_bits: int = 0, block_threads: int = 0,
-                 host_access: int = 0, batch_overlap: int = 0, batch_topk_ctas_per_sm: int = 0):
+                 host_access: int = 0, batch_overlap: int = 0, batch_topk_ctas_per_sm: int = 0,
+                 join_prefilter: int = PREFILTER_AUTO, staging_threads: int = 0):
         self.lib = load()
         opts = olap_opts(device, stream, mem_budget_bytes, margin_ms, block_threads, load_factor, staging_bytes,
                          topk_filter, topk_tile_bytes, topk_stages, topk_ctas_per_sm, join_partitions,
                          join_bucket_loads, l2_fetch_bytes, topk_digit_bits, host_access, batch_overlap,
-                         batch_topk_ctas_per_sm)
+                         batch_topk_ctas_per_sm, join_prefilter, staging_threads)
         h = ctypes.c_void_p()
         st = self.lib.olap_ctx_create(ctypes.byref(opts), ctypes.byref(h))
         if st != OK:
@@ -477,6 +485,14 @@ class Context:
         parts = ctypes.c_int()
         self.check(self.lib.olap_join_probe_partitions(self.h, table.h, int(n), ctypes.byref(parts)))
         return parts.value
+
+    def join_probe_info(self) -> dict:
+        """olap_join_probe_info_last: partitions, whether the Bloom pre-probe
+        dropped rows, and the rows left to probe, of the last probe."""
+        parts, pf, rows = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64()
+        self.check(self.lib.olap_join_probe_info_last(self.h, ctypes.byref(parts), ctypes.byref(pf),
+                                                      ctypes.byref(rows)))
+        return {"parts": parts.value, "prefiltered": bool(pf.value), "rows_probed": rows.value}
 
     def batch(self, items) -> "Batch":
         """olap_batch_create from a list of olap_batch_item."""

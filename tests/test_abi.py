@@ -48,7 +48,8 @@ def test_no_cpu_fallback_without_gpu(lib):
                                          ("load_factor", 0.95), ("topk_filter", 7), ("join_bucket_loads", 3),
                                          ("l2_fetch_bytes", 48), ("topk_digit_bits", 7), ("topk_digit_bits", 13),
                                          ("block_threads", 384), ("host_access", 2), ("batch_overlap", 2),
-                                         ("batch_topk_ctas_per_sm", 3)])
+                                         ("batch_topk_ctas_per_sm", 3), ("join_prefilter", 3),
+                                         ("join_prefilter", -1), ("staging_threads", -1), ("staging_threads", 65)])
 def test_bad_options_are_rejected_before_any_device_call(lib, field, value):
     opts = olap.olap_opts()
     setattr(opts, field, value)

@@ -200,6 +200,73 @@ def test_bucket_load_paths(loads, parts):
         c.close()
 
 
+@pytest.mark.parametrize("parts", [1, 8])
+def test_prefilter_forced_matches_oracle(parts):
+    """The Bloom pre-probe (Sec. III-B, "bloom-filter/partitioned hash")
+    forced on, before a direct and a partitioned probe: the same pair
+    multiset as the oracle; it drops rows (hit rate 0.1) but never a match,
+    and keeps probe rows with the empty-marker key for the side list."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0, join_partitions=parts, join_prefilter=olap.PREFILTER_ON)
+    try:
+        for mult, dist, hit, n in (("unique", "uniform", 0.1, 600_001), ("mult14", "zipf", 0.5, 300_007),
+                                   ("unique", "uniform", 1.0, 100_000)):
+            b = datagen.join_build(120_011, mult, seed=31)
+            p = datagen.join_probe(n, b, hit, dist, seed=31)
+            assert _check(c, b.keys, p.keys) == p.expected_pairs(b)
+            info = c.join_probe_info()
+            assert info["prefiltered"] and info["parts"] == parts
+            hits = int(p.hit.sum())
+            assert hits <= info["rows_probed"] <= hits + n // 50       # few false positives
+        b = datagen.join_build(50_000, "mult14", seed=32)
+        p = datagen.join_probe(200_000, b, 0.3, "zipf", seed=32)
+        br = (datagen.splitmix64(5, b.keys.shape[0]) >> np.uint64(33)).astype(np.uint32)
+        pr = (datagen.splitmix64(6, p.keys.shape[0]) >> np.uint64(33)).astype(np.uint32)
+        _check(c, b.keys, p.keys, br, pr)
+        _check(c, b.keys, p.keys, br, pr, device=False)
+        rng = np.random.default_rng(33)
+        alphabet = np.array([I64_MIN, I64_MAX, 0, -1, 1, -2], dtype=np.int64)
+        bk = alphabet[rng.integers(0, len(alphabet), 3000)]
+        for npr in (1, 5, 63, 4097, 20_000):
+            _check(c, bk, alphabet[rng.integers(0, len(alphabet), npr)])
+        _check(c, np.array([5, -1, 5], dtype=np.int64), np.array([-1, 7, -1, 5], dtype=np.int64))
+    finally:
+        c.close()
+
+
+def test_prefilter_auto_decides_on_the_device():
+    """Automatic mode: a table above L2 carries a filter; the pre-probe's
+    sample drops rows at hit rate 0.1 and leaves them at 0.9, and the pairs
+    match the oracle either way."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0)
+    try:
+        b = datagen.join_build(1 << 22, "unique", seed=34)
+        t = c.join_build(torch.from_numpy(b.keys).cuda())
+        for hit, want in ((0.1, True), (0.9, False)):
+            p = datagen.join_probe((1 << 21) + 7, b, hit, "uniform", seed=34)
+            need = p.expected_pairs(b)
+            out = torch.empty((need, 2), dtype=torch.int32, device="cuda")
+            got = c.join_probe(t, torch.from_numpy(p.keys).cuda(), out=out)
+            info = c.join_probe_info()
+            assert info["prefiltered"] == want
+            np.testing.assert_array_equal(packed(got.cpu().numpy().view(np.uint32)), oracle.join(b.keys, p.keys))
+        t.free()
+    finally:
+        c.close()
+    off = olap.Context(0, join_prefilter=olap.PREFILTER_OFF)
+    try:
+        t = off.join_build(b.keys)
+        p = datagen.join_probe(1 << 21, b, 0.1, "uniform", seed=35)
+        off.join_probe(t, p.keys)
+        assert not off.join_probe_info()["prefiltered"]
+        t.free()
+    finally:
+        off.close()
+
+
 _BUILDS = {}
 
 
@@ -235,6 +302,7 @@ def test_full_size(ctx, mult, dist, hit):
     ctx.sync()
     t.free()
     assert int(cnt.item()) == need
+    assert ctx.join_probe_info()["prefiltered"] == (hit < 0.5)      # the automatic pre-probe's choice
     pr = out[:, 0].to(torch.int64) & 0xFFFFFFFF
     br = out[:, 1].to(torch.int64) & 0xFFFFFFFF
     assert bool((pr < (1 << 28)).all()) and bool((br < (1 << 24)).all())
