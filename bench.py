@@ -522,35 +522,53 @@ def gate_leg(args, ctx, torch):
                                     max(t_all - t_in, 0.0), t_all))
     del dev
     table.free()
+    host_split = {op: host.parallel_from(op) for op in (olap.OP_TOPK, olap.OP_PROBE)}
     host.close()
     torch.cuda.empty_cache()
     result = {}
     for op, name in ((olap.OP_TOPK, "topk_k100"), (olap.OP_PROBE, "probe_hit0.9")):
         r = rows[op]
         cal = r[1::2]                                          # calibration points
-        cols = list(zip(*[x[:8] for x in cal]))
         gn = [x[0] for x in r]
+        mpp = r[-1][3] / r[-1][0]                              # pairs per probe
+
+        split = float(host_split[op])
+
+        def fit(points, margin, cpu_split):
+            m = olap.gate_calibrate(op, *list(zip(*[x[:8] for x in points])), margin_ms=margin,
+                                    weighting=olap.FIT_RELATIVE, cpu_split_n=cpu_split)
+            if op == olap.OP_TOPK:
+                return m, olap.gate_estimate(m, op, 1 << 20, kk, 8.0 * (1 << 20), kk, 8.0).n_star
+            return m, olap.gate_estimate(m, op, 1 << 20, 1.0 + mpp, 8.0 * (1 << 20), mpp * (1 << 20), 8.0,
+                                         mpp).n_star
+
         per_margin = {}
         for margin in (0.0, 5.0, 10.0):
-            m = olap.gate_calibrate(op, *cols, margin_ms=margin, weighting=olap.FIT_RELATIVE)
+            # the CPU cost per regime of the host engine (serial below the
+            # size it goes parallel at, parallel above), and one fit over
+            # everything for comparison
+            _, nstar_one = fit(cal, margin, 0.0)
+            m, nstar = fit(cal, margin, split)
             if op == olap.OP_TOPK:
-                nstar = olap.gate_estimate(m, op, 1 << 20, kk, 8.0 * (1 << 20), kk, 8.0).n_star
                 dec = [bool(olap.gate_estimate(m, op, x[0], kk, x[2], x[3], 8.0).offload) for x in r]
             else:
-                mpp = r[-1][3] / r[-1][0]                      # pairs per probe
-                nstar = olap.gate_estimate(m, op, 1 << 20, 1.0 + mpp, 8.0 * (1 << 20), mpp * (1 << 20), 8.0,
-                                           mpp).n_star
                 dec = [bool(olap.gate_estimate(m, op, x[0], x[1], x[2], x[3], 8.0, mpp).offload) for x in r]
             measured = _crossover(gn, [x[4] - x[8] - margin for x in r])
             per_margin[f"{margin:g}ms"] = {
                 "n_star_predicted": int(nstar), "crossover_measured": measured,
                 "rel_error": (abs(nstar - measured) / measured) if measured > 0 and nstar > 0 else None,
+                "n_star_one_regime_fit": int(nstar_one),
+                "rel_error_one_regime_fit": (abs(nstar_one - measured) / measured)
+                if measured > 0 and nstar_one > 0 else None,
                 "offload_at_n": dec}
-        result[name] = {"n": gn, "t_host_ms": [x[4] for x in r], "t_gpu_e2e_ms": [x[8] for x in r],
+        result[name] = {"cpu_split_n": split, "n": gn, "t_host_ms": [x[4] for x in r],
+                        "t_gpu_e2e_ms": [x[8] for x in r],
                         "t_tx_ms": [x[5] for x in r], "t_kernel_ms": [x[6] for x in r],
                         "t_post_ms": [x[7] for x in r], "margins": per_margin}
     return {"metric": "gate break-even: predicted N* vs measured crossover", "unit": "relative error",
-            "grid_points": len(ns), "calibration": "odd grid points, 1/y^2-weighted least squares",
+            "grid_points": len(ns),
+            "calibration": "odd grid points, 1/y^2-weighted least squares, the CPU cost fitted per regime of the "
+                           "host engine (below and above the size it goes parallel at)",
             "reps": args.gate_reps, "host_threads": args.serve_cpu_workers, **result}
 
 
@@ -675,7 +693,8 @@ def serving_leg(args, ctx, torch):
     for op, rows in samples.items():
         cols = list(zip(*rows))
         models[op] = olap.gate_calibrate(op, *cols, margin_ms=args.serve_margin, weighting=olap.FIT_RELATIVE,
-                                         topk_cpu=olap.CPU_MAX if args.serve_topk_cpu == "max" else 0)
+                                         topk_cpu=olap.CPU_MAX if args.serve_topk_cpu == "max" else 0,
+                                         cpu_split_n=float(host.parallel_from(op)))
     # -- arrival rate from the closed-loop always-on throughput -----------------
     reqs, keep = make_requests(args.serve_requests, seed=4)
     budget = max(1, args.serve_budget_gb * (1 << 30) - tbytes)

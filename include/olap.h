@@ -466,6 +466,11 @@ typedef struct {
     int topk_cpu;                 /* Top-K: 0 => the form with the smaller residual;
                                      OLAP_CPU_MAX => both forms, the larger estimate */
     int pad;
+    double cpu_split_n;           /* 0 => one CPU fit over every sample.  > 0 => the host engine
+                                     changes regime at this size (it goes parallel, say): the CPU
+                                     cost is fitted on its own over the samples with n < cpu_split_n
+                                     and over those with n >= cpu_split_n (each side needs at least
+                                     two samples of distinct x, else OLAP_E_INVALID) */
 } olap_gate_samples;
 
 typedef struct {
@@ -476,8 +481,13 @@ typedef struct {
     double e, f;                  /* kernel: e * N + f */
     double g, h;                  /* post-processing: g * rows + h */
     double margin_ms;
-    double rss_nlogn, rss_nk;     /* Top-K: residual sums of squares of both CPU forms */
+    double rss_nlogn, rss_nk;     /* Top-K: residual sums of squares of both CPU forms (summed over
+                                     both regimes when split) */
     double a2, b2;                /* OLAP_CPU_MAX: the N*K form (a, b hold the N*log2 N form) */
+    double split_n;               /* 0 => one regime; else a, b (a2, b2) hold the CPU fit for
+                                     n < split_n and a_hi, b_hi (a2_hi, b2_hi) the fit for
+                                     n >= split_n, both in cpu_form */
+    double a_hi, b_hi, a2_hi, b2_hi;
 } olap_gate_model;
 
 typedef struct {

@@ -30,6 +30,12 @@ Readings where it is open (kept identical in the library's contract):
   * N* is the smallest integer N in [1, 2^34] with C_cpu(N) - C_gpu(N) >
     margin, by bisection; 1 if that already holds at N = 1, 0 ("none") if it
     does not hold at 2^34.
+  * the CPU engine may change regime at a known size (a host engine that goes
+    parallel above some N): then the CPU cost is fitted on its own over the
+    samples below that size and over those at or above it, each estimate
+    uses its size's regime, and N* is searched in the lower regime first,
+    then in the upper one from its first size on (the gain is taken to grow
+    with N within each regime, not across the step between them).
 """
 from __future__ import annotations
 
@@ -86,44 +92,74 @@ def cpu_x(form, n, k_or_m):
 
 
 class Model:
-    def __init__(self, op, cpu_form, a, b, c, d, e, f, g, h, margin_ms, a2=0.0, b2=0.0):
+    """Cost model.  With split_n > 0, (a, b, a2, b2) is the CPU fit for
+    N < split_n and (a_hi, b_hi, a2_hi, b2_hi) the fit for N >= split_n."""
+
+    def __init__(self, op, cpu_form, a, b, c, d, e, f, g, h, margin_ms, a2=0.0, b2=0.0, split_n=0.0,
+                 a_hi=0.0, b_hi=0.0, a2_hi=0.0, b2_hi=0.0):
         self.op, self.cpu_form = op, cpu_form
         self.a2, self.b2 = a2, b2
         self.a, self.b, self.c, self.d = a, b, c, d
         self.e, self.f, self.g, self.h = e, f, g, h
         self.margin_ms = margin_ms
+        self.split_n = split_n
+        self.a_hi, self.b_hi, self.a2_hi, self.b2_hi = a_hi, b_hi, a2_hi, b2_hi
+
+
+def _cpu_fits(op, n, k_or_m, t_cpu, wt):
+    """CPU fits of one regime: {form: (slope, intercept)} and {form: rss}."""
+    forms = (CPU_NLOGN, CPU_NK) if op == TOPK else (CPU_NM,)
+    xs = {f: [cpu_x(f, ni, ki) for ni, ki in zip(n, k_or_m)] for f in forms}
+    fits = {f: ols(xs[f], t_cpu, wt) for f in forms}
+    return fits, {f: rss(xs[f], t_cpu, *fits[f], wt) for f in forms}
 
 
 def calibrate(op, n, k_or_m, tx_bytes, out_rows, t_cpu, t_tx, t_ker, t_post, margin_ms=0.0,
-              weighting=ORDINARY, topk_cpu=0):
-    """Fit every cost term from measured samples (all times in ms)."""
+              weighting=ORDINARY, topk_cpu=0, cpu_split_n=0.0):
+    """Fit every cost term from measured samples (all times in ms); with
+    cpu_split_n > 0 the CPU cost is fitted separately on the samples with
+    N < cpu_split_n and on the others."""
     wt = weighting
+    n, k_or_m, t_cpu = (np.asarray(v, dtype=np.float64) for v in (n, k_or_m, t_cpu))
+    if cpu_split_n > 0.0:
+        below = n < cpu_split_n
+        parts = [below, ~below]
+    else:
+        parts = [np.ones(n.shape[0], dtype=bool)]
+    regimes = [_cpu_fits(op, n[p], k_or_m[p], t_cpu[p], wt) for p in parts]
     if op == TOPK:
-        xs = {f: [cpu_x(f, ni, ki) for ni, ki in zip(n, k_or_m)] for f in (CPU_NLOGN, CPU_NK)}
-        fits = {f: ols(xs[f], t_cpu, wt) for f in xs}
-        res = {f: rss(xs[f], t_cpu, *fits[f], wt) for f in xs}
-        form = CPU_NLOGN if res[CPU_NLOGN] <= res[CPU_NK] else CPU_NK
+        r_nlogn = sum(r[CPU_NLOGN] for _, r in regimes)
+        r_nk = sum(r[CPU_NK] for _, r in regimes)
+        form = CPU_NLOGN if r_nlogn <= r_nk else CPU_NK
         if topk_cpu == CPU_MAX:
             form = CPU_MAX
     else:
         form = CPU_NM
-        fits = {form: ols([cpu_x(form, ni, mi) for ni, mi in zip(n, k_or_m)], t_cpu, wt)}
-    a2 = b2 = 0.0
-    if form == CPU_MAX:
-        (a, b), (a2, b2) = fits[CPU_NLOGN], fits[CPU_NK]
-    else:
-        a, b = fits[form]
+
+    def coef(fits):
+        if form == CPU_MAX:
+            return fits[CPU_NLOGN] + fits[CPU_NK]
+        return fits[form] + (0.0, 0.0)
+
+    a, b, a2, b2 = coef(regimes[0][0])
+    a_hi = b_hi = a2_hi = b2_hi = 0.0
+    if cpu_split_n > 0.0:
+        a_hi, b_hi, a2_hi, b2_hi = coef(regimes[1][0])
     c, d = ols(tx_bytes, t_tx, wt)
     e, f = ols(n, t_ker, wt)
     g, h = ols(out_rows, t_post, wt)
-    return Model(op, form, a, b, c, d, e, f, g, h, margin_ms, a2, b2)
+    return Model(op, form, a, b, c, d, e, f, g, h, margin_ms, a2, b2, float(cpu_split_n), a_hi, b_hi, a2_hi, b2_hi)
 
 
 def costs(m: Model, n, k_or_m, tx_bytes, out_rows):
-    if m.cpu_form == CPU_MAX:
-        c_cpu = max(m.a * cpu_x(CPU_NLOGN, n, k_or_m) + m.b, m.a2 * cpu_x(CPU_NK, n, k_or_m) + m.b2)
+    if m.split_n > 0.0 and float(n) >= m.split_n:
+        a, b, a2, b2 = m.a_hi, m.b_hi, m.a2_hi, m.b2_hi
     else:
-        c_cpu = m.a * cpu_x(m.cpu_form, n, k_or_m) + m.b
+        a, b, a2, b2 = m.a, m.b, m.a2, m.b2
+    if m.cpu_form == CPU_MAX:
+        c_cpu = max(a * cpu_x(CPU_NLOGN, n, k_or_m) + b, a2 * cpu_x(CPU_NK, n, k_or_m) + b2)
+    else:
+        c_cpu = a * cpu_x(m.cpu_form, n, k_or_m) + b
     c_tx = m.c * float(tx_bytes) + m.d
     c_ker = m.e * float(n) + m.f
     c_post = m.g * float(out_rows) + m.h
@@ -145,13 +181,9 @@ def gain(m: Model, n, k_or_m, bytes_per_row, out_per_row, out_fixed):
     return c_cpu - (c_tx + c_ker + c_post) - m.margin_ms
 
 
-def n_star(m: Model, k_or_m, bytes_per_row, out_per_row=0.0, out_fixed=None):
-    g = lambda nn: gain(m, nn, k_or_m, bytes_per_row, out_per_row, out_fixed)
-    if g(1) > 0.0:
-        return 1
-    if not g(N_STAR_HI) > 0.0:
-        return 0
-    lo, hi = 1, N_STAR_HI
+def _first_positive(g, lo, hi):
+    """Bisection for the smallest n in (lo, hi] with g(n) > 0, given
+    g(lo) <= 0 < g(hi)."""
     while hi - lo > 1:
         mid = (lo + hi) // 2
         if g(mid) > 0.0:
@@ -159,3 +191,22 @@ def n_star(m: Model, k_or_m, bytes_per_row, out_per_row=0.0, out_fixed=None):
         else:
             lo = mid
     return hi
+
+
+def n_star(m: Model, k_or_m, bytes_per_row, out_per_row=0.0, out_fixed=None):
+    g = lambda nn: gain(m, nn, k_or_m, bytes_per_row, out_per_row, out_fixed)
+    if g(1) > 0.0:
+        return 1
+    start = 1
+    if m.split_n > 1.0:
+        s = min(int(math.ceil(m.split_n)), N_STAR_HI)      # first size of the upper regime
+        if s >= 2 and g(s - 1) > 0.0:
+            return _first_positive(g, 1, s - 1)
+        if s >= N_STAR_HI:
+            return N_STAR_HI if g(N_STAR_HI) > 0.0 else 0
+        if g(s) > 0.0:
+            return s
+        start = s
+    if not g(N_STAR_HI) > 0.0:
+        return 0
+    return _first_positive(g, start, N_STAR_HI)

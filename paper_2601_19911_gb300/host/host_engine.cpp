@@ -327,6 +327,14 @@ void olap_host_engine_extract(void* eng, const void* rows, uint64_t n, uint32_t 
     });
 }
 
+// Smallest request size the engine runs on more than one thread (0 if it
+// never does): where its cost changes regime, for the gate's CPU model.
+uint64_t olap_host_engine_parallel_from(void* eng, int op) {
+    const Engine* E = static_cast<const Engine*>(eng);
+    if (E->threads < 2) return 0;
+    return 2 * (op == OLAP_OP_TOPK ? TOPK_CHUNK : PROBE_CHUNK);
+}
+
 void olap_host_engine_free(void* eng) { delete static_cast<Engine*>(eng); }
 
 }  // extern "C"

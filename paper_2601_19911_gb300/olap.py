@@ -89,13 +89,14 @@ class olap_gate_samples(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("weighting", ctypes.c_int), ("count", ctypes.c_uint64), ("n", _dp),
                 ("k_or_m", _dp),
                 ("tx_bytes", _dp), ("out_rows", _dp), ("t_cpu_ms", _dp), ("t_tx_ms", _dp),
-                ("t_ker_ms", _dp), ("t_post_ms", _dp), ("topk_cpu", ctypes.c_int), ("pad", ctypes.c_int)]
+                ("t_ker_ms", _dp), ("t_post_ms", _dp), ("topk_cpu", ctypes.c_int), ("pad", ctypes.c_int),
+                ("cpu_split_n", ctypes.c_double)]
 
 
 class olap_gate_model(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("cpu_form", ctypes.c_int)] + \
         [(nm, ctypes.c_double) for nm in ("a", "b", "c", "d", "e", "f", "g", "h", "margin_ms", "rss_nlogn",
-                                          "rss_nk", "a2", "b2")]
+                                          "rss_nk", "a2", "b2", "split_n", "a_hi", "b_hi", "a2_hi", "b2_hi")]
 
 
 class olap_gate_query(ctypes.Structure):
@@ -656,8 +657,10 @@ def topk_noalloc(d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=
 # ---------------------------------------------------------------------------
 
 def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_ker_ms, t_post_ms,
-                   margin_ms: float = 0.0, weighting: int = FIT_ORDINARY, topk_cpu: int = 0) -> olap_gate_model:
-    """olap_gate_calibrate over equal-length sample sequences (times in ms)."""
+                   margin_ms: float = 0.0, weighting: int = FIT_ORDINARY, topk_cpu: int = 0,
+                   cpu_split_n: float = 0.0) -> olap_gate_model:
+    """olap_gate_calibrate over equal-length sample sequences (times in ms);
+    cpu_split_n > 0 fits the CPU cost separately below and above that size."""
     lib = load()
     cols = [np.ascontiguousarray(np.asarray(c, dtype=np.float64)) for c in
             (n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_ker_ms, t_post_ms)]
@@ -665,7 +668,7 @@ def gate_calibrate(op: int, n, k_or_m, tx_bytes, out_rows, t_cpu_ms, t_tx_ms, t_
     if any(c.shape[0] != cnt for c in cols):
         raise ValueError("every sample sequence must have the same length")
     ptrs = [c.ctypes.data_as(_dp) for c in cols]
-    smp = olap_gate_samples(op, weighting, cnt, *ptrs, topk_cpu, 0)
+    smp = olap_gate_samples(op, weighting, cnt, *ptrs, topk_cpu, 0, float(cpu_split_n))
     m = olap_gate_model()
     st = lib.olap_gate_calibrate(ctypes.byref(smp), float(margin_ms), ctypes.byref(m))
     if st != OK:
@@ -707,8 +710,15 @@ class HostEngine:
         self.lib.olap_host_engine_extract.restype = None
         self.lib.olap_host_engine_extract.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
                                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
+        self.lib.olap_host_engine_parallel_from.restype = ctypes.c_uint64
+        self.lib.olap_host_engine_parallel_from.argtypes = [ctypes.c_void_p, ctypes.c_int]
         self.h = self.lib.olap_host_engine_create(threads)
         self._keep = []
+
+    def parallel_from(self, op: int) -> int:
+        """Smallest request size the engine splits over threads (0: never):
+        where its cost changes regime."""
+        return int(self.lib.olap_host_engine_parallel_from(self.h, int(op)))
 
     def add_table(self, keys: np.ndarray, rowids: np.ndarray | None = None) -> int:
         keys = np.ascontiguousarray(keys, dtype=np.int64)

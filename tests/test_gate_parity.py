@@ -68,12 +68,50 @@ def test_calibrate_and_decide_match_oracle(op, form, topk_cpu, seed, weighting):
             assert abs(int(d.n_star) - ns) <= max(1, ns * 1e-9)
 
 
+@pytest.mark.parametrize("op,form,topk_cpu", [(gate.TOPK, gate.CPU_NLOGN, 0), (gate.TOPK, gate.CPU_NK, 0),
+                                              (gate.PROBE, gate.CPU_NM, 0), (gate.TOPK, gate.CPU_NLOGN, gate.CPU_MAX)])
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("weighting", [gate.ORDINARY, gate.RELATIVE])
+def test_two_regime_fit_matches_oracle(op, form, topk_cpu, seed, weighting):
+    """A CPU engine with two regimes (serial below 131072 rows, parallel
+    above, as the host engine): the library's per-regime fits, decisions and
+    N* against the oracle's."""
+    rng = np.random.default_rng(100 + seed)
+    n, km, tx, out, t_cpu, t_tx, t_ker, t_post = _noisy_samples(rng, op, form, count=30)
+    split = 131072.0
+    t_cpu = np.where(n < split, t_cpu, t_cpu * 0.15 + 0.2)     # the parallel regime: cheaper slope, a hand-off
+    smp = (n, km, tx, out, t_cpu, t_tx, t_ker, t_post)
+    for margin in (0.0, 5.0):
+        want = gate.calibrate(op, *smp, margin_ms=margin, weighting=weighting, topk_cpu=topk_cpu,
+                              cpu_split_n=split)
+        got = olap.gate_calibrate(op, *smp, margin_ms=margin, weighting=weighting, topk_cpu=topk_cpu,
+                                  cpu_split_n=split)
+        assert got.cpu_form == want.cpu_form and got.split_n == split
+        for nm in ("a", "b", "c", "d", "e", "f", "g", "h", "a2", "b2", "a_hi", "b_hi", "a2_hi", "b2_hi"):
+            assert math.isclose(getattr(got, nm), getattr(want, nm), rel_tol=1e-9, abs_tol=1e-15), nm
+        for nq in (1000, 50_000, 131_071, 131_072, 10**6, 10**8):
+            kq = 100.0 if op == gate.TOPK else 1.9
+            outq = min(kq, nq) if op == gate.TOPK else nq * (kq - 1.0)
+            d = olap.gate_estimate(got, op, nq, kq, 8.0 * nq, outq, 8.0, kq - 1.0)
+            c = gate.costs(want, nq, kq, 8.0 * nq, outq)
+            assert math.isclose(d.c_cpu, c[0], rel_tol=1e-9, abs_tol=1e-12)
+            ns = gate.n_star(want, kq, 8.0, kq - 1.0, kq if op == gate.TOPK else None)
+            assert abs(int(d.n_star) - ns) <= max(1, ns * 1e-9)
+
+
+def test_two_regime_needs_two_samples_per_side():
+    n = [1e3, 2e3, 5e3, 1e6]
+    z = [0.1] * 4
+    with pytest.raises(olap.OlapError):
+        olap.gate_calibrate(gate.TOPK, n, [10.0] * 4, n, [10.0] * 4, z, z, z, z, cpu_split_n=1e5)
+
+
 def test_exact_knife_edge_is_not_offloaded():
     # dyadic constants: C_cpu - C_gpu equals the margin exactly (the paper's
     # "exceeds" is strict).  n=8, M=2: C_cpu = 0.5*16 + 1 = 9; C_tx = 0.25*8 +
     # 0.5 = 2.5; C_ker = 0.125*8 = 1; C_post = 0 -> gain 5.5.
     model = olap.olap_gate_model(gate.PROBE, gate.CPU_NM, 0.5, 1.0, 0.25, 0.5, 0.125, 0.0, 0.0, 0.0, 5.5, 0.0, 0.0,
-                                 0.0, 0.0)
+                                 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
     d = olap.gate_estimate(model, gate.PROBE, 8, 2.0, 8.0, 0.0)
     assert d.gain_ms == 5.5 and d.offload == 0
     model.margin_ms = 5.25

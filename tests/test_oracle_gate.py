@@ -125,3 +125,82 @@ def test_max_form_keeps_both_fits_and_takes_the_larger():
     for ni, ki in ((1e3, 1.0), (1e6, 1e5), (1e8, 10.0), (5e4, 5e4)):
         c_cpu = gate.costs(m, ni, ki, 8 * ni, ki)[0]
         assert math.isclose(c_cpu, max(m.a * ni * math.log2(ni) + m.b, m.a2 * ni * ki + m.b2), rel_tol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Two CPU regimes (a host engine that goes parallel above a size)
+# ---------------------------------------------------------------------------
+
+def _two_regime_samples(split, lo, hi, form=gate.CPU_NLOGN):
+    n = np.unique(np.floor(np.logspace(3, 8, 24)).astype(np.int64))
+    kk = np.array([10, 100, 1000, 37] * 6, dtype=np.int64)[: n.shape[0]]
+    x = n * np.log2(n) if form == gate.CPU_NLOGN else n * kk
+    t_cpu = np.where(n < split, lo[0] * x + lo[1], hi[0] * x + hi[1])
+    tx = 8 * n
+    out = np.minimum(kk, n)
+    return n, kk, tx, out, t_cpu, 2e-9 * tx + 0.03, 1e-7 * n + 0.01, 1e-6 * out + 0.002
+
+
+@pytest.mark.parametrize("form", [gate.CPU_NLOGN, gate.CPU_NK])
+def test_two_regimes_recover_each_regime(form):
+    """Exact timings that follow one line below the split and another above
+    it: each regime's coefficients come back exactly, in the right form."""
+    lo, hi = (6e-6, 0.002), (4e-7, 0.2)
+    smp = _two_regime_samples(131072, lo, hi, form)
+    for wt in (gate.ORDINARY, gate.RELATIVE):
+        m = gate.calibrate(gate.TOPK, *smp, weighting=wt, cpu_split_n=131072)
+        assert m.cpu_form == form and m.split_n == 131072
+        for got, want in ((m.a, lo[0]), (m.b, lo[1]), (m.a_hi, hi[0]), (m.b_hi, hi[1])):
+            assert math.isclose(got, want, rel_tol=1e-9, abs_tol=1e-12)
+        # below and above the split the estimate follows its own regime
+        assert math.isclose(gate.costs(m, 1e4, 10, 8e4, 10)[0],
+                            lo[0] * (1e4 * math.log2(1e4) if form == gate.CPU_NLOGN else 1e5) + lo[1],
+                            rel_tol=1e-9)
+        assert math.isclose(gate.costs(m, 1e7, 10, 8e7, 10)[0],
+                            hi[0] * (1e7 * math.log2(1e7) if form == gate.CPU_NLOGN else 1e8) + hi[1],
+                            rel_tol=1e-9)
+
+
+def test_two_regimes_one_line_is_no_split():
+    # timings on one line: the split changes nothing but where the fit is made
+    co = dict(a=3.1e-6, b=0.25, c=2.5e-9, d=0.04, e=1.5e-7, f=0.01, g=3e-6, h=0.002)
+    smp = _samples(**co, form=gate.CPU_NLOGN)
+    m0 = gate.calibrate(gate.TOPK, *smp)
+    m1 = gate.calibrate(gate.TOPK, *smp, cpu_split_n=1e5)
+    for nm in ("a", "b"):
+        assert math.isclose(getattr(m1, nm), getattr(m0, nm), rel_tol=1e-9)
+        assert math.isclose(getattr(m1, nm + "_hi"), getattr(m0, nm), rel_tol=1e-9)
+
+
+def _linear_two(split, lo, hi, margin=0.0):
+    # CPU a*N*K + b per regime; GPU C = 1e-8*8*N + 0.5 (transfer) + 0 + 0
+    return gate.Model(gate.TOPK, gate.CPU_NK, a=lo[0], b=lo[1], c=1e-8, d=0.5, e=0.0, f=0.0, g=0.0, h=0.0,
+                      margin_ms=margin, split_n=split, a_hi=hi[0], b_hi=hi[1])
+
+
+def test_two_regimes_n_star_in_the_lower_regime():
+    # root of a*K*N + b = 8e-8*N + 0.5 in the lower regime: N = (0.5 - b) / (a*K - 8e-8)
+    m = _linear_two(1e6, (1e-6, 0.0), (1e-9, 0.3))
+    k = 100
+    root = 0.5 / (1e-6 * k - 8e-8)
+    ns = gate.n_star(m, k, 8, out_fixed=k)
+    assert ns == math.floor(root) + 1 and ns < 1e6
+    assert gate.gain(m, ns, k, 8, 0.0, k) > 0.0 >= gate.gain(m, ns - 1, k, 8, 0.0, k)
+
+
+def test_two_regimes_n_star_at_the_step():
+    # the lower regime never pays; the upper one pays from its first size on
+    m = _linear_two(1e6, (0.0, 0.0), (1e-6, 10.0))
+    assert gate.n_star(m, 100, 8, out_fixed=100) == 1_000_000
+
+
+def test_two_regimes_n_star_in_the_upper_regime():
+    # neither the lower regime nor the step pays; the upper line crosses at
+    # N = (0.5 - b_hi) / (a_hi*K - 8e-8)
+    m = _linear_two(1000.5, (0.0, 0.0), (1e-9, -2.0))
+    k = 1000
+    root = (0.5 + 2.0) / (1e-9 * k - 8e-8)
+    ns = gate.n_star(m, k, 8, out_fixed=k)
+    assert ns == math.floor(root) + 1
+    assert gate.gain(m, ns, k, 8, 0.0, k) > 0.0 >= gate.gain(m, ns - 1, k, 8, 0.0, k)
+    assert gate.gain(m, 1000, k, 8, 0.0, k) <= 0.0 and gate.gain(m, 1001, k, 8, 0.0, k) <= 0.0
