@@ -242,11 +242,14 @@ def join_leg(args, ctx, torch, world):
     launches += ctx.launches() - l0
     kms = _kernel_pass(ctx, min(steps, 10), lambda: ctx.join_probe_async(table, dk, out, need, cnt))
     kern_ms = kms["join_probe_ms"]
-    # the partitioned probe is three launches (count, scatter, probe), the
-    # direct probe one; the events bracket all of them
-    parts = ctx.join_probe_partitions(table, npr)
-    kernels = ["olap::join_part_count_kernel", "olap::join_part_scatter_kernel", "olap::join_probe_part_kernel"] \
-        if parts > 1 else ["olap::join_probe_kernel"]
+    # the kernels of one probe call, all bracketed by the events: the Bloom
+    # pre-probe's sample and filter (when the table has a filter), the
+    # partition count and scatter (when partitioned), and the probe
+    pinfo = ctx.join_probe_info()
+    parts = pinfo["parts"]
+    kernels = (["olap::join_prefilter_sample_kernel", "olap::join_prefilter_kernel"] if table.has_bloom() else []) + \
+        (["olap::join_part_count_kernel", "olap::join_part_scatter_kernel"] if parts > 1 else []) + \
+        ["olap::join_probe_kernel"]
     peak, peak_kind = _peaks()
     m = need / npr
     honest = npr * (8 + 32) + need * 8
@@ -258,7 +261,8 @@ def join_leg(args, ctx, torch, world):
         "ms_per_step": ms, "steps": steps, "ms_median": _median_p95(per)[0], "ms_p95": _median_p95(per)[1],
         "cell": {"build_rows": nb, "build": mult, "probe_rows": npr, "dist": dist, "hit_rate": hit,
                  "pairs": need, "pairs_per_probe": m, "buckets": info["n_buckets"], "load": 0.5,
-                 "rowids": "implicit", "probe_partitions": parts},
+                 "rowids": "implicit", "probe_partitions": parts, "prefiltered": pinfo["prefiltered"],
+                 "rows_probed_after_prefilter": pinfo["rows_probed"]},
         "build": {"ms": build_s * 1e3, "Grows_per_s": nb / build_s / 1e9},
         "roofline": {"bound": "hbm", "kernel": " + ".join(kernels), "peak": peak, "peak_kind": peak_kind,
                      "unit": "GB/s",
@@ -276,6 +280,63 @@ def join_leg(args, ctx, torch, world):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+
+
+def join_cells_leg(args, ctx, torch, world):
+    """Every join cell: 2^24 build rows {unique, multiplicity 1-4} x 2^28
+    probe keys {uniform, Zipf 1.1} x hit rate {0.1, 0.9}, device resident,
+    seed 2 (the full-size parity tests' inputs).  Per cell: the probe call's
+    time (CUDA events around every kernel it launches, mean of a few steps),
+    probes/s and the fraction of the HBM roofline, with how the call ran
+    (partitions, Bloom pre-probe)."""
+    from paper_2601_19911_gb300 import datagen, olap
+    nb, npr = 1 << args.join_log2b, 1 << args.join_log2p
+    peak, peak_kind = _peaks()
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    cells = []
+    launches = 0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for mult in ("unique", "mult14"):
+            b = datagen.join_build(nb, mult, seed=2)
+            table = ctx.join_build(torch.from_numpy(b.keys).cuda())
+            for dist in ("uniform", "zipf"):
+                for hit in (0.1, 0.9):
+                    p = datagen.join_probe(npr, b, hit, dist, seed=2)
+                    need = p.expected_pairs(b)
+                    dk = torch.from_numpy(p.keys).cuda()
+                    out = torch.empty((need, 2), dtype=torch.int32, device="cuda")
+                    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+                    for _ in range(2):
+                        ctx.join_probe_async(table, dk, out, need, cnt)
+                    ctx.sync()
+                    assert int(cnt.item()) == need, (mult, dist, hit, int(cnt.item()), need)
+                    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                           for _ in range(args.join_cell_steps)]
+                    _barrier(world)
+                    l0 = ctx.launches()
+                    for a, e in evs:
+                        a.record(stream)
+                        ctx.join_probe_async(table, dk, out, need, cnt)
+                        e.record(stream)
+                    ctx.sync()
+                    launches += ctx.launches() - l0
+                    ms = _max_over_ranks(float(np.mean([a.elapsed_time(e) for a, e in evs])), world)
+                    info = ctx.join_probe_info()
+                    honest = npr * (8 + 32) + need * 8
+                    cells.append({"build": mult, "dist": dist, "hit_rate": hit, "pairs": need, "ms": ms,
+                                  "gprobes_s": world * npr / (ms * 1e-3) / 1e9,
+                                  "honest_frac": honest / (ms * 1e-3) / 1e9 / peak,
+                                  "streaming_only_frac": (npr * 8 + need * 8) / (ms * 1e-3) / 1e9 / peak,
+                                  "partitions": info["parts"], "prefiltered": info["prefiltered"],
+                                  "rows_probed": info["rows_probed"]})
+                    del dk, out
+                    torch.cuda.empty_cache()
+            table.free()
+    return {"metric": "join probes/s per cell", "unit": "Gprobes/s", "build_rows": nb, "probe_rows": npr,
+            "steps": args.join_cell_steps, "peak": peak, "peak_kind": peak_kind,
+            "honest_bytes_per_probe": "8 key + 32 table sector + 8 per pair",
+            "timing": "CUDA events around each probe call (every kernel it launches)", "cells": cells,
+            "gpu_launches": launches, "clocks": clk.summary()}
 
 
 def batched_leg(args, ctx, torch):
@@ -982,6 +1043,20 @@ def run_ours(args):
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     launches += ctx.launches() - l0
     e2e_value = replicas.whole_job_rate(n, world, e2e_s) / 1e9
+    e2e_keys_only = None
+    if hr is not None:
+        # the same call with implicit row-ids: only the keys cross the link
+        ctx.topk(hk, k, olap.DESC, out_keys=hok, out_rowids=horow)
+        _barrier(world)
+        l0 = ctx.launches()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.topk(hk, k, olap.DESC, out_keys=hok, out_rowids=horow)
+        ko_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+        launches += ctx.launches() - l0
+        e2e_keys_only = {"value": replicas.whole_job_rate(n, world, ko_s) / 1e9, "unit": "Gkeys/s",
+                         "h2d_bytes_per_step": n * w, "d2h_bytes_per_step": k * (w + 4) + 4,
+                         "ms_per_step": ko_s * 1e3}
 
     # -- per-kernel device time (events around each kernel), same workload ----
     kms = _kernel_pass(ctx, args.steps, lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr))
@@ -1023,7 +1098,9 @@ def run_ours(args):
                      "filter": args.filter, "last_launch": phases,
                      "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
         "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w + (4 * n if hr is not None else 0),
-                "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3},
+                "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3,
+                "rowids": "explicit (keys and row-ids cross the link)" if hr is not None else "implicit (keys only)",
+                "keys_only": e2e_keys_only},
         # the library's own count over the timed regions of `value` and `e2e`
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -1036,6 +1113,9 @@ def run_ours(args):
         del dk, hk, dr, hr
         torch.cuda.empty_cache()
         line["join"] = join_leg(args, ctx, torch, world)
+    if "joincells" in workloads:
+        torch.cuda.empty_cache()
+        line["join_cells"] = join_cells_leg(args, ctx, torch, world)
     if "batched" in workloads:
         torch.cuda.empty_cache()
         line["batched"] = batched_leg(args, ctx, torch)
@@ -1070,22 +1150,25 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--key-type", default="i64", choices=["i64", "f32", "f64", "u64", "i32", "u32"])
     ap.add_argument("--dist", default="uniform", choices=["uniform", "ascending", "dup1024"])
-    ap.add_argument("--rowids", default="implicit", choices=["implicit", "explicit"],
-                    help="explicit: uint32 row-ids 0..N-1 passed with the keys (read only for survivors)")
+    ap.add_argument("--rowids", default="explicit", choices=["implicit", "explicit"],
+                    help="explicit (the configured workload): uint32 row-ids 0..N-1 passed with the keys (read "
+                         "on the device only for survivors; they cross the link in the end-to-end figure)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,single,link,join,batched,fullrow,gate,serving",
+    ap.add_argument("--workload", default="topk,single,link,join,joincells,batched,fullrow,gate,serving",
                     help="comma list: topk (the headline value), single (2^20-key query latency), link (pinned "
                          "copy bandwidth), join (probe sub-object), batched (executor), "
-                         "fullrow (full-row vs key-only transfer), gate (break-even validation), "
+                         "joincells (every join cell), fullrow (full-row vs key-only transfer), "
+                         "gate (break-even validation), "
                          "serving (gated vs always-on stream)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",
                     help="build multiplicity (unique|mult14), probe distribution (uniform|zipf), hit rate")
     ap.add_argument("--join-log2b", type=int, default=24)
     ap.add_argument("--join-log2p", type=int, default=28)
     ap.add_argument("--join-steps", type=int, default=50)
+    ap.add_argument("--join-cell-steps", type=int, default=5, help="timed probes per cell of the joincells leg")
     ap.add_argument("--join-traffic", type=float, default=None)
     ap.add_argument("--gate-points", type=int, default=16, help="N grid points of the gate leg (1e3..1e8)")
     ap.add_argument("--fullrow-payload", type=int, default=100, help="payload bytes per row of the full-row leg")
@@ -1100,7 +1183,7 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--batch-topk", type=int, default=4096)
     ap.add_argument("--batch-probe", type=int, default=1024)
     ap.add_argument("--batch-reps", type=int, default=10)
-    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-arena", type=int, default=100_000_000)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-cpu-workers", type=int, default=12)

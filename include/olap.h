@@ -368,9 +368,10 @@ olap_status olap_join_probe_partitions(olap_ctx* ctx, const olap_join_table* tab
  * probe has run on the context. */
 olap_status olap_join_probe_info_last(olap_ctx* ctx, int* parts, int* prefiltered, uint64_t* rows_probed);
 
-/* Table facts: build rows, buckets (2 slots each), rows in the side list. */
+/* Table facts: build rows, buckets (2 slots each), rows in the side list,
+ * bytes of its Bloom filter (0: none).  Any output may be NULL. */
 olap_status olap_join_table_info(const olap_join_table* table, uint64_t* n_build, uint64_t* n_buckets,
-                                 uint64_t* n_side);
+                                 uint64_t* n_side, uint64_t* bloom_bytes);
 
 /* Free a table (NULL is ignored).  Waits for the table's device to finish
  * work that may still read it. */

@@ -836,11 +836,13 @@ olap_status olap_join_probe_info_last(olap_ctx* ctx, int* parts, int* prefiltere
     return OLAP_OK;
 }
 
-olap_status olap_join_table_info(const olap_join_table* t, uint64_t* n_build, uint64_t* n_buckets, uint64_t* n_side) {
+olap_status olap_join_table_info(const olap_join_table* t, uint64_t* n_build, uint64_t* n_buckets, uint64_t* n_side,
+                                 uint64_t* bloom_bytes) {
     if (!t || !t->slots) return OLAP_E_INVALID;
     if (n_build) *n_build = t->n_build;
     if (n_buckets) *n_buckets = t->n_buckets;
     if (n_side) *n_side = t->n_side;
+    if (bloom_bytes) *bloom_bytes = t->bloom_blocks * 32;
     return OLAP_OK;
 }
 

@@ -235,7 +235,8 @@ def load(path: str | None = None):
         lib.olap_join_probe_info_last.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                   ctypes.POINTER(u64)]
         lib.olap_join_table_info.restype = i32
-        lib.olap_join_table_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        lib.olap_join_table_info.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                             ctypes.POINTER(u64)]
         lib.olap_join_free.restype = None
         lib.olap_join_free.argtypes = [vp]
         lib.olap_gate_calibrate.restype = i32
@@ -605,11 +606,15 @@ class JoinTable:
         self.h = h
 
     def info(self) -> dict:
-        nb, nk, ns = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
-        st = self.lib.olap_join_table_info(self.h, ctypes.byref(nb), ctypes.byref(nk), ctypes.byref(ns))
+        nb, nk, ns, bb = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        st = self.lib.olap_join_table_info(self.h, ctypes.byref(nb), ctypes.byref(nk), ctypes.byref(ns),
+                                           ctypes.byref(bb))
         if st != OK:
             raise OlapError(st, "olap_join_table_info failed")
-        return {"n_build": nb.value, "n_buckets": nk.value, "n_side": ns.value}
+        return {"n_build": nb.value, "n_buckets": nk.value, "n_side": ns.value, "bloom_bytes": bb.value}
+
+    def has_bloom(self) -> bool:
+        return self.info()["bloom_bytes"] > 0
 
     def free(self):
         if getattr(self, "h", None):
