@@ -5,7 +5,7 @@ CPU-baseline leg of ``bench.py`` may import this package.  The library under
 ``paper_2601_19911_gb300`` never imports it and shares no code with it.
 
 ``oracle.cpp`` (plain C++, compiled here into ``_build/liboracle.so`` with g++)
-holds the Top-K and join definitions; ``gate.py`` holds the gate's fits and
+holds the Top-K (one key column or two) and join definitions; ``gate.py`` holds the gate's fits and
 decision in numpy fp64.
 """
 from __future__ import annotations
@@ -47,6 +47,8 @@ def _load():
             u64, vp, i32 = ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
             lib.oracle_topk.restype = u64
             lib.oracle_topk.argtypes = [i32, vp, vp, u64, u64, i32, vp, vp]
+            lib.oracle_topk_pair.restype = u64
+            lib.oracle_topk_pair.argtypes = [i32, vp, i32, i32, vp, i32, vp, u64, u64, vp, vp, vp]
             for name in ("oracle_join", "oracle_join_nested"):
                 fn = getattr(lib, name)
                 fn.restype = u64
@@ -88,6 +90,28 @@ def topk(keys: np.ndarray, k: int, order: int = DESC, rowids: np.ndarray | None 
                           _ptr(ok), _ptr(orow))
     assert got == cnt
     return ok[:cnt], orow[:cnt]
+
+
+def topk_pair(keys0: np.ndarray, order0: int, keys1: np.ndarray, order1: int, k: int,
+              rowids: np.ndarray | None = None):
+    """First min(k, n) rows of the (c0 in order0, c1 in order1, row-id
+    ascending) sort: (c0 keys, c1 keys, row-ids)."""
+    lib = _load()
+    keys0 = np.ascontiguousarray(keys0)
+    keys1 = np.ascontiguousarray(keys1)
+    n = keys0.shape[0]
+    assert keys1.shape[0] == n
+    if rowids is not None:
+        rowids = np.ascontiguousarray(rowids, dtype=np.uint32)
+        assert rowids.shape[0] == n
+    cnt = min(int(k), n)
+    o0 = np.empty(max(cnt, 1), dtype=keys0.dtype)
+    o1 = np.empty(max(cnt, 1), dtype=keys1.dtype)
+    orow = np.empty(max(cnt, 1), dtype=np.uint32)
+    got = lib.oracle_topk_pair(_key_type(keys0), _ptr(keys0), int(order0), _key_type(keys1), _ptr(keys1),
+                               int(order1), _ptr(rowids), n, int(k), _ptr(o0), _ptr(o1), _ptr(orow))
+    assert got == cnt
+    return o0[:cnt], o1[:cnt], orow[:cnt]
 
 
 def _join_call(fn, bkeys, brow, pkeys, prow):

@@ -11,6 +11,8 @@
 //     of the Top-K results"; Sec. V-B, ORDER BY value DESC LIMIT 100): build
 //     the (key, row-id) pairs, stable-sort them by key in the requested order
 //     with row-id ascending as the tie-break, keep the first min(k, n).
+//   * Top-K over a two-column key (ORDER BY c0, c1 LIMIT K): the same with
+//     the rows compared column by column, each in its own order.
 //   * Join probe (Sec. III-B, "key-only hash table ... pointer return"; Sec.
 //     II-C, "returns ... a set of matched pointers"): every (probe row-id,
 //     build row-id) pair whose keys are equal, as a sorted multiset.
@@ -98,9 +100,74 @@ struct Less {
     }
 };
 
+// Two-column key (ORDER BY c0, c1): the rows in lexicographic order of
+// (c0 in its order, c1 in its order), then row-id ascending.
+struct Row2 {
+    uint64_t k0, k1;  // raw key bits of each column
+    uint32_t rowid;
+};
+
+struct Less2 {
+    Less c0, c1;      // each column's own comparator (its rowid tie-break unused)
+    bool operator()(const Row2& a, const Row2& b) const {
+        const bool a0 = c0.order == 0 ? c0.key_below(a.k0, b.k0) : c0.key_below(b.k0, a.k0);
+        if (a0) return true;
+        const bool b0 = c0.order == 0 ? c0.key_below(b.k0, a.k0) : c0.key_below(a.k0, b.k0);
+        if (b0) return false;
+        const bool a1 = c1.order == 0 ? c1.key_below(a.k1, b.k1) : c1.key_below(b.k1, a.k1);
+        if (a1) return true;
+        const bool b1 = c1.order == 0 ? c1.key_below(b.k1, a.k1) : c1.key_below(a.k1, b.k1);
+        if (b1) return false;
+        return a.rowid < b.rowid;
+    }
+};
+
+uint64_t read_key(const void* keys, int key_type, uint64_t i) {
+    if (key_width(key_type) == 8) {
+        uint64_t v;
+        std::memcpy(&v, static_cast<const uint64_t*>(keys) + i, 8);
+        return v;
+    }
+    uint32_t v;
+    std::memcpy(&v, static_cast<const uint32_t*>(keys) + i, 4);
+    return v;
+}
+
+void write_key(void* out, int key_type, uint64_t i, uint64_t v) {
+    if (key_width(key_type) == 8) {
+        std::memcpy(static_cast<uint64_t*>(out) + i, &v, 8);
+    } else {
+        const uint32_t w = static_cast<uint32_t>(v);
+        std::memcpy(static_cast<uint32_t*>(out) + i, &w, 4);
+    }
+}
+
 }  // namespace
 
 extern "C" {
+
+// Top-K over a two-column key: the first min(k, n) rows of the stable sort by
+// (c0 in order0, c1 in order1, row-id ascending); each output column receives
+// its own key bits.  Any key types.  Returns the count.
+uint64_t oracle_topk_pair(int type0, const void* keys0, int order0, int type1, const void* keys1, int order1,
+                          const uint32_t* rowids, uint64_t n, uint64_t k, void* out0, void* out1,
+                          uint32_t* out_rowids) {
+    std::vector<Row2> rows(n);
+    for (uint64_t i = 0; i < n; ++i) {
+        rows[i].k0 = read_key(keys0, type0, i);
+        rows[i].k1 = read_key(keys1, type1, i);
+        rows[i].rowid = rowids ? rowids[i] : static_cast<uint32_t>(i);
+    }
+    std::stable_sort(rows.begin(), rows.end(), Less2{Less{type0, order0}, Less{type1, order1}});
+    const uint64_t cnt = std::min(k, n);
+    for (uint64_t i = 0; i < cnt; ++i) {
+        write_key(out0, type0, i, rows[i].k0);
+        write_key(out1, type1, i, rows[i].k1);
+        out_rowids[i] = rows[i].rowid;
+    }
+    return cnt;
+}
+
 
 // Top-K: out_keys (same element type as keys) and out_rowids receive the
 // first min(k, n) rows of the ordering; returns that count.  rowids == NULL
