@@ -282,6 +282,49 @@ def join_leg(args, ctx, torch, world):
     }
 
 
+def pair_leg(args, ctx, torch, world):
+    """Top-K over a two-column key, ORDER BY c0 DESC, c1 ASC LIMIT 1000, at
+    2^log2n rows of two device-resident int32 columns: c0 with 1024 distinct
+    values (seed 1), c1 uniform (seed 2), so ties on c0 are broken by c1.
+    CUDA events around each call on the library stream; the roofline counts
+    both columns read once (8 bytes per row)."""
+    from paper_2601_19911_gb300 import datagen, olap
+    n, k = 1 << args.log2n, args.k
+    d0 = torch.from_numpy(datagen.topk_keys(n, "dup1024", "i32", seed=1)).cuda()
+    d1 = torch.from_numpy(datagen.topk_keys(n, "uniform", "i32", seed=2)).cuda()
+    g0 = torch.empty(k, dtype=torch.int32, device="cuda")
+    g1 = torch.empty(k, dtype=torch.int32, device="cuda")
+    gr = torch.empty(k, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    for _ in range(max(3, args.warmup)):
+        ctx.topk_pair(d0, olap.DESC, d1, olap.ASC, k, out_keys0=g0, out_keys1=g1, out_rowids=gr)
+    steps = max(3, min(args.steps, 100))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    _barrier(world)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        l0 = ctx.launches()
+        for a, e in evs:
+            a.record(stream)
+            ctx.topk_pair(d0, olap.DESC, d1, olap.ASC, k, out_keys0=g0, out_keys1=g1, out_rowids=gr)
+            e.record(stream)
+        ctx.sync()
+        launches = ctx.launches() - l0
+    per = [a.elapsed_time(e) for a, e in evs]
+    ms = _max_over_ranks(float(np.mean(per)), world)
+    peak, peak_kind = _peaks()
+    info = ctx.topk_info()
+    del d0, d1
+    torch.cuda.empty_cache()
+    return {"metric": "two-column Top-K rows/s", "unit": "Grows/s", "value": world * n / (ms * 1e-3) / 1e9,
+            "ms_per_step": ms, "ms_median": _median_p95(per)[0], "ms_p95": _median_p95(per)[1], "steps": steps,
+            "config": {"rows": n, "k": k, "order": "c0 desc, c1 asc", "c0": "int32, 1024 distinct (seed 1)",
+                       "c1": "int32 uniform (seed 2)"},
+            "roofline": {"bound": "hbm", "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                         "bytes_per_row": 8, "achieved": n * 8 / (ms * 1e-3) / 1e9,
+                         "frac": n * 8 / (ms * 1e-3) / 1e9 / peak, "timing": "CUDA events around the whole call"},
+            "last_launch": info, "gpu_launches": launches, "clocks": clk.summary()}
+
+
 def join_cells_leg(args, ctx, torch, world):
     """Every join cell: 2^24 build rows {unique, multiplicity 1-4} x 2^28
     probe keys {uniform, Zipf 1.1} x hit rate {0.1, 0.9}, device resident,
@@ -1113,6 +1156,9 @@ def run_ours(args):
         del dk, hk, dr, hr
         torch.cuda.empty_cache()
         line["join"] = join_leg(args, ctx, torch, world)
+    if "pair" in workloads:
+        torch.cuda.empty_cache()
+        line["pair"] = pair_leg(args, ctx, torch, world)
     if "joincells" in workloads:
         torch.cuda.empty_cache()
         line["join_cells"] = join_cells_leg(args, ctx, torch, world)
@@ -1157,10 +1203,11 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,single,link,join,joincells,batched,fullrow,gate,serving",
+    ap.add_argument("--workload", default="topk,single,pair,link,join,joincells,batched,fullrow,gate,serving",
                     help="comma list: topk (the headline value), single (2^20-key query latency), link (pinned "
                          "copy bandwidth), join (probe sub-object), batched (executor), "
-                         "joincells (every join cell), fullrow (full-row vs key-only transfer), "
+                         "pair (two-column key Top-K), joincells (every join cell), fullrow (full-row vs "
+                         "key-only transfer), "
                          "gate (break-even validation), "
                          "serving (gated vs always-on stream)")
     ap.add_argument("--join-cell", default="unique,uniform,0.9",

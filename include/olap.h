@@ -193,6 +193,22 @@ olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const
                       void* out_keys, uint32_t* out_rowids, olap_mem out_where,
                       uint64_t* out_count);
 
+/* Top-K over a two-column key: ORDER BY c0 [ASC|DESC], c1 [ASC|DESC] LIMIT k
+ * (Sec. III-A's ORDER BY key LIMIT K, Sec. V-B, with a second key column, as
+ * SQL's ORDER BY lists allow).  Rows are compared on c0 in order0, then on c1
+ * in order1, then by row-id ascending.  Both columns hold n keys of a 4-byte
+ * type (int32, uint32 or float32 by IEEE totalOrder; other widths return
+ * OLAP_E_UNIMPLEMENTED), in memory `where` with the row-ids (NULL => index).
+ * out_keys0 / out_keys1 receive each column's key bits of the min(k, n)
+ * selected rows, out_rowids their row-ids, in order (memory `out_where`).
+ * The composite key maps to one 64-bit rank word (c0's order-preserving
+ * 32 bits above c1's), which the same select refines.  Errors as olap_topk.
+ * Blocking. */
+olap_status olap_topk_pair(olap_ctx* ctx, const void* keys0, olap_key_type type0, olap_order order0,
+                           const void* keys1, olap_key_type type1, olap_order order1, const uint32_t* rowids,
+                           olap_mem where, uint64_t n, uint64_t k, void* out_keys0, void* out_keys1,
+                           uint32_t* out_rowids, olap_mem out_where, uint64_t* out_count);
+
 /* Asynchronous Top-K on device pointers only, enqueued on `stream` (NULL =>
  * the context's stream).  Writes min(k, n) results; `dev_status` (device
  * int32, may be NULL) receives an olap_status from the device side.  The

@@ -243,11 +243,19 @@ olap_status copy_d2h(olap_ctx* ctx, void* dst, const void* src, size_t bytes, ol
     return OLAP_OK;
 }
 
+// The second column of a two-column key (ORDER BY c0, c1).
+struct PairSpec {
+    const void* keys;
+    olap_key_type type;
+    olap_order order;
+    void* out_keys;
+};
+
 // Enqueue one Top-K on device pointers.  The caller has validated arguments.
 static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type type,
                                 const uint32_t* d_rowids, uint64_t n, uint64_t kk, olap_order order,
                                 void* d_out_keys, uint32_t* d_out_rowids, int32_t* dev_status,
-                                cudaStream_t stream, TopkCtl** ctl_out) {
+                                cudaStream_t stream, TopkCtl** ctl_out, const PairSpec* pair = nullptr) {
     const TopkPlan plan = topk_plan(n, kk);
     const bool reset = ctx->barrier_dirty || ctx->scratch_bytes < topk_scratch_bytes(plan, kk);
     olap_status st = ensure_scratch(ctx, topk_scratch_bytes(plan, kk));
@@ -269,6 +277,14 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
     a.out_keys = d_out_keys;
     a.out_rowids = d_out_rowids;
     a.dev_status = dev_status;
+    if (pair) {
+        a.pair = 1;
+        a.w4 = 0;                                           // 64-bit composite rank words
+        a.keys2 = pair->keys;
+        a.kind2 = pair->type;
+        a.desc2 = pair->order == OLAP_DESC;
+        a.out_keys2 = pair->out_keys;
+    }
     a.filter = ctx->opts.topk_filter == OLAP_FILTER_BULK ? TK_FILTER_BULK : TK_FILTER_REGS;
     a.digit = ctx->opts.topk_digit_bits ? ctx->opts.topk_digit_bits : TK_DIG;
     ctx->last_topk_ctl = a.ctl;
@@ -545,6 +561,77 @@ olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const
         if (st != OLAP_OK) return st;
         st = copy_d2h(ctx, out_rowids, dor, kk * 4, out_where);
         if (st != OLAP_OK) return st;
+    }
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Top-K");
+    if (*ctx->host_status != OLAP_OK) {
+        ctx->barrier_dirty = true;
+        return fail(ctx, static_cast<olap_status>(*ctx->host_status), "Top-K device wait expired");
+    }
+    *out_count = kk;
+    return OLAP_OK;
+}
+
+olap_status olap_topk_pair(olap_ctx* ctx, const void* keys0, olap_key_type type0, olap_order order0,
+                           const void* keys1, olap_key_type type1, olap_order order1, const uint32_t* rowids,
+                           olap_mem in_where, uint64_t n, uint64_t k, void* out_keys0, void* out_keys1,
+                           uint32_t* out_rowids, olap_mem out_where, uint64_t* out_count) {
+    if (!ctx) return OLAP_E_INVALID;
+    ctx->last_error.clear();
+    if (!out_count) return fail(ctx, OLAP_E_INVALID, "out_count is NULL");
+    *out_count = 0;
+    if (in_where < OLAP_MEM_HOST || in_where > OLAP_MEM_DEVICE || out_where < OLAP_MEM_HOST ||
+        out_where > OLAP_MEM_DEVICE)
+        return fail(ctx, OLAP_E_INVALID, "bad memory kind");
+    const uint64_t kk = std::min(k, n);
+    olap_status st = check_topk_args(ctx, keys0, type0, n, kk, order0, out_keys0, out_rowids);
+    if (st != OLAP_OK) return st;
+    if ((st = check_topk_args(ctx, keys1, type1, n, kk, order1, out_keys1, out_rowids)) != OLAP_OK) return st;
+    if (key_bytes(type0) != 4 || key_bytes(type1) != 4)
+        return fail(ctx, OLAP_E_UNIMPLEMENTED, "two-column keys take 4-byte columns (int32, uint32, float32)");
+    if (kk == 0) return OLAP_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
+
+    // Key-only input: both key columns (and explicit row-ids) to the device.
+    const void* d0 = keys0;
+    const void* d1 = keys1;
+    const uint32_t* dr = rowids;
+    const size_t cb = (n * 4 + 255) & ~static_cast<size_t>(255);
+    if (in_where != OLAP_MEM_DEVICE) {
+        if ((st = ensure_dev_in(ctx, 2 * cb + (rowids ? n * 4 : 0))) != OLAP_OK) return st;
+        unsigned char* m = static_cast<unsigned char*>(ctx->dev_in);
+        if ((st = copy_h2d(ctx, m, keys0, n * 4, in_where)) != OLAP_OK) return st;
+        if ((st = copy_h2d(ctx, m + cb, keys1, n * 4, in_where)) != OLAP_OK) return st;
+        d0 = m;
+        d1 = m + cb;
+        if (rowids) {
+            dr = reinterpret_cast<const uint32_t*>(m + 2 * cb);
+            if ((st = copy_h2d(ctx, const_cast<uint32_t*>(dr), rowids, n * 4, in_where)) != OLAP_OK) return st;
+        }
+    }
+    void* do0 = out_keys0;
+    void* do1 = out_keys1;
+    uint32_t* dor = out_rowids;
+    const size_t ob = (kk * 4 + 255) & ~static_cast<size_t>(255);
+    if (out_where != OLAP_MEM_DEVICE) {
+        if ((st = ensure_dev_out(ctx, 3 * ob)) != OLAP_OK) return st;
+        unsigned char* m = static_cast<unsigned char*>(ctx->dev_out);
+        do0 = m;
+        do1 = m + ob;
+        dor = reinterpret_cast<uint32_t*>(m + 2 * ob);
+    }
+    TopkCtl* ctl = nullptr;
+    const PairSpec ps{d1, type1, order1, do1};
+    if ((st = topk_enqueue(ctx, d0, type0, dr, n, kk, order0, do0, dor, nullptr, ctx->stream, &ctl, &ps)) !=
+        OLAP_OK)
+        return st;
+    e = cudaMemcpyAsync(ctx->host_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
+    if (out_where != OLAP_MEM_DEVICE) {
+        if ((st = copy_d2h(ctx, out_keys0, do0, kk * 4, out_where)) != OLAP_OK) return st;
+        if ((st = copy_d2h(ctx, out_keys1, do1, kk * 4, out_where)) != OLAP_OK) return st;
+        if ((st = copy_d2h(ctx, out_rowids, dor, kk * 4, out_where)) != OLAP_OK) return st;
     }
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "Top-K");

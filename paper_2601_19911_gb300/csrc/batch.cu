@@ -5,7 +5,9 @@
 // dominant" (Sec. IV, small-N interval).  Here one CTA runs one work item
 // start to finish; CTAs take the next item from an atomic queue head, items
 // sorted largest first on the host, so thousands of uneven items cost one
-// launch.  Per item:
+// launch.  A Top-K item of 2^19 keys or more is split into parts of about
+// 2^18 keys that run as items of their own; a second launch merges each
+// split item's parts.  Per item:
 //   * Top-K (K <= 4096): a stratified sample of 2048 keys gives a threshold
 //     rank word; one streaming pass appends the keys at or below it to the
 //     CTA's own candidate buffer (no global atomics); block-local radix passes
@@ -42,6 +44,14 @@ constexpr int BT_WS = 128;                // staged hits per warp
 constexpr int BT_BINS = 4096;
 constexpr int BT_SMEM = 2 * BT_SMALL * 12; // two sort areas; also the histogram, stages, probe stage
 constexpr uint64_t BP_CHUNK = 32768;       // probe rows per work unit
+#ifndef OLAP_BT_SPLIT_LOG2
+#define OLAP_BT_SPLIT_LOG2 19
+#endif
+#ifndef OLAP_BT_PART_LOG2
+#define OLAP_BT_PART_LOG2 18
+#endif
+constexpr uint64_t BT_SPLIT_N = 1ull << OLAP_BT_SPLIT_LOG2;  // Top-K items from this size on are split into parts
+constexpr uint64_t BT_PART = 1ull << OLAP_BT_PART_LOG2;      // target rows per part (balanced: >= BT_PART / 2)
 static_assert(JP_STAGE * 8 <= BT_SMEM, "probe stage must fit");
 static_assert((BT_TPB / 32) * BT_WS * 12 <= BT_SMEM, "warp stages must fit");
 
@@ -64,7 +74,19 @@ struct __align__(8) Item {
     uint64_t cap;
     unsigned long long* count;   // rows (Top-K) or pairs (probe) written
     int32_t* status;
+    uint64_t rowid_base;         // implicit row-ids: rowid_base + index
+    int out_mode;                // Top-K output: ITEM_OUT_KEYS, ITEM_OUT_RANKS or ITEM_OUT_MERGE
+    int out_kind;                // ITEM_OUT_MERGE: key kind and order of the original query
+    int out_desc;
+    int pad;
 };
+
+// How a Top-K item writes its result.  A large item is split into parts that
+// each select their own Top-K and write rank words (ITEM_OUT_RANKS); a merge
+// item then selects the Top-K of the parts' results (keys are rank words,
+// read as uint64 ascending, with explicit row-ids) and writes the original
+// key bits (ITEM_OUT_MERGE).
+enum { ITEM_OUT_KEYS = 0, ITEM_OUT_RANKS = 1, ITEM_OUT_MERGE = 2 };
 
 // One probe work unit: rows [chunk * BP_CHUNK, (chunk + 1) * BP_CHUNK) of probe
 // item `item` (the last chunk of an item is shorter).
@@ -78,13 +100,24 @@ __device__ __forceinline__ uint64_t item_rank(const Item& it, uint64_t i, uint32
     const uint64_t bits = it.w4 ? static_cast<uint64_t>(static_cast<const uint32_t*>(it.keys)[i])
                                 : static_cast<const uint64_t*>(it.keys)[i];
     r = rank_key(bits, it.kind, it.desc);
-    *rid = it.rowids ? it.rowids[i] : static_cast<uint32_t>(i);
+    *rid = it.rowids ? it.rowids[i] : static_cast<uint32_t>(it.rowid_base + i);
     return r;
 }
 
 __device__ __forceinline__ void put_result(const Item& it, uint64_t i, uint64_t r, uint32_t rid) {
-    if (it.w4) static_cast<uint32_t*>(it.out_keys)[i] = static_cast<uint32_t>(unrank_key(r, it.kind, it.desc));
-    else static_cast<uint64_t*>(it.out_keys)[i] = unrank_key(r, it.kind, it.desc);
+    if (it.out_mode == ITEM_OUT_RANKS) {
+        static_cast<uint64_t*>(it.out_keys)[i] = r;
+    } else if (it.out_mode == ITEM_OUT_MERGE) {
+        // r is the rank word of the original key (uint64 ascending is identity)
+        if (key_bytes(it.out_kind) == 4)
+            static_cast<uint32_t*>(it.out_keys)[i] = static_cast<uint32_t>(unrank_key(r, it.out_kind, it.out_desc));
+        else
+            static_cast<uint64_t*>(it.out_keys)[i] = unrank_key(r, it.out_kind, it.out_desc);
+    } else if (it.w4) {
+        static_cast<uint32_t*>(it.out_keys)[i] = static_cast<uint32_t>(unrank_key(r, it.kind, it.desc));
+    } else {
+        static_cast<uint64_t*>(it.out_keys)[i] = unrank_key(r, it.kind, it.desc);
+    }
     it.out_rowids[i] = rid;
 }
 
@@ -135,7 +168,7 @@ __device__ __forceinline__ void cta_flush_stage(uint64_t* ws_r, uint32_t* ws_idx
         if (base + j < BT_CAND) {
             const uint32_t idx = ws_idx[j];
             cand_r[base + j] = ws_r[j];
-            cand_rid[base + j] = it.rowids ? it.rowids[idx] : idx;
+            cand_rid[base + j] = it.rowids ? it.rowids[idx] : static_cast<uint32_t>(it.rowid_base + idx);
         }
     }
     __syncwarp();
@@ -483,6 +516,11 @@ struct olap_batch {
     int* d_errors = nullptr;
     uint64_t* cand_r = nullptr;
     uint32_t* cand_rid = nullptr;
+    // Split Top-K items: the merge items (run after the first Top-K launch)
+    // and the parts' results (rank words, row-ids, counts).
+    Item* d_merge = nullptr;
+    uint64_t n_merge = 0;
+    void* part_buf = nullptr;
     int grid_topk = 0, grid_probe = 0;
     // Overlap: the probe branch runs on a second stream forked from the
     // launch stream inside the graph (the two kernels are independent).
@@ -525,6 +563,12 @@ olap_status enqueue_batch(olap_batch* b, cudaStream_t s) {
                                                                 b->cand_rid, b->d_errors, b->digit);
         ++b->graph_kernels;
     }
+    if (b->n_merge) {          // after every part: the merges of split items
+        const unsigned mg = static_cast<unsigned>(std::min<uint64_t>(b->n_merge, b->grid_topk));
+        batch_topk_kernel<<<mg, BT_TPB, BT_SMEM, s>>>(b->d_merge, b->n_merge, b->d_next + 2, b->cand_r,
+                                                      b->cand_rid, b->d_errors, b->digit);
+        ++b->graph_kernels;
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(b->ctx, e, "batch launch");
     if (b->overlap &&
         ((e = cudaEventRecord(b->ev_join, b->side)) != cudaSuccess || (e = cudaStreamWaitEvent(s, b->ev_join, 0)) !=
@@ -541,6 +585,8 @@ void batch_release(olap_batch* b) {
     if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->side) cudaStreamDestroy(b->side);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_merge) cudaFree(b->d_merge);
+    if (b->part_buf) cudaFree(b->part_buf);
     if (b->d_chunks) cudaFree(b->d_chunks);
     if (b->d_next) cudaFree(b->d_next);
     if (b->cand_r) cudaFree(b->cand_r);
@@ -606,17 +652,90 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
         if (dev[a].op != dev[b].op) return dev[a].op == OLAP_OP_TOPK;
         return cost[a] > cost[b];
     });
-    std::vector<Item> sorted(n_items);
-    uint64_t n_topk = 0;
+    // Large Top-K items are split into parts of about BT_PART rows: one CTA
+    // streaming a 4M-key item alone was the batch's tail.  Each part selects
+    // its own Top-K (rank words and row-ids into part_buf); a merge item
+    // selects the item's Top-K from the parts' results in a second launch.
+    struct Split {
+        uint64_t item, parts, len;
+    };
+    std::vector<Split> splits;
+    uint64_t part_entries = 0;
     for (uint64_t i = 0; i < n_items; ++i) {
-        sorted[i] = dev[order[i]];
-        if (sorted[i].op == OLAP_OP_TOPK) ++n_topk;
+        const Item& d = dev[i];
+        const size_t w = d.w4 ? 4 : 8;
+        if (d.op != OLAP_OP_TOPK || d.n < BT_SPLIT_N || d.k == 0 || reinterpret_cast<uintptr_t>(d.keys) % w)
+            continue;
+        const uint64_t parts = (d.n + BT_PART - 1) / BT_PART;
+        splits.push_back({i, parts, (d.n + parts - 1) / parts});
+        part_entries += parts * d.k;
     }
+    std::vector<Item> topk_units, merges;
+    void* part_buf = nullptr;
+    if (!splits.empty()) {
+        // [rank words | row-ids | counts], each 256-byte aligned
+        const size_t rb = (part_entries * 8 + 255) & ~static_cast<size_t>(255);
+        const size_t ib = (part_entries * 4 + 255) & ~static_cast<size_t>(255);
+        e = cudaMalloc(&part_buf, rb + ib + splits.size() * 8);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(ctx, e, "batch part results");
+        }
+        unsigned char* pb = static_cast<unsigned char*>(part_buf);
+        uint64_t* ranks = reinterpret_cast<uint64_t*>(pb);
+        uint32_t* rids = reinterpret_cast<uint32_t*>(pb + rb);
+        unsigned long long* counts = reinterpret_cast<unsigned long long*>(pb + rb + ib);
+        uint64_t at = 0, nc = 0;
+        for (const Split& sp : splits) {
+            Item& orig = dev[sp.item];
+            const size_t w = orig.w4 ? 4 : 8;
+            for (uint64_t p = 0; p < sp.parts; ++p) {
+                Item part = orig;
+                const uint64_t off = p * sp.len;
+                part.keys = static_cast<const unsigned char*>(orig.keys) + off * w;
+                part.rowids = orig.rowids ? orig.rowids + off : nullptr;
+                part.rowid_base = orig.rowids ? 0 : off;
+                part.n = std::min(sp.len, orig.n - off);
+                part.out_mode = ITEM_OUT_RANKS;
+                part.out_keys = ranks + at + p * orig.k;
+                part.out_rowids = rids + at + p * orig.k;
+                part.count = counts + nc;                    // parts share one scratch count word per item
+                part.status = nullptr;
+                topk_units.push_back(part);
+            }
+            Item m = orig;
+            m.kind = OLAP_KEY_U64;
+            m.w4 = 0;
+            m.desc = 0;
+            m.keys = ranks + at;
+            m.rowids = rids + at;
+            m.rowid_base = 0;
+            m.n = sp.parts * orig.k;
+            m.out_mode = ITEM_OUT_MERGE;
+            m.out_kind = orig.kind;
+            m.out_desc = orig.desc;
+            merges.push_back(m);
+            at += sp.parts * orig.k;
+            nc += 1;
+            orig.op = -1;                                    // replaced by its parts and merge
+        }
+    }
+    std::vector<Item> sorted;
+    sorted.reserve(n_items + topk_units.size());
+    for (uint64_t i = 0; i < n_items; ++i)
+        if (dev[order[i]].op == OLAP_OP_TOPK) topk_units.push_back(dev[order[i]]);
+    std::stable_sort(topk_units.begin(), topk_units.end(),
+                     [](const Item& a, const Item& b) { return a.n * (a.w4 ? 4 : 8) > b.n * (b.w4 ? 4 : 8); });
+    const uint64_t n_topk = topk_units.size();
+    sorted = topk_units;
+    for (uint64_t i = 0; i < n_items; ++i)
+        if (dev[order[i]].op == OLAP_OP_PROBE) sorted.push_back(dev[order[i]]);
+    const uint64_t n_units = sorted.size();
 
     // Probe work units: each item cut into chunks of BP_CHUNK rows, in the
     // items' (largest first) order.
     std::vector<ProbeChunk> chunks;
-    for (uint64_t i = n_topk; i < n_items; ++i) {
+    for (uint64_t i = n_topk; i < n_units; ++i) {
         const uint64_t nch = (sorted[i].n + BP_CHUNK - 1) / BP_CHUNK;
         for (uint64_t c = 0; c < nch; ++c)
             chunks.push_back({static_cast<uint32_t>(i - n_topk), static_cast<uint32_t>(c)});
@@ -628,7 +747,9 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
     b->n_chunks = chunks.size();
     b->items.assign(items, items + n_items);
     b->n_topk = n_topk;
-    b->n_probe = n_items - n_topk;
+    b->n_probe = n_units - n_topk;
+    b->part_buf = part_buf;
+    b->n_merge = merges.size();
     int per_t = 0, per_p = 0;
     if ((e = cudaFuncSetAttribute(batch_topk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, BT_SMEM)) !=
             cudaSuccess ||
@@ -644,7 +765,7 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
     }
     const int topk_per_sm = ctx->opts.batch_topk_ctas_per_sm > 0 ? ctx->opts.batch_topk_ctas_per_sm : 2;
     b->grid_topk = ctx->sm_count * std::max(1, std::min(per_t, topk_per_sm));
-    b->overlap = ctx->opts.batch_overlap == 1 && n_topk > 0 && n_items > n_topk;
+    b->overlap = ctx->opts.batch_overlap == 1 && n_topk > 0 && n_units > n_topk;
     if (b->overlap &&
         ((e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking)) != cudaSuccess ||
          (e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
@@ -654,7 +775,8 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
         return cuda_fail(ctx, e, "batch streams");
     }
     b->grid_probe = ctx->sm_count * std::max(1, per_p);
-    if ((e = cudaMalloc(&b->d_items, std::max<uint64_t>(1, n_items) * sizeof(Item))) != cudaSuccess ||
+    if ((e = cudaMalloc(&b->d_items, std::max<uint64_t>(1, n_units) * sizeof(Item))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_merge, std::max<size_t>(1, merges.size()) * sizeof(Item))) != cudaSuccess ||
         (e = cudaMalloc(&b->d_chunks, std::max<size_t>(1, chunks.size()) * sizeof(ProbeChunk))) != cudaSuccess ||
         (e = cudaMalloc(reinterpret_cast<void**>(&b->d_next), 256)) != cudaSuccess ||
         (e = cudaMalloc(&b->cand_r, static_cast<size_t>(b->grid_topk) * BT_CAND * 8)) != cudaSuccess ||
@@ -665,8 +787,10 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
     }
     b->d_errors = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(b->d_next) + 64);
 
-    if (n_items && (e = cudaMemcpy(b->d_items, sorted.data(), n_items * sizeof(Item), cudaMemcpyHostToDevice)) !=
-                       cudaSuccess) {
+    if ((n_units && (e = cudaMemcpy(b->d_items, sorted.data(), n_units * sizeof(Item), cudaMemcpyHostToDevice)) !=
+                        cudaSuccess) ||
+        (!merges.empty() && (e = cudaMemcpy(b->d_merge, merges.data(), merges.size() * sizeof(Item),
+                                            cudaMemcpyHostToDevice)) != cudaSuccess)) {
         batch_release(b);
         return cuda_fail(ctx, e, "batch descriptor upload");
     }

@@ -204,6 +204,8 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 struct GridBar {
     unsigned count;
     unsigned gen;
+    unsigned prep;        // tickets of the Top-K prepare kernel's CTAs (a multiple of its grid between launches)
+    unsigned pad;
 };
 
 // Wait until *word differs from `old`, at most `limit` clock cycles; on

@@ -3,11 +3,12 @@
 // row pointers of the Top-K rows in order).
 //
 // Three launches on one stream:
-//   0. topk_prepare_kernel (one CTA) zeroes the control block and, when
-//      N > 2^21 and K is small against N, reads a stratified sample of 8192
-//      keys and finds the rank word of the sample's r-th best entry by a
-//      radix select; r is chosen so that, with high probability, at least K
-//      keys but not many more fall at or below it.
+//   0. topk_prepare_kernel zeroes the control block and, when N > 2^21 and K
+//      is small against N, reads a stratified sample of 8192 keys (16 CTAs,
+//      one key per thread) and finds the rank word of the sample's r-th best
+//      entry by a radix select in the last CTA to finish; r is chosen so that,
+//      with high probability, at least K keys but not many more fall at or
+//      below it.
 //   1. topk_filter_regs_kernel (default) or topk_filter_bulk_kernel (TMA
 //      bulk copies into a shared-memory ring): the only full pass over the
 //      keys, run only when there is a sample.  16-byte streaming loads, one
@@ -45,11 +46,20 @@ struct Elem {
     uint32_t rid;
 };
 
+// Rank word of a two-column key: c0's 32-bit rank above c1's.
+__device__ __forceinline__ uint64_t pair_rank(uint32_t b0, uint32_t b1, const TopkArgs& a) {
+    return rank_key(b0, a.kind, a.desc) | (rank_key(b1, a.kind2, a.desc2) >> 32);
+}
+
 __device__ __forceinline__ Elem load_input(const TopkArgs& a, uint64_t i) {
     Elem e;
-    const uint64_t bits = a.w4 ? static_cast<uint64_t>(static_cast<const uint32_t*>(a.keys)[i])
-                               : static_cast<const uint64_t*>(a.keys)[i];
-    e.r = rank_key(bits, a.kind, a.desc);
+    if (a.pair) {
+        e.r = pair_rank(static_cast<const uint32_t*>(a.keys)[i], static_cast<const uint32_t*>(a.keys2)[i], a);
+    } else {
+        const uint64_t bits = a.w4 ? static_cast<uint64_t>(static_cast<const uint32_t*>(a.keys)[i])
+                                   : static_cast<const uint64_t*>(a.keys)[i];
+        e.r = rank_key(bits, a.kind, a.desc);
+    }
     e.rid = a.rowids ? a.rowids[i] : static_cast<uint32_t>(i);
     return e;
 }
@@ -60,7 +70,10 @@ __device__ __forceinline__ Elem load_src(const TopkArgs& a, bool cand, uint64_t 
 }
 
 __device__ __forceinline__ void write_result(const TopkArgs& a, uint64_t i, uint64_t r, uint32_t rid) {
-    if (a.w4)
+    if (a.pair) {
+        static_cast<uint32_t*>(a.out_keys)[i] = static_cast<uint32_t>(unrank_key(r & 0xFFFFFFFF00000000ull, a.kind, a.desc));
+        static_cast<uint32_t*>(a.out_keys2)[i] = static_cast<uint32_t>(unrank_key(r << 32, a.kind2, a.desc2));
+    } else if (a.w4)
         static_cast<uint32_t*>(a.out_keys)[i] = static_cast<uint32_t>(unrank_key(r, a.kind, a.desc));
     else
         static_cast<uint64_t*>(a.out_keys)[i] = unrank_key(r, a.kind, a.desc);
@@ -68,19 +81,18 @@ __device__ __forceinline__ void write_result(const TopkArgs& a, uint64_t i, uint
 }
 
 // Prepare kernel: a threshold rank word for the streaming pass from a
-// stratified sample of TK_SAMPLE keys.  Radix select with a.digit-bit digits on the
-// sample held in registers; it stops as soon as the upper edge of the chosen
-// bucket has between r and r + 8 samples at or below it (any such threshold
-// serves), which for spread-out keys is after the first digit.
+// stratified sample of TK_SAMPLE keys (sample j is key (j * n) / TK_SAMPLE +
+// (n / TK_SAMPLE) / 2).  The prepare CTAs load it together, one key per
+// thread, into a.samples -- from one SM, 8192 scattered loads wait on each
+// other's DRAM latency -- and the last CTA to finish runs this radix select
+// with a.digit-bit digits on the sample held in registers; it stops as soon as
+// the upper edge of the chosen bucket has between r and r + 8 samples at or
+// below it (any such threshold serves), which for spread-out keys is after the
+// first digit.
 __device__ uint64_t sample_threshold(const TopkArgs& a, unsigned* sh, unsigned long long* sc) {
     uint64_t s[TK_SPT];
-    const uint64_t n = a.n;
 #pragma unroll
-    for (int j = 0; j < TK_SPT; ++j) {
-        const uint64_t idx = static_cast<uint64_t>(j) * TK_TPB + threadIdx.x;
-        const uint64_t pos = (idx * n) / TK_SAMPLE + (n / TK_SAMPLE) / 2;
-        s[j] = load_input(a, pos).r;
-    }
+    for (int j = 0; j < TK_SPT; ++j) s[j] = __ldcg(a.samples + static_cast<uint64_t>(j) * TK_TPB + threadIdx.x);
     const int kb = a.w4 ? 32 : 64;
     const unsigned long long r = a.sample_rank;
     uint64_t prefix = 0;
@@ -255,6 +267,122 @@ __device__ void filter_pass(const TopkArgs& a, uint64_t t, unsigned char* stage_
     }
     stage_flush(a, ws);
     filter_ends(a, t, head, tail0);
+}
+
+// The 32-bit order-preserving transform of one 4-byte key kind as two masks:
+// rank = b ^ (sign-extended top bit of b & flip) ^ fixed.  float32 flips the
+// magnitude of negatives and sets the sign bit of the others (IEEE
+// totalOrder), int32 flips the sign bit, uint32 keeps the bits; DESC
+// complements the result.  The same map as rank_key, without branches.
+struct Rank32 {
+    uint32_t flip, fixed;
+};
+__device__ __forceinline__ Rank32 rank32_of(int kind, bool desc) {
+    Rank32 m;
+    m.flip = kind == OLAP_KEY_F32 ? 0x7FFFFFFFu : 0u;
+    m.fixed = (kind == OLAP_KEY_U32 ? 0u : 0x80000000u) ^ (desc ? 0xFFFFFFFFu : 0u);
+    return m;
+}
+__device__ __forceinline__ uint32_t rank32(uint32_t b, Rank32 m) {
+    return b ^ (static_cast<uint32_t>(static_cast<int32_t>(b) >> 31) & m.flip) ^ m.fixed;
+}
+
+// Stage the hits among the four rows of one 16-byte vector of each column.
+__device__ __forceinline__ void filter_vector_pair(const TopkArgs& a, uint64_t t, Rank32 m0, Rank32 m1, uint4 x0,
+                                                   uint4 x1, bool valid, uint64_t idx0, WarpStage& ws) {
+    const uint32_t c0[4] = {x0.x, x0.y, x0.z, x0.w}, c1[4] = {x1.x, x1.y, x1.z, x1.w};
+    uint64_t r[4];
+    unsigned hit = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        r[e] = (static_cast<uint64_t>(rank32(c0[e], m0)) << 32) | rank32(c1[e], m1);
+        hit |= (valid && r[e] <= t) ? (1u << e) : 0u;
+    }
+    if (!__any_sync(0xFFFFFFFFu, hit != 0)) return;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned bal[4];
+    unsigned total = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        bal[e] = __ballot_sync(0xFFFFFFFFu, (hit >> e) & 1u);
+        total += __popc(bal[e]);
+    }
+    if (ws.count + total > WS_CAP) stage_flush(a, ws);
+    unsigned before = ws.count;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if ((hit >> e) & 1u) {
+            const unsigned pos = before + __popc(bal[e] & lt);
+            ws.r[pos] = r[e];
+            ws.idx[pos] = static_cast<uint32_t>(idx0 + e);
+        }
+        before += __popc(bal[e]);
+    }
+    ws.count += total;
+}
+
+// Phase 1 for a two-column key: both columns streamed with 16-byte loads when
+// they share their alignment (a scalar head and tail around the vectors),
+// else row by row; every row whose composite rank word is <= t is appended.
+constexpr int TK_PAIR_UNROLL = 2;          // vector pairs (32 bytes) in flight per thread
+
+template <int TPB>
+__device__ void filter_pass_pair(const TopkArgs& a, uint64_t t, unsigned char* stage_smem) {
+    const uint64_t n = a.n;
+    const Rank32 m0 = rank32_of(a.kind, a.desc), m1 = rank32_of(a.kind2, a.desc2);
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a.keys), a1 = reinterpret_cast<uintptr_t>(a.keys2);
+    WarpStage ws = warp_stage(stage_smem);
+    const unsigned lane = threadIdx.x & 31u;
+    if (((a0 ^ a1) & 15) == 0) {
+        const uint64_t head0 = ((16 - (a0 & 15)) & 15) / 4;
+        const uint64_t head = head0 < n ? head0 : n;
+        const uint64_t nvec = (n - head) / 4;
+        const uint64_t tail0 = head + nvec * 4;
+        const unsigned char* v0 = static_cast<const unsigned char*>(a.keys) + head * 4;
+        const unsigned char* v1 = static_cast<const unsigned char*>(a.keys2) + head * 4;
+        const uint64_t per_block = static_cast<uint64_t>(TPB) * TK_PAIR_UNROLL;
+        const uint64_t stride = per_block * gridDim.x;
+        for (uint64_t bb = per_block * blockIdx.x; bb < nvec; bb += stride) {
+            uint4 x0[TK_PAIR_UNROLL], x1[TK_PAIR_UNROLL];
+#pragma unroll
+            for (int u = 0; u < TK_PAIR_UNROLL; ++u) {
+                const uint64_t vi = bb + static_cast<uint64_t>(u) * TPB + threadIdx.x;
+                if (vi < nvec) {
+                    x0[u] = ld_stream_v4(v0 + vi * 16);
+                    x1[u] = ld_stream_v4(v1 + vi * 16);
+                } else {
+                    x0[u] = x1[u] = make_uint4(0, 0, 0, 0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TK_PAIR_UNROLL; ++u) {
+                const uint64_t vi = bb + static_cast<uint64_t>(u) * TPB + threadIdx.x;
+                filter_vector_pair(a, t, m0, m1, x0[u], x1[u], vi < nvec, head + vi * 4, ws);
+            }
+        }
+        stage_flush(a, ws);
+        filter_ends(a, t, head, tail0);
+        return;
+    }
+    const uint64_t stride = static_cast<uint64_t>(TPB) * gridDim.x;
+    const uint64_t lt = (1u << lane) - 1u;
+    for (uint64_t wb = static_cast<uint64_t>(blockIdx.x) * TPB + (threadIdx.x & ~31u); wb < n; wb += stride) {
+        const uint64_t i = wb + lane;
+        uint64_t r = ~0ull;
+        if (i < n) r = pair_rank(static_cast<const uint32_t*>(a.keys)[i], static_cast<const uint32_t*>(a.keys2)[i], a);
+        const bool hit = i < n && r <= t;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
+        if (!bal) continue;
+        if (ws.count + __popc(bal) > WS_CAP) stage_flush(a, ws);
+        if (hit) {
+            const unsigned pos = ws.count + __popc(bal & static_cast<unsigned>(lt));
+            ws.r[pos] = r;
+            ws.idx[pos] = static_cast<uint32_t>(i);
+        }
+        ws.count += __popc(bal);
+    }
+    stage_flush(a, ws);
 }
 
 // Issue the bulk copy of the tile at byte offset `off` of the key body into
@@ -491,13 +619,15 @@ __device__ __forceinline__ void report(const TopkArgs& a) {
 
 }  // namespace
 
-// Kernel 1 of 3 (one CTA): reset the control block and the histograms, and
-// when the sampled path is taken estimate the filter threshold.
+// Kernel 1 of 3: reset the control block and the histograms (CTA 0, and all
+// CTAs' shares), and on the sampled path load the sample and estimate the
+// filter threshold (TK_PREP_CTAS CTAs; the last one to finish selects).
 __global__ void __launch_bounds__(TK_TPB) topk_prepare_kernel(TopkArgs a) {
     __shared__ unsigned sh[TK_BINS];
     __shared__ unsigned long long sc[24];
+    __shared__ int last;
     TopkCtl* ctl = a.ctl;
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->ts[0] = gtimer();
         ctl->cand_count = 0;
         ctl->out_count = 0;
@@ -514,12 +644,24 @@ __global__ void __launch_bounds__(TK_TPB) topk_prepare_kernel(TopkArgs a) {
         ctl->fin[0] = ctl->fin[1] = ~0ull;
         ctl->fin[2] = ctl->fin[3] = 0ull;
     }
-    for (int b = threadIdx.x; b < 3 * TK_BINS; b += TK_TPB) a.ghist[b] = 0;
-    if (a.use_sample) {
-        const uint64_t t = sample_threshold(a, sh, sc);
-        if (threadIdx.x == 0) ctl->thresh = t;
+    for (int b = blockIdx.x * TK_TPB + threadIdx.x; b < 3 * TK_BINS; b += gridDim.x * TK_TPB) a.ghist[b] = 0;
+    if (!a.use_sample) {
+        if (threadIdx.x == 0) ctl->ts[1] = gtimer();
+        return;
     }
-    if (threadIdx.x == 0) ctl->ts[1] = gtimer();
+    const uint64_t j = static_cast<uint64_t>(blockIdx.x) * TK_TPB + threadIdx.x;   // < TK_SAMPLE
+    a.samples[j] = load_input(a, (j * a.n) / TK_SAMPLE + (a.n / TK_SAMPLE) / 2).r;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&a.bar->prep, 1u) + 1u) % gridDim.x == 0;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const uint64_t t = sample_threshold(a, sh, sc);
+    if (threadIdx.x == 0) {
+        ctl->thresh = t;
+        ctl->ts[1] = gtimer();
+    }
 }
 
 // Kernel 2 of 3 (sampled path only): the single streaming pass over the keys,
@@ -538,6 +680,14 @@ __global__ void __launch_bounds__(TPB) topk_filter_regs_kernel(TopkArgs a) {
     extern __shared__ __align__(16) unsigned char stage[];
     const uint64_t t = __ldcg(&a.ctl->thresh);
     filter_pass<W4, TPB>(a, t, stage);
+}
+
+// Kernel 2 of 3 for a two-column key (register loads of both columns).
+template <int TPB>
+__global__ void __launch_bounds__(TPB, 1024 / TPB) topk_filter_pair_kernel(TopkArgs a) {
+    extern __shared__ __align__(16) unsigned char stage[];
+    const uint64_t t = __ldcg(&a.ctl->thresh);
+    filter_pass_pair<TPB>(a, t, stage);
 }
 
 // Kernel 3 of 3 (cooperative): refine, split, finish and sort.
@@ -957,6 +1107,7 @@ static size_t up256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 size_t topk_scratch_bytes(const TopkPlan& p, uint64_t k) {
     size_t b = up256(sizeof(TopkCtl)) + up256(sizeof(GridBar)) + up256(3 * TK_BINS * 4);
+    if (p.use_sample) b += up256(TK_SAMPLE * 8);
     b += up256(p.cand_cap * 8) + up256(p.cand_cap * 4);
     b += up256(TK_SMALL * 8) + up256(TK_SMALL * 4);
     const uint64_t kk = std::max<uint64_t>(k, 1);
@@ -992,6 +1143,7 @@ void topk_carve(TopkArgs& a, const TopkPlan& p, void* base) {
         a.out_r1 = nullptr;
         a.out_rid1 = nullptr;
     }
+    a.samples = p.use_sample ? static_cast<uint64_t*>(take(TK_SAMPLE * 8)) : nullptr;
     a.use_sample = p.use_sample;
     a.sample_rank = p.sample_rank;
     a.filter = TK_FILTER_BULK;
@@ -1020,6 +1172,8 @@ static bool set_kernel_attrs(int device) {
         cudaFuncSetAttribute(topk_filter_regs_kernel<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              32 * WS_BYTES) != cudaSuccess ||
         cudaFuncSetAttribute(topk_filter_regs_kernel<true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             32 * WS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_pair_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              32 * WS_BYTES) != cudaSuccess ||
         cudaFuncSetAttribute(topk_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              TK_SORT_SMEM) != cudaSuccess)
@@ -1080,11 +1234,19 @@ cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t
     if (a.digit < TK_DIG_MIN || a.digit > TK_DIG) return cudaErrorInvalidValue;
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
-    topk_prepare_kernel<<<1, TK_TPB, 0, stream>>>(a);
+    topk_prepare_kernel<<<a.use_sample ? TK_PREP_CTAS : 1, TK_TPB, 0, stream>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev && (e = cudaEventRecord(ev[1], stream)) != cudaSuccess) return e;
-    if (a.use_sample) {
+    if (a.use_sample && a.pair) {
+        const size_t rs = static_cast<size_t>(geom.regs_tpb / 32) * WS_BYTES;
+        const unsigned gr = static_cast<unsigned>(geom.regs_grid);
+        if (geom.regs_tpb == 256) topk_filter_pair_kernel<256><<<gr, 256, rs, stream>>>(a);
+        else if (geom.regs_tpb == 1024) topk_filter_pair_kernel<1024><<<gr, 1024, rs, stream>>>(a);
+        else topk_filter_pair_kernel<512><<<gr, 512, rs, stream>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    } else if (a.use_sample) {
         if (a.filter == TK_FILTER_REGS) {
             const size_t rs = static_cast<size_t>(geom.regs_tpb / 32) * WS_BYTES;
             const unsigned gr = static_cast<unsigned>(geom.regs_grid);

@@ -15,6 +15,7 @@ constexpr int TK_BINS = 1 << TK_DIG;
 constexpr int TK_SMALL = 4096;            // entries one CTA sorts in shared memory
 constexpr int TK_SAMPLE = 8192;           // sample size of the threshold estimate
 constexpr int TK_SPT = TK_SAMPLE / TK_TPB;
+constexpr int TK_PREP_CTAS = TK_SAMPLE / TK_TPB;   // prepare CTAs on the sampled path: one key per thread
 constexpr int TK_UNROLL = 4;              // 16-byte loads in flight per thread (register filter)
 constexpr uint64_t TK_DIRECT_N = 1ull << 21;   // at or below: no sample, refine the input
 constexpr int TK_RANK_MAX = 8192;         // survivors ranked in shared memory by the whole grid
@@ -83,8 +84,17 @@ struct TopkArgs {
     uint32_t* out_rid0;
     uint64_t* out_r1;                // k entries, merge ping-pong (k > TK_SMALL)
     uint32_t* out_rid1;
+    uint64_t* samples;               // TK_SAMPLE rank words of the sample (sampled path)
     void* out_keys;                  // caller's outputs (device)
     uint32_t* out_rowids;
+    // Two-column key (ORDER BY c0, c1): keys / kind / desc describe c0 and
+    // these c1; both columns are 4-byte kinds and the rank word is c0's rank
+    // in the upper 32 bits and c1's in the lower 32 (w4 = 0).
+    int pair;
+    int kind2;
+    int desc2;
+    const void* keys2;
+    void* out_keys2;
     int32_t* dev_status;             // optional device status word
 };
 
@@ -119,8 +129,9 @@ struct TopkGeom {
 // fit, the block size is not one of 256/512/1024, or no CTA fits.
 bool topk_geometry(int device, int tile_bytes, int stages, int ctas_per_sm, int regs_tpb, TopkGeom* out);
 
-// Enqueue one Top-K: prepare (1 CTA), the streaming filter when the sampled
-// path is taken, then the cooperative select kernel.  Returns the first CUDA
+// Enqueue one Top-K: prepare (1 CTA, or TK_PREP_CTAS that load the sample),
+// the streaming filter when the sampled path is taken, then the cooperative
+// select kernel.  Returns the first CUDA
 // launch error.
 // ev (optional, 4 events): recorded before the prepare kernel and after the
 // prepare, filter and select kernels (the filter pair is empty when the plan

@@ -30,7 +30,7 @@ MEM_HOST, MEM_HOST_PINNED, MEM_DEVICE = 0, 1, 2
 EXPORTS = [
     "olap_ctx_create", "olap_ctx_destroy", "olap_last_error", "olap_ctx_stream", "olap_ctx_sync",
     "olap_ctx_host_direct", "olap_selftest_wait",
-    "olap_topk", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last", "olap_topk_rows",
+    "olap_topk", "olap_topk_pair", "olap_topk_async", "olap_topk_noalloc", "olap_topk_info_last", "olap_topk_rows",
     "olap_ctx_time_kernels", "olap_kernel_ms_last", "olap_ctx_launches", "olap_autotune",
     "olap_join_build", "olap_join_probe", "olap_join_probe_async", "olap_join_probe_partitions",
     "olap_join_probe_info_last",
@@ -208,6 +208,9 @@ def load(path: str | None = None):
         lib.olap_selftest_wait.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int32)]
         lib.olap_topk.restype = i32
         lib.olap_topk.argtypes = [vp, vp, i32, vp, i32, u64, u64, i32, vp, vp, i32, ctypes.POINTER(u64)]
+        lib.olap_topk_pair.restype = i32
+        lib.olap_topk_pair.argtypes = [vp, vp, i32, i32, vp, i32, i32, vp, i32, u64, u64, vp, vp, vp, i32,
+                                       ctypes.POINTER(u64)]
         lib.olap_topk_async.restype = i32
         lib.olap_topk_async.argtypes = [vp, vp, i32, vp, u64, u64, i32, vp, vp, vp, vp]
         lib.olap_topk_rows.restype = i32
@@ -419,6 +422,31 @@ class Context:
         self.check(st)
         _check_count(got.value, cnt)
         return out_keys[:cnt], out_rowids[:cnt]
+
+    def topk_pair(self, keys0, order0: int, keys1, order1: int, k: int, rowids=None, out_keys0=None,
+                  out_keys1=None, out_rowids=None):
+        """olap_topk_pair (ORDER BY c0, c1 LIMIT k over two 4-byte key
+        columns): returns (c0 keys, c1 keys, row-ids) cut to min(k, n)."""
+        n = numel(keys0)
+        if numel(keys1) != n:
+            raise ValueError("both key columns must hold the same number of rows")
+        where = mem_kind(keys0)
+        if mem_kind(keys1) != where:
+            raise ValueError("both key columns must be in the same kind of memory")
+        _check_rowids(rowids, where, n)
+        t0, t1 = key_type_of(keys0), key_type_of(keys1)
+        cnt = min(int(k), n)
+        if out_keys0 is None:
+            out_keys0 = np.empty(max(cnt, 1), dtype=KEY_NUMPY[t0])
+            out_keys1 = np.empty(max(cnt, 1), dtype=KEY_NUMPY[t1])
+            out_rowids = np.empty(max(cnt, 1), dtype=np.uint32)
+        got = ctypes.c_uint64()
+        st = self.lib.olap_topk_pair(self.h, ptr(keys0), t0, int(order0), ptr(keys1), t1, int(order1), ptr(rowids),
+                                     where, n, int(k), ptr(out_keys0), ptr(out_keys1), ptr(out_rowids),
+                                     mem_kind(out_keys0), ctypes.byref(got))
+        self.check(st)
+        _check_count(got.value, cnt)
+        return out_keys0[:cnt], out_keys1[:cnt], out_rowids[:cnt]
 
     def topk_rows(self, rows, row_bytes: int, key_offset: int, key_type: int, k: int, order: int = DESC,
                   out_rows=None, out_rowids=None):

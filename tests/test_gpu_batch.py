@@ -274,8 +274,9 @@ def test_launch_counter_counts_every_kernel():
     """olap_ctx_launches: the direct Top-K is two kernels (prepare, select),
     the sampled one three (prepare, filter, select); a build without key -1
     two (insert, chain counts); a direct probe one, a partitioned probe three; a batch replay the
-    kernels of its graph (probe reset, probe, Top-K); the per-query run the
-    sum of its calls.  A staged context launches no copy kernels."""
+    kernels of its graph (probe reset, probe, Top-K, and the merge of split
+    Top-K items: the 2^20-key item here is split); the per-query run the sum
+    of its calls.  A staged context launches no copy kernels."""
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     c = olap.Context(0, host_access=olap.HOST_STAGED)
@@ -307,7 +308,7 @@ def test_launch_counter_counts_every_kernel():
         items = [olap.topk_item(small, 100, olap.DESC, ok, orow, cnt2[0:1]),
                  olap.probe_item(t, pk, out, need, cnt2[1:2])]
         bt = c.batch(items)
-        assert delta(bt.run) == 3
+        assert delta(bt.run) == 4
         assert delta(bt.run_per_query) == 3
         bt.free()
         t.free()
@@ -323,3 +324,38 @@ def test_launch_counter_counts_every_kernel():
         t.free()
     finally:
         cp.close()
+
+
+def test_split_items_match_oracle(ctx):
+    """Top-K items of 2^19 keys and more run as parts of about 2^18 keys and a
+    merge launch: every split item equals the oracle bit for bit, at the split
+    threshold and above it, for both key widths and orders, the largest k,
+    and explicit row-ids (reversed, so the merge's row-id tie-break is not
+    the index order)."""
+    cases = [(1 << 19, 1, olap.DESC, "i64", False), ((1 << 19) + 1, 4096, olap.ASC, "i64", False),
+             (3 * (1 << 18) + 5, 1000, olap.DESC, "f32", False), (1_500_007, 777, olap.ASC, "f32", True),
+             (2_000_003, 4096, olap.DESC, "i64", True), ((1 << 19) - 1, 100, olap.DESC, "i64", False)]
+    items, q = [], []
+    for j, (n, k, order, kt, explicit) in enumerate(cases):
+        keys = datagen.topk_keys(n, "dup1024" if kt == "f32" else "uniform", kt, seed=40 + j)
+        rid = np.arange(n, dtype=np.uint32)[::-1].copy() if explicit else None
+        dk = torch.from_numpy(keys).cuda()
+        dr = None if rid is None else torch.from_numpy(rid.view(np.int32)).cuda()
+        ok = torch.empty(k, dtype=dk.dtype, device="cuda")
+        orow = torch.empty(k, dtype=torch.int32, device="cuda")
+        c = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        items.append(olap.topk_item(dk, k, order, ok, orow, c, d_rowids=dr, d_status=st))
+        q.append((keys, rid, k, order, dk, dr, ok, orow, c, st))
+    bt = ctx.batch(items)
+    try:
+        bt.run()
+        ctx.sync()
+        assert bt.errors() == 0
+        for keys, rid, k, order, _dk, _dr, ok, orow, c, st in q:
+            assert int(st.item()) == olap.OK and int(c.item()) == k
+            wk, wr = oracle.topk(keys, k, order, rid)
+            np.testing.assert_array_equal(orow.cpu().numpy().view(np.uint32), wr)
+            np.testing.assert_array_equal(ok.cpu().numpy().view(np.uint8), wk.view(np.uint8))
+    finally:
+        bt.free()
