@@ -5,8 +5,8 @@
 // dominant" (Sec. IV, small-N interval).  Here one CTA runs one work item
 // start to finish; CTAs take the next item from an atomic queue head, items
 // sorted largest first on the host, so thousands of uneven items cost one
-// launch.  A Top-K item of 2^19 keys or more is split into parts of about
-// 2^18 keys that run as items of their own; a second launch merges each
+// launch.  A Top-K item larger than one CTA's share of the batch is split
+// into parts that run as items of their own; a second launch merges each
 // split item's parts.  Per item:
 //   * Top-K (K <= 4096): a stratified sample of 2048 keys gives a threshold
 //     rank word; one streaming pass appends the keys at or below it to the
@@ -15,10 +15,11 @@
 //     the selected entries in shared memory, where they are sorted.  Small
 //     items (n <= 4096) are sorted whole; a misjudged sample falls back to
 //     radix passes over the item's keys.
-//   * probe: the probe rounds of the join kernel over one chunk of at most
-//     BP_CHUNK probe rows of an item; a large item is many chunks taken by
-//     many CTAs, all appending to the item's own count word, which a reset
-//     kernel zeroes before the probe queue starts.
+//   * probe: the probe loop of the join kernel over one chunk of at most
+//     BP_CHUNK probe rows of an item, handed to the CTA's warps by a row
+//     queue in shared memory; a large item is many chunks taken by many
+//     CTAs, all appending to the item's own count word, which a reset kernel
+//     zeroes before the probe queue starts.
 // Descriptors are checked on the device; a bad one gets OLAP_E_DEVICE in its
 // status word and is skipped.
 #include <algorithm>
@@ -44,14 +45,8 @@ constexpr int BT_WS = 128;                // staged hits per warp
 constexpr int BT_BINS = 4096;
 constexpr int BT_SMEM = 2 * BT_SMALL * 12; // two sort areas; also the histogram, stages, probe stage
 constexpr uint64_t BP_CHUNK = 32768;       // probe rows per work unit
-#ifndef OLAP_BT_SPLIT_LOG2
-#define OLAP_BT_SPLIT_LOG2 19
-#endif
-#ifndef OLAP_BT_PART_LOG2
-#define OLAP_BT_PART_LOG2 18
-#endif
-constexpr uint64_t BT_SPLIT_N = 1ull << OLAP_BT_SPLIT_LOG2;  // Top-K items from this size on are split into parts
-constexpr uint64_t BT_PART = 1ull << OLAP_BT_PART_LOG2;      // target rows per part (balanced: >= BT_PART / 2)
+constexpr uint64_t BT_SPLIT_N = 1ull << 19;  // smallest Top-K item that may be split into parts
+constexpr uint64_t BT_PART = 1ull << 18;     // smallest target rows per part (parts are balanced)
 static_assert(JP_STAGE * 8 <= BT_SMEM, "probe stage must fit");
 static_assert((BT_TPB / 32) * BT_WS * 12 <= BT_SMEM, "warp stages must fit");
 
@@ -462,6 +457,7 @@ __global__ void __launch_bounds__(JP_TPB, 3) batch_probe_kernel(const Item* item
     __shared__ ProbeChunk s_ch;
     __shared__ int s_ok;
     __shared__ ProbeArgs s_args;       // kept in shared memory, read as needed
+    __shared__ unsigned long long s_next;   // the chunk's row queue, shared by the CTA's warps
     uint32_t cur = 0xFFFFFFFFu;        // item whose arguments s_args holds
     while (true) {
         if (threadIdx.x == 0) s_item = atomicAdd(next, 1ull);
@@ -484,16 +480,17 @@ __global__ void __launch_bounds__(JP_TPB, 3) batch_probe_kernel(const Item* item
                 s_args.cap = it.cap;
                 s_args.count = it.count;
             }
+            s_next = static_cast<uint64_t>(s_ch.chunk) * BP_CHUNK;
         }
         __syncthreads();
         cur = s_ch.item;
         if (s_ok) {
-            const uint64_t r0 = static_cast<uint64_t>(s_ch.chunk) * BP_CHUNK;
-            const uint64_t r1 = min(s_args.n, r0 + BP_CHUNK);
-            const unsigned warp = threadIdx.x >> 5;
-            uint64_t b, e;
-            warp_share(r0, r1, warp, JP_WARPS, &b, &e);
-            probe_warp<true>(s_args, b, e, stage + warp * JP_WCAP);
+            // the chunk's rows go to the CTA's warps through a row queue in
+            // shared memory (the probe loop of the join kernel)
+            RowQueue q;
+            q.counter = &s_next;
+            q.n = min(s_args.n, static_cast<uint64_t>(s_ch.chunk) * BP_CHUNK + BP_CHUNK);
+            probe_queue<true, JP_S>(s_args, q, stage + (threadIdx.x >> 5) * JP_WCAP);
         }
         __syncthreads();
     }
@@ -652,10 +649,20 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
         if (dev[a].op != dev[b].op) return dev[a].op == OLAP_OP_TOPK;
         return cost[a] > cost[b];
     });
-    // Large Top-K items are split into parts of about BT_PART rows: one CTA
-    // streaming a 4M-key item alone was the batch's tail.  Each part selects
-    // its own Top-K (rank words and row-ids into part_buf); a merge item
-    // selects the item's Top-K from the parts' results in a second launch.
+    // A Top-K item larger than one CTA's share of the batch's Top-K bytes
+    // would keep its CTA busy after the others run dry (the items are
+    // scheduled largest first, so smaller ones balance the rest).  Such an
+    // item is split into parts of about that share (at least BT_PART rows):
+    // each part selects its own Top-K (rank words and row-ids into part_buf)
+    // and a merge item selects the item's Top-K from the parts' results in a
+    // second launch.  Measured on the 4096-query batch, where no item exceeds
+    // the share, splitting every item above 2^19 keys was slower (8.0 against
+    // 6.3 ms): the parts' fixed costs outweigh a tail that is not there.
+    const int topk_ctas_hint = ctx->sm_count * 2;
+    double topk_bytes = 0.0;
+    for (uint64_t i = 0; i < n_items; ++i)
+        if (dev[i].op == OLAP_OP_TOPK) topk_bytes += static_cast<double>(dev[i].n) * (dev[i].w4 ? 4.0 : 8.0);
+    const double share = topk_bytes / std::max(1, topk_ctas_hint);
     struct Split {
         uint64_t item, parts, len;
     };
@@ -664,9 +671,12 @@ olap_status olap_batch_create(olap_ctx* ctx, const olap_batch_item* items, uint6
     for (uint64_t i = 0; i < n_items; ++i) {
         const Item& d = dev[i];
         const size_t w = d.w4 ? 4 : 8;
-        if (d.op != OLAP_OP_TOPK || d.n < BT_SPLIT_N || d.k == 0 || reinterpret_cast<uintptr_t>(d.keys) % w)
+        if (d.op != OLAP_OP_TOPK || d.n < BT_SPLIT_N || d.k == 0 || reinterpret_cast<uintptr_t>(d.keys) % w ||
+            static_cast<double>(d.n) * w <= share)
             continue;
-        const uint64_t parts = (d.n + BT_PART - 1) / BT_PART;
+        const uint64_t part = std::max<uint64_t>(BT_PART, static_cast<uint64_t>(share / w));
+        const uint64_t parts = (d.n + part - 1) / part;
+        if (parts < 2) continue;
         splits.push_back({i, parts, (d.n + parts - 1) / parts});
         part_entries += parts * d.k;
     }

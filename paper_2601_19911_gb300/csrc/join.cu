@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs args, u
     RowQueue q;
     q.counter = next_row;
     q.n = a.n;
-    probe_queue<L2_ONLY>(a, q, stage + warp * JP_WCAP);
+    probe_queue<L2_ONLY, JP_S>(a, q, stage + warp * JP_WCAP);
 }
 
 // ---- Bloom pre-probe ------------------------------------------------------
@@ -318,32 +318,44 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs args) 
 // running offset (partition start + rows of that partition in lower CTAs +
 // rows already placed), reordered in shared memory so the writes of a
 // partition's run are contiguous.  The keys of the CTA's next tile are loaded
-// while the current one is reordered.
+// while the current one is reordered.  Three CTA barriers per tile: the
+// per-tile counts alternate between two arrays (the next tile's is zeroed
+// while this one is scanned), one warp scans them, and the next tile cannot
+// overwrite the reorder buffer before every thread has passed its first
+// barrier, which it reaches only after writing this tile out.
 __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs args) {
     const PartArgs a = part_source(args);
-    __shared__ unsigned h[JQ_PMAX];
+    __shared__ unsigned h[2][JQ_PMAX];
     __shared__ unsigned off[JQ_PMAX];
     __shared__ unsigned long long base[JQ_PMAX];
+    __shared__ unsigned long long tbase[JQ_PMAX];
     __shared__ unsigned long long wsum[JQ_TPB / 32];
     __shared__ unsigned long long total;
     __shared__ int64_t sk[JQ_TILE];
     __shared__ uint32_t sr[JQ_TILE];
     __shared__ uint8_t sp[JQ_TILE];
     const int p = threadIdx.x;
+    const int P = a.parts;
     {
         unsigned long long below = 0, all = 0;
-        if (p < a.parts) {
+        if (p < P) {
             for (unsigned c = 0; c < gridDim.x; ++c) {
-                const unsigned long long v = a.cnt[static_cast<uint64_t>(c) * a.parts + p];
+                const unsigned long long v = a.cnt[static_cast<uint64_t>(c) * P + p];
                 all += v;
                 if (c < blockIdx.x) below += v;
             }
         }
         const unsigned long long start = block_excl_scan<JQ_TPB>(all, wsum, &total);
-        if (p < a.parts) base[p] = start + below;
-        if (blockIdx.x == 0 && p < a.parts) a.pstart[p] = start;
-        if (blockIdx.x == 0 && p == 0) a.pstart[a.parts] = total;
+        if (p < P) {
+            base[p] = start + below;
+            h[0][p] = 0;
+        }
+        if (blockIdx.x == 0 && p < P) a.pstart[p] = start;
+        if (blockIdx.x == 0 && p == 0) a.pstart[P] = total;
     }
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31u;
+    const int PP = (P + 31) / 32;                      // partitions per lane of the scanning warp
     const uint64_t stride = static_cast<uint64_t>(gridDim.x) * JQ_TILE;
     uint64_t kc[JQ_PER];
     const uint64_t first = static_cast<uint64_t>(blockIdx.x) * JQ_TILE;
@@ -352,26 +364,50 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs args
         const uint64_t idx = first + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
         kc[j] = idx < a.n ? ld_stream_u64(a.keys + idx) : 0ull;
     }
-    for (uint64_t t0 = first; t0 < a.n; t0 += stride) {
+    int cur = 0;
+    for (uint64_t t0 = first; t0 < a.n; t0 += stride, cur ^= 1) {
         uint64_t kn[JQ_PER];
 #pragma unroll
         for (int j = 0; j < JQ_PER; ++j) {
             const uint64_t idx = t0 + stride + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
             kn[j] = idx < a.n ? ld_stream_u64(a.keys + idx) : 0ull;
         }
-        if (p < a.parts) h[p] = 0;
-        __syncthreads();
+        unsigned* hc = h[cur];
         unsigned pr[JQ_PER];                   // partition | rank in the tile << 8
 #pragma unroll
         for (int j = 0; j < JQ_PER; ++j) {
             const uint64_t idx = t0 + static_cast<uint64_t>(j) * JQ_TPB + threadIdx.x;
             const unsigned q = part_of(kc[j], a);
-            pr[j] = idx < a.n ? (q | (atomicAdd(&h[q], 1u) << 8)) : 0u;
+            pr[j] = idx < a.n ? (q | (atomicAdd(&hc[q], 1u) << 8)) : 0u;
         }
         __syncthreads();
-        const unsigned hv = p < a.parts ? h[p] : 0u;
-        const unsigned long long o = block_excl_scan<JQ_TPB>(hv, wsum, &total);
-        if (p < a.parts) off[p] = static_cast<unsigned>(o);
+        if (threadIdx.x < 32) {
+            // the tile's run starts (exclusive scan of its counts), the
+            // partitions' output positions, and the other count array zeroed
+            unsigned run = 0;
+            for (int i = 0; i < PP; ++i) {
+                const int q = static_cast<int>(lane) * PP + i;
+                if (q < P) run += hc[q];
+            }
+            unsigned incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= static_cast<unsigned>(o)) incl += v;
+            }
+            unsigned at = incl - run;
+            for (int i = 0; i < PP; ++i) {
+                const int q = static_cast<int>(lane) * PP + i;
+                if (q < P) {
+                    const unsigned c = hc[q];
+                    off[q] = at;
+                    tbase[q] = base[q];
+                    base[q] += c;
+                    h[cur ^ 1][q] = 0;
+                    at += c;
+                }
+            }
+        }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < JQ_PER; ++j) {
@@ -388,12 +424,10 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs args
         const unsigned len = static_cast<unsigned>(min(static_cast<uint64_t>(JQ_TILE), a.n - t0));
         for (unsigned i = threadIdx.x; i < len; i += JQ_TPB) {
             const unsigned q = sp[i];
-            const unsigned long long dst = base[q] + (i - off[q]);
+            const unsigned long long dst = tbase[q] + (i - off[q]);
             a.out_keys[dst] = sk[i];
             a.out_rowids[dst] = sr[i];
         }
-        __syncthreads();
-        if (p < a.parts) base[p] += hv;
 #pragma unroll
         for (int j = 0; j < JQ_PER; ++j) kc[j] = kn[j];
     }

@@ -158,104 +158,6 @@ __device__ __forceinline__ void warp_put(const ProbeArgs& a, uint2* ws, unsigned
     cnt += __popc(b);
 }
 
-// One warp probes the rows [begin, end).  Each lane runs JP_S independent
-// streams; stream s of lane L takes rows begin + L + 32*s, then every
-// 32*JP_S-th row after it.  A stream walks its chain one bucket per step;
-// when the chain ends it starts its next row at once (the key and row-id of
-// that row are already loaded), so every lane keeps bucket loads in flight
-// however uneven the chain lengths are.  Matches go to the warp's own stage
-// `ws` (JP_WCAP pairs), flushed to the output whenever it could overflow and
-// before returning.
-template <bool L2_ONLY>
-__device__ __forceinline__ void probe_warp(const ProbeArgs& a, uint64_t begin, uint64_t end, uint2* ws) {
-    constexpr uint64_t STEP = 32ull * JP_S;
-    const unsigned lane = threadIdx.x & 31u;
-    const uint32_t mask = static_cast<uint32_t>(a.mask);
-    unsigned cnt = 0;
-    uint64_t key[JP_S], pkey[JP_S], nxt[JP_S];
-    uint32_t rid[JP_S], prid[JP_S], bk[JP_S];
-    bool live[JP_S], plive[JP_S];
-    Bucket v[JP_S];
-#pragma unroll
-    for (int s = 0; s < JP_S; ++s) {
-        const uint64_t i = begin + lane + 32ull * s;
-        live[s] = i < end;
-        key[s] = live[s] ? ld_stream_u64(a.keys + i) : JN_EMPTY;
-        rid[s] = live[s] ? (a.rowids ? ld_stream_u32(a.rowids + i) : static_cast<uint32_t>(i)) : 0u;
-        nxt[s] = i + STEP;
-        plive[s] = nxt[s] < end;
-        pkey[s] = plive[s] ? ld_stream_u64(a.keys + nxt[s]) : JN_EMPTY;
-        prid[s] = plive[s] ? (a.rowids ? ld_stream_u32(a.rowids + nxt[s]) : static_cast<uint32_t>(nxt[s])) : 0u;
-    }
-#pragma unroll
-    for (int s = 0; s < JP_S; ++s) {
-        bk[s] = static_cast<uint32_t>(fmix64(key[s])) & mask;
-        if (live[s] && key[s] != JN_EMPTY)
-            v[s] = ld_bucket<L2_ONLY>(a.slots, bk[s]);
-        else
-            v[s] = Bucket{JN_EMPTY, 0, JN_EMPTY, 0};
-    }
-    while (true) {
-        bool any = false;
-#pragma unroll
-        for (int s = 0; s < JP_S; ++s) any = any || live[s];
-        if (!__any_sync(0xFFFFFFFFu, any)) break;
-        // Probe keys equal to the empty marker pair with every side-list row;
-        // the warp emits them together, one such key at a time (rare).
-#pragma unroll
-        for (int s = 0; s < JP_S; ++s) {
-            unsigned sb = __ballot_sync(0xFFFFFFFFu, live[s] && key[s] == JN_EMPTY);
-            while (sb) {
-                const int src = __ffs(sb) - 1;
-                sb &= sb - 1;
-                const uint32_t r = __shfl_sync(0xFFFFFFFFu, rid[s], src);
-                for (uint64_t o0 = 0; o0 < a.n_side; o0 += 32) {
-                    const bool m = o0 + lane < a.n_side;
-                    warp_put(a, ws, cnt, m, make_uint2(r, m ? a.side[o0 + lane] : 0u));
-                }
-            }
-        }
-        // Matches in the current bucket of every stream.  A match whose slot
-        // counts no further copies of its key is the chain's last copy: the
-        // stream's walk for this row ends there.
-        bool last[JP_S];
-#pragma unroll
-        for (int s = 0; s < JP_S; ++s) {
-            const bool real = live[s] && key[s] != JN_EMPTY;
-            const bool m0 = real && v[s].k0 == key[s], m1 = real && v[s].k1 == key[s];
-            warp_put(a, ws, cnt, m0, make_uint2(rid[s], static_cast<uint32_t>(v[s].w0)));
-            warp_put(a, ws, cnt, m1, make_uint2(rid[s], static_cast<uint32_t>(v[s].w1)));
-            last[s] = (m0 && (v[s].w0 >> 32) == 0) || (m1 && (v[s].w1 >> 32) == 0);
-        }
-        // Next bucket of the chain, or the stream's next row.
-#pragma unroll
-        for (int s = 0; s < JP_S; ++s) {
-            if (!live[s]) continue;
-            if (key[s] != JN_EMPTY && !last[s] && v[s].k0 != JN_EMPTY && v[s].k1 != JN_EMPTY) {
-                bk[s] = (bk[s] + 1u) & mask;
-            } else {
-                live[s] = plive[s];
-                key[s] = pkey[s];
-                rid[s] = prid[s];
-                if (!live[s]) continue;
-                bk[s] = static_cast<uint32_t>(fmix64(key[s])) & mask;
-                nxt[s] += STEP;
-                plive[s] = nxt[s] < end;
-                if (plive[s]) {
-                    pkey[s] = ld_stream_u64(a.keys + nxt[s]);
-                    prid[s] = a.rowids ? ld_stream_u32(a.rowids + nxt[s]) : static_cast<uint32_t>(nxt[s]);
-                }
-                if (key[s] == JN_EMPTY) {
-                    v[s] = Bucket{JN_EMPTY, 0, JN_EMPTY, 0};
-                    continue;
-                }
-            }
-            v[s] = ld_bucket<L2_ONLY>(a.slots, bk[s]);
-        }
-    }
-    warp_flush(a, ws, cnt);
-}
-
 // Rows handed to the lanes of one warp.  The warp takes chunks of JQ_CHUNK
 // consecutive rows from a global counter and gives them out in order, the
 // lanes that need a row in one step getting consecutive rows, so the loads of
@@ -312,46 +214,48 @@ __device__ __forceinline__ bool queue_next(RowQueue& q, unsigned need, uint64_t*
 // step and, when the chain ends, switches at once to the row it has already
 // loaded and asks the queue for the next one.  Matches go to the warp's own
 // stage `ws`, flushed to the output whenever it could overflow and at the end.
-template <bool L2_ONLY>
+template <bool L2_ONLY, int S>
 __device__ __forceinline__ void probe_queue(const ProbeArgs& a, RowQueue& q, uint2* ws) {
     const unsigned lane = threadIdx.x & 31u;
     const uint32_t mask = static_cast<uint32_t>(a.mask);
     unsigned cnt = 0;
-    uint64_t key[JP_S], pkey[JP_S];
-    uint32_t rid[JP_S], prid[JP_S], bk[JP_S];
-    bool live[JP_S], plive[JP_S];
-    Bucket v[JP_S];
+    uint64_t key[S], pkey[S];
+    uint32_t rid[S], prid[S], bk[S];
+    bool live[S], plive[S];
+    Bucket v[S];
     q.cur = take_chunk(q);
     q.nxt = RowRange{0, 0};
     // current rows, then the rows loaded ahead
 #pragma unroll
-    for (int s = 0; s < JP_S; ++s) {
+    for (int s = 0; s < S; ++s) {
         uint64_t i = 0;
         live[s] = queue_next(q, 0xFFFFFFFFu, &i);
         key[s] = live[s] ? ld_stream_u64(a.keys + i) : JN_EMPTY;
         rid[s] = live[s] ? (a.rowids ? ld_stream_u32(a.rowids + i) : static_cast<uint32_t>(i)) : 0u;
     }
 #pragma unroll
-    for (int s = 0; s < JP_S; ++s) {
+    for (int s = 0; s < S; ++s) {
         uint64_t i = 0;
         plive[s] = queue_next(q, 0xFFFFFFFFu, &i);
         pkey[s] = plive[s] ? ld_stream_u64(a.keys + i) : JN_EMPTY;
         prid[s] = plive[s] ? (a.rowids ? ld_stream_u32(a.rowids + i) : static_cast<uint32_t>(i)) : 0u;
     }
 #pragma unroll
-    for (int s = 0; s < JP_S; ++s) {
+    for (int s = 0; s < S; ++s) {
         bk[s] = static_cast<uint32_t>(fmix64(key[s])) & mask;
         v[s] = (live[s] && key[s] != JN_EMPTY) ? ld_bucket<L2_ONLY>(a.slots, bk[s]) : Bucket{JN_EMPTY, 0, JN_EMPTY, 0};
     }
     while (true) {
         bool any = false;
 #pragma unroll
-        for (int s = 0; s < JP_S; ++s) any = any || live[s];
+        for (int s = 0; s < S; ++s) any = any || live[s];
         if (!__any_sync(0xFFFFFFFFu, any)) break;
         // Probe keys equal to the empty marker pair with every side-list row;
-        // the warp emits them together, one such key at a time (rare).
+        // the warp emits them together, one such key at a time (rare).  With
+        // no side list such rows match nothing and are simply passed over.
 #pragma unroll
-        for (int s = 0; s < JP_S; ++s) {
+        for (int s = 0; s < S; ++s) {
+            if (a.n_side == 0) break;
             unsigned sb = __ballot_sync(0xFFFFFFFFu, live[s] && key[s] == JN_EMPTY);
             while (sb) {
                 const int src = __ffs(sb) - 1;
@@ -365,9 +269,9 @@ __device__ __forceinline__ void probe_queue(const ProbeArgs& a, RowQueue& q, uin
         }
         // Matches in the current bucket of every stream; a match whose slot
         // counts no further copies of its key ends the row's walk.
-        bool go[JP_S];
+        bool go[S];
 #pragma unroll
-        for (int s = 0; s < JP_S; ++s) {
+        for (int s = 0; s < S; ++s) {
             const bool real = live[s] && key[s] != JN_EMPTY;
             const bool m0 = real && v[s].k0 == key[s], m1 = real && v[s].k1 == key[s];
             warp_put(a, ws, cnt, m0, make_uint2(rid[s], static_cast<uint32_t>(v[s].w0)));
@@ -378,7 +282,7 @@ __device__ __forceinline__ void probe_queue(const ProbeArgs& a, RowQueue& q, uin
         // Each stream steps along its chain, or takes the row it loaded ahead
         // and loads the queue's next row in its place.
 #pragma unroll
-        for (int s = 0; s < JP_S; ++s) {
+        for (int s = 0; s < S; ++s) {
             const bool swap = live[s] && !go[s];
             uint64_t i = 0;
             const bool got = queue_next(q, __ballot_sync(0xFFFFFFFFu, swap && plive[s]), &i);
@@ -399,15 +303,6 @@ __device__ __forceinline__ void probe_queue(const ProbeArgs& a, RowQueue& q, uin
         }
     }
     warp_flush(a, ws, cnt);
-}
-
-// Rows [begin, end) split evenly over `warps` warps; this warp's share.
-__device__ __forceinline__ void warp_share(uint64_t begin, uint64_t end, uint64_t w, uint64_t warps, uint64_t* b,
-                                           uint64_t* e) {
-    const uint64_t len = end - begin;
-    const uint64_t per = (len + warps - 1) / warps;
-    *b = begin + min(len, w * per);
-    *e = begin + min(len, (w + 1) * per);
 }
 
 }  // namespace olap
