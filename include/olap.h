@@ -135,7 +135,7 @@ typedef enum {
 
 /* Cache path of the join probe's random bucket reads. */
 typedef enum {
-    OLAP_LOADS_AUTO = 0,        /* the default: L2_ONLY */
+    OLAP_LOADS_AUTO = 0,        /* the default: L2_ONLY, L1 for a probe made direct by a skewed sample */
     OLAP_LOADS_L1 = 1,          /* read-only path through L1 (ld.global.nc) */
     OLAP_LOADS_L2_ONLY = 2      /* bypass L1 (ld.global.cg): no L1 line fills for 32-byte reads */
 } olap_loads;
@@ -372,12 +372,19 @@ olap_status olap_join_probe_async(olap_ctx* ctx, const olap_join_table* table, c
  * parallel probing): *parts = 1 for the direct probe (one kernel), else the
  * number of radix partitions of the partitioned probe (a count, a scatter and
  * a probe kernel).  Decided by the context's join_partitions option and, when
- * automatic, by the table's size against the device's L2.  Host arithmetic
- * only; OLAP_E_INVALID for a NULL or freed table or a NULL *parts. */
+ * automatic, by the table's size against the device's L2.  An automatic
+ * partitioned plan is confirmed on the device by a sample of the probe keys:
+ * when they repeat (a skewed stream: at least a fifth of the sampled keys
+ * that reach the probe equal an earlier one), the partition kernels return at
+ * once and the probe reads its rows directly, its bucket reads through L1
+ * unless join_bucket_loads says otherwise; olap_join_probe_info_last reports
+ * what ran.  Host arithmetic only; OLAP_E_INVALID for a NULL or freed table
+ * or a NULL *parts. */
 olap_status olap_join_probe_partitions(olap_ctx* ctx, const olap_join_table* table, uint64_t n, int* parts);
 
 /* How the last probe enqueued on this context ran: *parts as
- * olap_join_probe_partitions; *prefiltered = 1 when the Bloom pre-probe
+ * olap_join_probe_partitions, or 1 when the device-side sample made an
+ * automatic partitioned probe direct; *prefiltered = 1 when the Bloom pre-probe
  * dropped rows before the probe (0 when it was not used or the sample said
  * not to); *rows_probed = the probe rows left after it (n when not used).
  * Waits for the context's stream.  OLAP_E_INVALID for NULL outputs or when no

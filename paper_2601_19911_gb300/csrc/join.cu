@@ -116,27 +116,34 @@ __global__ void __launch_bounds__(JB_TPB) join_side_kernel(const int64_t* keys, 
 // by partition (pass 3 of the partitioned probe): there the chunks come out in
 // partition order, so the warps of the whole grid work on one partition's
 // table slice at a time and that slice stays in L2.
-// With the Bloom pre-probe (pf non-NULL and active on the device) the row
-// count is the number of rows it kept, and a direct probe reads those rows
-// (pf_keys non-NULL); a partitioned probe already reads them reordered.
+// `args` holds the rows as launched (the probe's input, or its partitioned
+// rows).  The device-side plan (ctl, when non-NULL) may change that: with the
+// Bloom pre-probe active the row count is the number of rows it kept, and
+// with `redirect` the rows are read from where the plan says (the kept rows,
+// or the input when the partition passes were skipped), through L1 when the
+// plan says so.
 template <bool L2_ONLY>
 __global__ void __launch_bounds__(JP_TPB, 4) join_probe_kernel(ProbeArgs args, unsigned long long* next_row,
-                                                               const PrefilterCtl* pf, const int64_t* pf_keys,
-                                                               const uint32_t* pf_rowids) {
+                                                               const ProbeCtl* ctl) {
     extern __shared__ __align__(16) uint2 stage[];
     const unsigned warp = threadIdx.x >> 5;
     ProbeArgs a = args;
-    if (pf && pf->active) {
-        a.n = pf->count;
-        if (pf_keys) {
-            a.keys = pf_keys;
-            a.rowids = pf_rowids;
+    bool l1 = !L2_ONLY;
+    if (ctl) {
+        if (ctl->active) a.n = ctl->count;
+        if (ctl->redirect) {
+            a.keys = ctl->keys;
+            a.rowids = ctl->rowids;
         }
+        l1 = l1 || ctl->l1;
     }
     RowQueue q;
     q.counter = next_row;
     q.n = a.n;
-    probe_queue<L2_ONLY, JP_S>(a, q, stage + warp * JP_WCAP);
+    if (l1)
+        probe_queue<false, JP_S>(a, q, stage + warp * JP_WCAP);
+    else
+        probe_queue<true, JP_S>(a, q, stage + warp * JP_WCAP);
 }
 
 // ---- Bloom pre-probe ------------------------------------------------------
@@ -163,28 +170,72 @@ constexpr uint64_t PF_MIN_N = 1ull << 20;      // smaller probes skip the pre-pr
 constexpr int PF_PER = 4;                      // keys per lane per step
 constexpr unsigned PF_WCAP = 256;              // rows staged per warp
 
-// Decide on the device whether the pre-probe runs: a stratified sample of
-// PF_SAMPLE probe keys (n >= PF_SAMPLE) against the filter; it runs when at
-// most 60 % pass (or always when forced).  Also zeroes the kept-row count.
-__global__ void __launch_bounds__(PF_TPB) join_prefilter_sample_kernel(const int64_t* keys, uint64_t n,
-                                                                       const uint32_t* bloom, uint64_t bmask,
-                                                                       int force, PrefilterCtl* ctl) {
-    __shared__ unsigned passes;
-    if (threadIdx.x == 0) passes = 0;
+constexpr int PLAN_SLOTS = 2 * PF_SAMPLE;      // fingerprint set of the sample (32 KB)
+
+// The probe's plan, decided on the device from a stratified sample of
+// PF_SAMPLE probe keys (n >= PF_SAMPLE; fewer rows are each taken once or
+// more).  With a Bloom filter (pf_mode 1 = automatic, 2 = forced) the
+// pre-probe runs when at most 60 % of the sample may be in the table, or
+// always when forced.  With `skew_check` the probe skips its partition passes
+// when the rows it will probe repeat: at least a fifth of the sampled keys
+// that reach the probe (those the filter keeps, when it runs) equal an
+// earlier sampled key.  Such a stream sends most probes to a few hot buckets,
+// which stay in cache, while the partition passes would cost two more passes
+// over the rows.  A key's repeats are found by a 32-bit fingerprint in a
+// shared-memory set; a fingerprint collision counts as a repeat (about
+// 2^-9 of one per sample).  Zeroes the kept-row count and tells the probe
+// kernel where its rows are: the partitioned rows (`partitioned` and not
+// direct, as launched), else the kept rows (pf_keys, pf_rowids) when the
+// pre-probe runs, else the input; a direct probe reads buckets through L1
+// when `skew_l1`.
+__global__ void __launch_bounds__(PF_TPB) join_probe_plan_kernel(const int64_t* keys, const uint32_t* rowids,
+                                                                 uint64_t n, const uint32_t* bloom, uint64_t bmask,
+                                                                 int pf_mode, int skew_check, int partitioned,
+                                                                 int skew_l1, const int64_t* pf_keys,
+                                                                 const uint32_t* pf_rowids, ProbeCtl* ctl) {
+    __shared__ uint32_t fset[PLAN_SLOTS];
+    __shared__ unsigned passes, dup_all, dup_kept;
+    for (int j = threadIdx.x; j < PLAN_SLOTS; j += PF_TPB) fset[j] = 0u;
+    if (threadIdx.x == 0) passes = dup_all = dup_kept = 0;
     __syncthreads();
-    unsigned mine = 0;
-    if (!force) {
-        for (int j = threadIdx.x; j < PF_SAMPLE; j += PF_TPB) {
-            const uint64_t key = static_cast<uint64_t>(keys[(static_cast<uint64_t>(j) * n) / PF_SAMPLE]);
-            const bool maybe = bloom_maybe(bloom, bmask, key);
-            mine += (key == JN_EMPTY || maybe) ? 1u : 0u;
+    unsigned m_pass = 0, m_dup = 0, m_dup_kept = 0;
+    for (int j = threadIdx.x; j < PF_SAMPLE; j += PF_TPB) {
+        const uint64_t key = static_cast<uint64_t>(keys[(static_cast<uint64_t>(j) * n) / PF_SAMPLE]);
+        const bool kept = bloom ? (key == JN_EMPTY || bloom_maybe(bloom, bmask, key)) : true;
+        m_pass += kept ? 1u : 0u;
+        if (skew_check) {
+            const uint32_t fp = static_cast<uint32_t>(fmix64(key) >> 32) | 1u;   // 0 marks a free slot
+            uint32_t slot = fp & (PLAN_SLOTS - 1);
+            bool dup = false;
+            for (int tries = 0; tries < PLAN_SLOTS; ++tries) {
+                const uint32_t prev = atomicCAS(&fset[slot], 0u, fp);
+                if (prev == 0u) break;
+                if (prev == fp) {
+                    dup = true;
+                    break;
+                }
+                slot = (slot + 1) & (PLAN_SLOTS - 1);
+            }
+            m_dup += dup ? 1u : 0u;
+            m_dup_kept += (dup && kept) ? 1u : 0u;
         }
     }
-    atomicAdd(&passes, mine);
+    atomicAdd(&passes, m_pass);
+    atomicAdd(&dup_all, m_dup);
+    atomicAdd(&dup_kept, m_dup_kept);
     __syncthreads();
     if (threadIdx.x == 0) {
-        ctl->active = (force || passes * 10u <= static_cast<unsigned>(PF_SAMPLE) * 6u) ? 1 : 0;
+        const bool active = bloom && (pf_mode == 2 || passes * 10u <= static_cast<unsigned>(PF_SAMPLE) * 6u);
+        const unsigned reach = active ? passes : static_cast<unsigned>(PF_SAMPLE);
+        const unsigned rep = active ? dup_kept : dup_all;
+        const bool direct = skew_check && reach >= 64u && rep * 5u >= reach;
+        ctl->active = active ? 1 : 0;
+        ctl->direct = direct ? 1 : 0;
         ctl->count = 0;
+        ctl->redirect = (!partitioned || direct) ? 1 : 0;
+        ctl->keys = active ? pf_keys : keys;
+        ctl->rowids = active ? pf_rowids : rowids;
+        ctl->l1 = (direct && skew_l1) ? 1 : 0;
     }
 }
 
@@ -193,7 +244,7 @@ __global__ void __launch_bounds__(PF_TPB) join_prefilter_sample_kernel(const int
 // appended with their row-ids through a per-warp stage, one atomic per flush.
 __global__ void __launch_bounds__(PF_TPB) join_prefilter_kernel(const int64_t* keys, const uint32_t* rowids,
                                                                 uint64_t n, const uint32_t* bloom, uint64_t bmask,
-                                                                PrefilterCtl* ctl, int64_t* out_keys,
+                                                                ProbeCtl* ctl, int64_t* out_keys,
                                                                 uint32_t* out_rowids) {
     if (!ctl->active) return;
     __shared__ int64_t sk[PF_TPB / 32][PF_WCAP];
@@ -267,8 +318,8 @@ struct PartArgs {
     unsigned long long* pstart;                // [parts + 1] partition offsets (written by CTA 0)
     int64_t* out_keys;
     uint32_t* out_rowids;
-    const PrefilterCtl* pf;                    // non-NULL: rows may come from the Bloom pre-probe
-    const int64_t* pf_keys;                    // its surviving rows, used when pf->active
+    const ProbeCtl* pf;                        // non-NULL: the device-side plan (pre-probe, direct)
+    const int64_t* pf_keys;                    // the pre-probe's surviving rows, used when pf->active
     const uint32_t* pf_rowids;
 };
 
@@ -291,6 +342,7 @@ __device__ __forceinline__ unsigned part_of(uint64_t key, const PartArgs& a) {
 // Pass 1: rows of each partition in the tiles of this CTA (tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...).
 __global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs args) {
+    if (args.pf && args.pf->direct) return;
     const PartArgs a = part_source(args);
     __shared__ unsigned h[JQ_PMAX];
     for (int p = threadIdx.x; p < a.parts; p += JQ_TPB) h[p] = 0;
@@ -324,6 +376,7 @@ __global__ void __launch_bounds__(JQ_TPB) join_part_count_kernel(PartArgs args) 
 // overwrite the reorder buffer before every thread has passed its first
 // barrier, which it reaches only after writing this tile out.
 __global__ void __launch_bounds__(JQ_TPB) join_part_scatter_kernel(PartArgs args) {
+    if (args.pf && args.pf->direct) return;
     const PartArgs a = part_source(args);
     __shared__ unsigned h[2][JQ_PMAX];
     __shared__ unsigned off[JQ_PMAX];
@@ -508,7 +561,8 @@ bool probe_prefilter(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) 
 }
 
 // Partition scratch: [partitioned keys | row-ids | count matrix | partition
-// starts]; then, with the pre-probe, [kept keys | kept row-ids | control].
+// starts]; then, with the pre-probe, [kept keys | kept row-ids].  The probe's
+// device-side plan lives in the context's small device area.
 size_t probe_part_bytes(const olap_ctx* ctx, uint64_t n, int parts) {
     if (parts <= 1) return 0;
     // room for the largest grid the partition passes can take
@@ -519,7 +573,7 @@ size_t probe_part_bytes(const olap_ctx* ctx, uint64_t n, int parts) {
 size_t probe_scratch_bytes(const olap_ctx* ctx, const olap_join_table* t, uint64_t n) {
     const size_t pb = probe_part_bytes(ctx, n, probe_parts(ctx, t, n));
     if (!probe_prefilter(ctx, t, n)) return pb;
-    return pb + align256(n * 8) + align256(n * 4) + align256(sizeof(PrefilterCtl));
+    return pb + align256(n * 8) + align256(n * 4);
 }
 
 }  // namespace olap
@@ -554,21 +608,23 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     a.count = reinterpret_cast<unsigned long long*>(d_count);
     const int parts = probe_parts(ctx, t, n);
     const bool pre = probe_prefilter(ctx, t, n);
+    // the sample may still turn an automatically partitioned probe direct
+    const bool skew_check = parts > 1 && ctx->opts.join_partitions == 0;
     PartArgs q{};
     unsigned qgrid = 0;
-    PrefilterCtl* pf = nullptr;
+    ProbeCtl* pf = nullptr;
     int64_t* pf_keys = nullptr;
     uint32_t* pf_rowids = nullptr;
     if (parts > 1 || pre) {
         olap_status st = ensure_part(ctx, probe_scratch_bytes(ctx, t, n));
         if (st != OLAP_OK) return st;
     }
+    if (pre || skew_check) pf = reinterpret_cast<ProbeCtl*>(static_cast<unsigned char*>(ctx->aux) + 1024);
     if (pre) {
         unsigned char* m = static_cast<unsigned char*>(ctx->part) + probe_part_bytes(ctx, n, parts);
         pf_keys = reinterpret_cast<int64_t*>(m);
         pf_rowids = reinterpret_cast<uint32_t*>(m + align256(n * 8));
-        pf = reinterpret_cast<PrefilterCtl*>(m + align256(n * 8) + align256(n * 4));
-        if (reinterpret_cast<unsigned char*>(pf + 1) > static_cast<unsigned char*>(ctx->part) + ctx->part_bytes)
+        if (m + align256(n * 8) + align256(n * 4) > static_cast<unsigned char*>(ctx->part) + ctx->part_bytes)
             return fail(ctx, OLAP_E_INVALID, "probe pre-filter scratch too small");
     }
     if (parts > 1) {
@@ -603,29 +659,30 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     if ((e = cudaMemsetAsync(next_row, 0, sizeof(unsigned long long), s)) != cudaSuccess)
         return cuda_fail(ctx, e, "probe queue reset");
     ProbeArgs pa = a;
-    if (pre) {
-        const uint64_t bmask = t->bloom_blocks - 1;
-        join_prefilter_sample_kernel<<<1, PF_TPB, 0, s>>>(d_keys, n, t->bloom, bmask,
-                                                          ctx->opts.join_prefilter == OLAP_PREFILTER_ON, pf);
+    const uint64_t bmask = pre ? t->bloom_blocks - 1 : 0;
+    if (pf) {
+        const int pf_mode = pre ? (ctx->opts.join_prefilter == OLAP_PREFILTER_ON ? 2 : 1) : 0;
+        const int skew_l1 = ctx->opts.join_bucket_loads == OLAP_LOADS_AUTO ? 1 : 0;
+        join_probe_plan_kernel<<<1, PF_TPB, 0, s>>>(d_keys, d_rowids, n, pre ? t->bloom : nullptr, bmask, pf_mode,
+                                                    skew_check ? 1 : 0, parts > 1 ? 1 : 0, skew_l1, pf_keys,
+                                                    pf_rowids, pf);
+    }
+    if (pre)
         join_prefilter_kernel<<<ctx->sm_count * 4, PF_TPB, 0, s>>>(d_keys, d_rowids, n, t->bloom, bmask, pf,
                                                                    pf_keys, pf_rowids);
-    }
-    const int64_t* direct_keys = pre ? pf_keys : nullptr;   // the direct probe reads the kept rows
-    const uint32_t* direct_rowids = pre ? pf_rowids : nullptr;
     if (parts > 1) {
         join_part_count_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
         join_part_scatter_kernel<<<qgrid, JQ_TPB, 0, s>>>(q);
         pa.keys = q.out_keys;
         pa.rowids = q.out_rowids;
-        direct_keys = nullptr;
-        direct_rowids = nullptr;
     }
     if (ctx->opts.join_bucket_loads == OLAP_LOADS_L1)
-        join_probe_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row, pf, direct_keys, direct_rowids);
+        join_probe_kernel<false><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row, pf);
     else
-        join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row, pf, direct_keys, direct_rowids);
+        join_probe_kernel<true><<<grid, JP_TPB, JP_SMEM, s>>>(pa, next_row, pf);
     e = cudaGetLastError();
-    if (e == cudaSuccess) ctx->launches += (parts > 1 ? 3 : 1) + (pre ? 2 : 0);   // [sample, filter,] [count, scatter,] probe
+    // [plan,] [filter,] [count, scatter,] probe
+    if (e == cudaSuccess) ctx->launches += (pf ? 1 : 0) + (pre ? 1 : 0) + (parts > 1 ? 2 : 0) + 1;
     if (e == cudaSuccess && ctx->time_kernels) e = cudaEventRecord(ctx->kev[5], s);
     return e == cudaSuccess ? OLAP_OK : cuda_fail(ctx, e, "probe launch");
 }
@@ -859,13 +916,14 @@ olap_status olap_join_probe_info_last(olap_ctx* ctx, int* parts, int* prefiltere
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "probe info");
     if (ctx->last_probe_pf) {
-        PrefilterCtl c;
+        ProbeCtl c;
         e = cudaMemcpy(&c, ctx->last_probe_pf, sizeof(c), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "probe info");
         if (c.active) {
             *prefiltered = 1;
             *rows_probed = c.count;
         }
+        if (c.direct) *parts = 1;
     }
     return OLAP_OK;
 }

@@ -89,13 +89,18 @@ __device__ __forceinline__ bool bloom_maybe(const uint32_t* bloom, uint64_t bmas
     return (a & want01) == want01 && (b & want23) == want23 && (c & want45) == want45 && (d & want67) == want67;
 }
 
-// Device-side state of one probe's Bloom pre-probe: whether the rows were
-// filtered, and how many passed.  The stages after the filter read it, so the
-// decision never travels through the host.
-struct PrefilterCtl {
-    int active;
-    int pad;
-    unsigned long long count;
+// Device-side plan of one probe, written by its sampling stage: whether the
+// Bloom pre-probe filters the rows (and how many it kept), and whether the
+// probe skips the partition passes and reads its rows directly.  The stages
+// after the sample read it, so the decision never travels through the host.
+struct ProbeCtl {
+    int active;                    // the pre-probe drops rows
+    int direct;                    // the partition passes are skipped
+    unsigned long long count;      // rows the pre-probe kept
+    const int64_t* keys;           // with `redirect`: the rows the probe kernel reads
+    const uint32_t* rowids;
+    int redirect;
+    int l1;                        // the probe's bucket reads go through L1
 };
 
 struct ProbeArgs {

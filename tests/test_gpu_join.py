@@ -267,6 +267,42 @@ def test_prefilter_auto_decides_on_the_device():
         off.close()
 
 
+@pytest.mark.parametrize("loads", [olap.LOADS_AUTO, olap.LOADS_L2_ONLY])
+@pytest.mark.parametrize("prefilter", [olap.PREFILTER_AUTO, olap.PREFILTER_OFF])
+def test_skewed_probe_goes_direct(prefilter, loads):
+    """A table above L2 with a probe side large enough to partition: the
+    device-side sample sends a Zipf-distributed probe stream (its sampled keys
+    repeat) straight to the direct probe, skipping the partition passes, and
+    leaves a uniform stream partitioned; the pairs match the oracle either
+    way, with the pre-probe on its own choice or off, through either bucket
+    load path."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0, join_prefilter=prefilter, join_bucket_loads=loads)
+    try:
+        b = datagen.join_build(1 << 22, "mult14", seed=36)
+        t = c.join_build(torch.from_numpy(b.keys).cuda())
+        n = (1 << 21) + 13
+        planned = c.join_probe_partitions(t, n)
+        assert planned > 1
+        for dist, hit, direct in (("zipf", 0.9, True), ("uniform", 0.9, False), ("zipf", 0.1, None)):
+            p = datagen.join_probe(n, b, hit, dist, seed=36)
+            need = p.expected_pairs(b)
+            out = torch.empty((need, 2), dtype=torch.int32, device="cuda")
+            got = c.join_probe(t, torch.from_numpy(p.keys).cuda(), out=out)
+            info = c.join_probe_info()
+            if direct is not None:
+                assert info["parts"] == (1 if direct else planned)
+            elif prefilter == olap.PREFILTER_AUTO:
+                # hit rate 0.1: the kept rows are mostly the Zipf hits, which repeat
+                assert info["prefiltered"] and info["parts"] == 1
+            assert got.shape[0] == need
+            np.testing.assert_array_equal(packed(got.cpu().numpy().view(np.uint32)), oracle.join(b.keys, p.keys))
+        t.free()
+    finally:
+        c.close()
+
+
 _BUILDS = {}
 
 
@@ -302,7 +338,9 @@ def test_full_size(ctx, mult, dist, hit):
     ctx.sync()
     t.free()
     assert int(cnt.item()) == need
-    assert ctx.join_probe_info()["prefiltered"] == (hit < 0.5)      # the automatic pre-probe's choice
+    info = ctx.join_probe_info()
+    assert info["prefiltered"] == (hit < 0.5)                 # the automatic pre-probe's choice
+    assert (info["parts"] == 1) == (dist == "zipf")           # the sample's skew check: Zipf probes go direct
     pr = out[:, 0].to(torch.int64) & 0xFFFFFFFF
     br = out[:, 1].to(torch.int64) & 0xFFFFFFFF
     assert bool((pr < (1 << 28)).all()) and bool((br < (1 << 24)).all())
