@@ -134,8 +134,54 @@ __device__ __forceinline__ WarpStage warp_stage(unsigned char* base) {
     return WarpStage{reinterpret_cast<uint64_t*>(p), reinterpret_cast<uint32_t*>(p + WS_CAP * 8), 0u};
 }
 
+// The select's first radix pass, folded into the streaming filter (the
+// register and two-column filters).  Every candidate already passes through
+// a warp stage; as it leaves, its digit at the first bit where candidates can
+// differ (just below the threshold's leading zeros, the select's first pass
+// position) is counted in a CTA histogram in shared memory, which the CTA adds
+// to the select's pass-0 histogram when it is done.  The select then starts
+// at the bucket pick, one pass over the candidates and one grid barrier
+// sooner.  (The pass's AND / OR fold, which lets a pass skip bits all its
+// entries share, is left to the select's later passes: four 64-bit shared
+// atomics per candidate slowed the streaming pass by 5-10 %.)
+__shared__ unsigned g_fuse_hist[TK_BINS];
+
+// Bit position and width of the fused digit (those of the select's first pass).
+struct FuseDigit {
+    int L, d, kb;
+};
+__device__ __forceinline__ FuseDigit fuse_digit(const TopkArgs& a, uint64_t t) {
+    FuseDigit f;
+    f.kb = a.w4 ? 32 : 64;
+    const int lz = __clzll(static_cast<long long>(t));
+    f.L = lz < f.kb ? lz : f.kb;
+    f.d = min(a.digit, f.kb + 32 - f.L);
+    return f;
+}
+
+template <int TPB>
+__device__ __forceinline__ void fuse_init() {
+    for (int b = threadIdx.x; b < TK_BINS; b += TPB) g_fuse_hist[b] = 0;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void fuse_add(const FuseDigit& f, uint64_t r, uint32_t rid) {
+    uint64_t w0, w1;
+    comp_words(r, rid, f.kb, w0, w1);
+    atomicAdd(&g_fuse_hist[comp_digit(w0, w1, f.L, f.d)], 1u);
+}
+
+// Whole CTA, after its last candidate: add the CTA's counts to the pass-0
+// histogram (non-zero bins only).
+template <int TPB>
+__device__ __forceinline__ void fuse_merge(const TopkArgs& a) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < TK_BINS; b += TPB)
+        if (g_fuse_hist[b]) atomicAdd(&a.ghist[b], g_fuse_hist[b]);
+}
+
 // Move the warp's staged hits to the candidate buffer (all 32 lanes call).
-__device__ __forceinline__ void stage_flush(const TopkArgs& a, WarpStage& ws) {
+__device__ __forceinline__ void stage_flush_plain(const TopkArgs& a, WarpStage& ws) {
     if (ws.count == 0) return;
     __syncwarp();
     const unsigned lane = threadIdx.x & 31u;
@@ -154,10 +200,46 @@ __device__ __forceinline__ void stage_flush(const TopkArgs& a, WarpStage& ws) {
     ws.count = 0;
 }
 
+// The same, also counting the hits for the fused first pass.  Kept out of
+// line: it runs once per WS_CAP hits of a warp, and inlined into the
+// filter's unrolled loop it would cost the loop registers (occupancy).
+__device__ __forceinline__ void stage_flush_fused(const TopkArgs& a, const uint64_t* sr, const uint32_t* sidx,
+                                               unsigned count) {
+    __syncwarp();
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctl->cand_count, static_cast<unsigned long long>(count));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    const FuseDigit f = fuse_digit(a, __ldcg(&a.ctl->thresh));
+    for (unsigned j = lane; j < count; j += 32) {
+        const unsigned long long pos = base + j;
+        const uint32_t idx = sidx[j];
+        const uint64_t r = sr[j];
+        const uint32_t rid = a.rowids ? a.rowids[idx] : idx;
+        if (pos < a.cand_cap) {
+            a.cand_r[pos] = r;
+            a.cand_rid[pos] = rid;
+        }
+        fuse_add(f, r, rid);
+    }
+    __syncwarp();
+}
+
+template <bool FUSE = false>
+__device__ __forceinline__ void stage_flush(const TopkArgs& a, WarpStage& ws) {
+    if (!FUSE) {
+        stage_flush_plain(a, ws);
+        return;
+    }
+    if (ws.count == 0) return;
+    stage_flush_fused(a, ws.r, ws.idx, ws.count);
+    ws.count = 0;
+}
+
 // Test the VEC keys of one 16-byte vector (keys idx0 .. idx0 + VEC - 1)
 // against the threshold and stage the hits.  Called by all 32 lanes of a
 // warp together.
-template <bool W4>
+template <bool W4, bool FUSE = false>
 __device__ __forceinline__ void filter_vector(const TopkArgs& a, const KeyLimit& lim, uint4 x, bool valid,
                                               uint64_t idx0, WarpStage& ws) {
     constexpr int VEC = W4 ? 4 : 2;
@@ -188,7 +270,7 @@ __device__ __forceinline__ void filter_vector(const TopkArgs& a, const KeyLimit&
         bal[e] = __ballot_sync(0xFFFFFFFFu, (hit >> e) & 1u);
         total += __popc(bal[e]);
     }
-    if (ws.count + total > WS_CAP) stage_flush(a, ws);
+    if (ws.count + total > WS_CAP) stage_flush<FUSE>(a, ws);
     unsigned before = ws.count;
     const uint32_t w[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -208,6 +290,7 @@ __device__ __forceinline__ void filter_vector(const TopkArgs& a, const KeyLimit&
 
 // The unaligned head [0, head) and ragged tail [tail0, n) of the keys: at
 // most 2 * VEC - 2 keys, one per lane of warp 0 of CTA 0.
+template <bool FUSE = false>
 __device__ __forceinline__ void filter_ends(const TopkArgs& a, uint64_t t, uint64_t head, uint64_t tail0) {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const uint64_t rest = head + (a.n - tail0);
@@ -226,10 +309,12 @@ __device__ __forceinline__ void filter_ends(const TopkArgs& a, uint64_t t, uint6
     base = __shfl_sync(0xFFFFFFFFu, base, 0);
     if (hit) {
         const unsigned long long pos = base + __popc(bal & ((1u << threadIdx.x) - 1u));
+        const uint32_t rid = a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx);
         if (pos < a.cand_cap) {
             a.cand_r[pos] = r;
-            a.cand_rid[pos] = a.rowids ? a.rowids[idx] : static_cast<uint32_t>(idx);
+            a.cand_rid[pos] = rid;
         }
+        if (FUSE) fuse_add(fuse_digit(a, t), r, rid);
     }
 }
 
@@ -262,11 +347,11 @@ __device__ void filter_pass(const TopkArgs& a, uint64_t t, unsigned char* stage_
 #pragma unroll
         for (int u = 0; u < TK_UNROLL; ++u) {
             const uint64_t vi = bb + static_cast<uint64_t>(u) * TPB + threadIdx.x;
-            filter_vector<W4>(a, lim, v[u], vi < nvec, head + vi * VEC, ws);
+            filter_vector<W4, true>(a, lim, v[u], vi < nvec, head + vi * VEC, ws);
         }
     }
-    stage_flush(a, ws);
-    filter_ends(a, t, head, tail0);
+    stage_flush<true>(a, ws);
+    filter_ends<true>(a, t, head, tail0);
 }
 
 // The 32-bit order-preserving transform of one 4-byte key kind as two masks:
@@ -308,7 +393,7 @@ __device__ __forceinline__ void filter_vector_pair(const TopkArgs& a, uint64_t t
         bal[e] = __ballot_sync(0xFFFFFFFFu, (hit >> e) & 1u);
         total += __popc(bal[e]);
     }
-    if (ws.count + total > WS_CAP) stage_flush(a, ws);
+    if (ws.count + total > WS_CAP) stage_flush<true>(a, ws);
     unsigned before = ws.count;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -361,8 +446,8 @@ __device__ void filter_pass_pair(const TopkArgs& a, uint64_t t, unsigned char* s
                 filter_vector_pair(a, t, m0, m1, x0[u], x1[u], vi < nvec, head + vi * 4, ws);
             }
         }
-        stage_flush(a, ws);
-        filter_ends(a, t, head, tail0);
+        stage_flush<true>(a, ws);
+        filter_ends<true>(a, t, head, tail0);
         return;
     }
     const uint64_t stride = static_cast<uint64_t>(TPB) * gridDim.x;
@@ -374,7 +459,7 @@ __device__ void filter_pass_pair(const TopkArgs& a, uint64_t t, unsigned char* s
         const bool hit = i < n && r <= t;
         const unsigned bal = __ballot_sync(0xFFFFFFFFu, hit);
         if (!bal) continue;
-        if (ws.count + __popc(bal) > WS_CAP) stage_flush(a, ws);
+        if (ws.count + __popc(bal) > WS_CAP) stage_flush<true>(a, ws);
         if (hit) {
             const unsigned pos = ws.count + __popc(bal & static_cast<unsigned>(lt));
             ws.r[pos] = r;
@@ -382,7 +467,7 @@ __device__ void filter_pass_pair(const TopkArgs& a, uint64_t t, unsigned char* s
         }
         ws.count += __popc(bal);
     }
-    stage_flush(a, ws);
+    stage_flush<true>(a, ws);
 }
 
 // Issue the bulk copy of the tile at byte offset `off` of the key body into
@@ -676,10 +761,12 @@ __global__ void __launch_bounds__(TKF_TPB, 4) topk_filter_bulk_kernel(TopkArgs a
 // Kernel 2 of 3, register-load flavour (TPB threads; the per-warp stages are
 // dynamic shared memory, (TPB / 32) * WS_BYTES).
 template <bool W4, int TPB>
-__global__ void __launch_bounds__(TPB) topk_filter_regs_kernel(TopkArgs a) {
+__global__ void __launch_bounds__(TPB, 1024 / TPB) topk_filter_regs_kernel(TopkArgs a) {
     extern __shared__ __align__(16) unsigned char stage[];
     const uint64_t t = __ldcg(&a.ctl->thresh);
+    fuse_init<TPB>();
     filter_pass<W4, TPB>(a, t, stage);
+    fuse_merge<TPB>(a);
 }
 
 // Kernel 2 of 3 for a two-column key (register loads of both columns).
@@ -687,7 +774,9 @@ template <int TPB>
 __global__ void __launch_bounds__(TPB, 1024 / TPB) topk_filter_pair_kernel(TopkArgs a) {
     extern __shared__ __align__(16) unsigned char stage[];
     const uint64_t t = __ldcg(&a.ctl->thresh);
+    fuse_init<TPB>();
     filter_pass_pair<TPB>(a, t, stage);
+    fuse_merge<TPB>(a);
 }
 
 // Kernel 3 of 3 (cooperative): refine, split, finish and sort.
@@ -720,20 +809,32 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
     // all at or below the threshold, so they share its leading zero bits: the
     // refine starts below them.
     uint64_t p0 = 0, p1 = 0, krem = a.k, bcnt = src_n;
-    int L = 0, pass = 0;
+    int L = 0, pass = 0, npass = 0;
     if (cand) {
         const int lz = __clzll(static_cast<long long>(__ldcg(&ctl->thresh)));
         L = lz < kb ? lz : kb;
     }
+    // With the filter's fused first pass, pass 0's histogram is ready on the
+    // candidate path; on the fallback path it holds the filter's partial
+    // counts, so the passes start at buffer 1 (clean) and pass 2 clears
+    // buffer 0 before pass 3 uses it.
+    bool ready = a.fuse && cand;
+    if (a.fuse && !cand) pass = 1;
     while (bcnt > TK_SMALL && L < TB && krem < bcnt) {
         const int d = min(a.digit, TB - L);
         unsigned* gh = a.ghist + (pass % 3) * TK_BINS;
         unsigned* gz = a.ghist + ((pass + 1) % 3) * TK_BINS;
         unsigned long long* ao = ctl->ao[pass % 3];
-        hist_pass(a, cand, src_n, p0, p1, L, d, kb, gh, gz, sh, ao, ctl->ao[(pass + 1) % 3]);
-        if (!grid_sync(a.bar, &ctl->err)) return report(a);
+        const bool fused_pass = ready;
+        if (!ready) {
+            hist_pass(a, cand, src_n, p0, p1, L, d, kb, gh, gz, sh, ao, ctl->ao[(pass + 1) % 3]);
+            if (!grid_sync(a.bar, &ctl->err)) return report(a);
+        }
+        ready = false;
+        ++npass;
         const Pick pk = pick_bucket<TK_TPB>(gh, krem, sc);
-        const bool whole = pk.below == 0 && pk.in_b == bcnt;     // every matching entry in one bucket
+        // every matching entry in one bucket (the fused pass folds no AND / OR)
+        const bool whole = pk.below == 0 && pk.in_b == bcnt && !fused_pass;
         krem -= pk.below;
         bcnt = pk.in_b;
         prefix_set(p0, p1, L, d, pk.b);
@@ -750,8 +851,11 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
         }
         ++pass;
     }
+    // The buffer at pass % 3 must be clean for the finish: when the fused
+    // pass-0 histogram was never consumed, buffer 1 (zeroed by prepare) is.
+    if (ready) pass = 1;
     if (stamp) {
-        ctl->passes = pass;
+        ctl->passes = npass;
         ctl->ts[3] = use_ts3;
         ctl->ts[4] = gtimer();
     }
@@ -1169,6 +1273,20 @@ static bool set_kernel_attrs(int device) {
                              lim) != cudaSuccess ||
         cudaFuncSetAttribute(topk_filter_bulk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              lim) != cudaSuccess ||
+        // the register filters' stages are dynamic, next to the fused pass's
+        // static histogram: above 48 KB together, so every variant opts in
+        cudaFuncSetAttribute(topk_filter_regs_kernel<false, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             8 * WS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_regs_kernel<true, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             8 * WS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_pair_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             8 * WS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_regs_kernel<false, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             16 * WS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_regs_kernel<true, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             16 * WS_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(topk_filter_pair_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             16 * WS_BYTES) != cudaSuccess ||
         cudaFuncSetAttribute(topk_filter_regs_kernel<false, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              32 * WS_BYTES) != cudaSuccess ||
         cudaFuncSetAttribute(topk_filter_regs_kernel<true, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1232,6 +1350,8 @@ cudaError_t topk_launch(const TopkArgs& args, const TopkGeom& geom, cudaStream_t
     a.stages = geom.stages;
     if (a.digit == 0) a.digit = TK_DIG;
     if (a.digit < TK_DIG_MIN || a.digit > TK_DIG) return cudaErrorInvalidValue;
+    // the register and two-column filters fold the select's first pass
+    a.fuse = a.use_sample && (a.pair || a.filter == TK_FILTER_REGS) ? 1 : 0;
     cudaError_t e;
     if (ev && (e = cudaEventRecord(ev[0], stream)) != cudaSuccess) return e;
     topk_prepare_kernel<<<a.use_sample ? TK_PREP_CTAS : 1, TK_TPB, 0, stream>>>(a);

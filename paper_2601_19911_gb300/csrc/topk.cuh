@@ -69,6 +69,7 @@ struct TopkArgs {
     int use_sample;
     unsigned sample_rank;            // 1-based rank of the threshold in the sample
     int filter;                      // TopkFilter
+    int fuse;                        // the filter folds the select's first radix pass (set at launch)
     int digit;                       // radix digit width, TK_DIG_MIN..TK_DIG (0 => TK_DIG)
     int tile_bytes;                  // bulk-copy size (multiple of 16 * TK_TPB)
     int stages;                      // copies in flight per CTA (<= TK_MAX_STAGES)
