@@ -32,6 +32,10 @@
  *   - Blocking calls return after the result is in the output buffers.
  *     Calls suffixed _async only enqueue work on the given stream, take device
  *     pointers only, and report device-side status through a device word.
+ *   - A context works on its own non-blocking stream, which waits for no
+ *     other stream: device buffers a blocking call reads or writes must be
+ *     complete (inputs written, outputs no longer in use) when it is made,
+ *     and an _async call on another stream must be ordered by the caller.
  *   - There is no CPU fallback: when no GPU is usable a call fails with
  *     OLAP_E_CUDA.  The gate only advises; running the CPU path is the
  *     caller's engine's job.

@@ -121,6 +121,7 @@ struct TopkGeom {
     int ctas_per_sm;       // filter CTAs per SM (cap)
     int smem_bytes;        // filter dynamic shared bytes: ring + mbarriers
     int grid;              // cooperative select kernel CTAs
+    int grid_small;        // the same for a candidate-path select with k <= TK_SMALL (one CTA per SM)
     int filter_grid;       // bulk-copy filter CTAs
     int regs_grid;         // register-load filter CTAs
     int regs_tpb;          // register-load filter threads per CTA (256, 512, 1024)

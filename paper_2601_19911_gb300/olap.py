@@ -401,6 +401,22 @@ class Context:
     def sync(self):
         self.check(self.lib.olap_ctx_sync(self.h))
 
+    def _after_torch(self, *bufs, stream: int | None = None, force: bool = False):
+        """Order the library's stream (`stream`, else the context's) after the
+        work queued on torch's current stream, when a buffer is a CUDA tensor
+        (or `force`): the library runs on its own non-blocking stream, so a
+        tensor that torch is still writing would otherwise be read early, and
+        one that torch is still clearing (a count, a status word) could be
+        cleared after the library wrote it."""
+        if not force and not any(b is not None and mem_kind(b) == MEM_DEVICE for b in bufs
+                                 if not isinstance(b, np.ndarray)):
+            return
+        torch = _torch()
+        cur = torch.cuda.current_stream()
+        target = self.stream if stream is None else int(stream)
+        if target != cur.cuda_stream:
+            torch.cuda.ExternalStream(target).wait_stream(cur)
+
     # -- Top-K ---------------------------------------------------------------
     def topk(self, keys, k: int, order: int = DESC, rowids=None, out_keys=None, out_rowids=None):
         """olap_topk: returns (out_keys, out_rowids) cut to min(k, n).
@@ -416,6 +432,7 @@ class Context:
         where = mem_kind(keys)
         _check_rowids(rowids, where, n)
         ow = mem_kind(out_keys)
+        self._after_torch(keys, rowids, out_keys, out_rowids)
         got = ctypes.c_uint64()
         st = self.lib.olap_topk(self.h, ptr(keys), kt, ptr(rowids), where, n, int(k), int(order),
                                 ptr(out_keys), ptr(out_rowids), ow, ctypes.byref(got))
@@ -440,6 +457,7 @@ class Context:
             out_keys0 = np.empty(max(cnt, 1), dtype=KEY_NUMPY[t0])
             out_keys1 = np.empty(max(cnt, 1), dtype=KEY_NUMPY[t1])
             out_rowids = np.empty(max(cnt, 1), dtype=np.uint32)
+        self._after_torch(keys0, keys1, rowids, out_keys0, out_keys1, out_rowids)
         got = ctypes.c_uint64()
         st = self.lib.olap_topk_pair(self.h, ptr(keys0), t0, int(order0), ptr(keys1), t1, int(order1), ptr(rowids),
                                      where, n, int(k), ptr(out_keys0), ptr(out_keys1), ptr(out_rowids),
@@ -461,6 +479,7 @@ class Context:
         if out_rows is None:
             out_rows = np.empty(max(cnt, 1) * row_bytes, dtype=np.uint8)
             out_rowids = np.empty(max(cnt, 1), dtype=np.uint32)
+        self._after_torch(rows, out_rows, out_rowids)
         got = ctypes.c_uint64()
         self.check(self.lib.olap_topk_rows(self.h, ptr(rows), mem_kind(rows), n, row_bytes, key_offset, key_type,
                                            int(k), int(order), ptr(out_rows), ptr(out_rowids), mem_kind(out_rows),
@@ -473,6 +492,7 @@ class Context:
         """olap_join_build over int64 keys (numpy, pinned or CUDA tensor)."""
         where = mem_kind(keys)
         _check_rowids(rowids, where, numel(keys))
+        self._after_torch(keys, rowids)
         h = ctypes.c_void_p()
         self.check(self.lib.olap_join_build(self.h, ptr(keys), ptr(rowids), where, numel(keys),
                                             float(load_factor), ctypes.byref(h)))
@@ -491,6 +511,7 @@ class Context:
             capacity = capacity if capacity is not None else max(16, 2 * n)
             out = np.empty((capacity, 2), dtype=np.uint32)
         cap = (out.shape[0] if isinstance(out, np.ndarray) else out.numel() // 2) if capacity is None else capacity
+        self._after_torch(keys, rowids, out)
         got = ctypes.c_uint64()
         st = self.lib.olap_join_probe(self.h, table.h, ptr(keys), ptr(rowids), where, n, ptr(out), mem_kind(out),
                                       cap, ctypes.byref(got))
@@ -505,6 +526,7 @@ class Context:
 
     def join_probe_async(self, table: "JoinTable", d_keys, d_out, capacity: int, d_count, d_rowids=None,
                          stream: int | None = None):
+        self._after_torch(d_keys, stream=stream, force=True)
         self.check(self.lib.olap_join_probe_async(self.h, table.h, ptr(d_keys), ptr(d_rowids), numel(d_keys),
                                                   ptr(d_out), int(capacity), ptr(d_count), stream))
 
@@ -579,6 +601,7 @@ class Context:
     def topk_async(self, d_keys, k: int, order: int, d_out_keys, d_out_rowids, d_rowids=None,
                    dev_status=None, stream: int | None = None):
         """olap_topk_async on CUDA tensors; enqueues only."""
+        self._after_torch(d_keys, stream=stream, force=True)
         st = self.lib.olap_topk_async(self.h, ptr(d_keys), key_type_of(d_keys), ptr(d_rowids),
                                       numel(d_keys), int(k), int(order), ptr(d_out_keys),
                                       ptr(d_out_rowids), ptr(dev_status), stream)
@@ -593,9 +616,11 @@ class Batch:
         self.h = h
 
     def run(self, stream: int | None = None):
+        self.ctx._after_torch(stream=stream, force=True)
         self.ctx.check(self.ctx.lib.olap_batch_run(self.h, stream))
 
     def run_per_query(self, stream: int | None = None):
+        self.ctx._after_torch(stream=stream, force=True)
         self.ctx.check(self.ctx.lib.olap_batch_run_per_query(self.h, stream))
 
     def errors(self) -> int:
