@@ -35,10 +35,11 @@ METRIC = "Top-K Gkeys/s & join probes/s (% HBM peak); batched vs per-query; gate
 
 # DRAM bytes (read + write) per input key of the Top-K filter kernel, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of that kernel at
-# 2^26 uniform keys, K = 1000, register filter; the traffic of a full launch
-# is this figure times n (the reads are the keys, the writes the candidates,
-# both in proportion to n).  Valid only for that configuration.
-FILTER_DRAM_BYTES_PER_KEY = {"i64": 540_344_320 / 2**26, "f32": 271_533_824 / 2**26}
+# 2^26 uniform keys with explicit row-ids, K = 1000, register filter; the
+# traffic of a full launch is this figure times n (the reads are the keys and
+# the candidates' row-ids, the writes the candidates, all in proportion to n).
+# Valid only for that configuration.
+FILTER_DRAM_BYTES_PER_KEY = {"i64": 546_427_136 / 2**26, "f32": 277_938_944 / 2**26}
 
 
 def _kernel_pass(ctx, steps, launch):
@@ -1113,7 +1114,7 @@ def run_ours(args):
     achieved = algo_bytes / (kern_ms * 1e-3) / 1e9
     traffic = args.traffic
     if traffic is None and top == "topk_filter_ms" and k == 1000 and args.dist == "uniform" \
-            and args.filter == "regs":
+            and args.filter == "regs" and args.rowids == "explicit":
         traffic = FILTER_DRAM_BYTES_PER_KEY[args.key_type] * n if args.key_type in FILTER_DRAM_BYTES_PER_KEY \
             else None
     line = {
