@@ -1234,7 +1234,9 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-arena", type=int, default=100_000_000)
     ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--serve-cpu-workers", type=int, default=12)
+    ap.add_argument("--serve-cpu-workers", type=int, default=4,
+                    help="host engine workers (and its threads); the rest of the host's cores stage the GPU "
+                         "requests' copies")
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-margin", type=float, default=0.0)
     ap.add_argument("--serve-cal-points", type=int, default=18)
