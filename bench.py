@@ -493,7 +493,7 @@ def fullrow_leg(args, ctx, torch):
     from paper_2601_19911_gb300 import datagen, olap
     P = args.fullrow_payload
     rb = 8 + P
-    host = olap.HostEngine(threads=args.serve_cpu_workers)
+    host = olap.HostEngine(threads=args.host_threads)
     kk = 100
     reps = args.fullrow_reps
     out = {}
@@ -578,7 +578,7 @@ def gate_leg(args, ctx, torch):
     from paper_2601_19911_gb300 import datagen, olap
     ns = np.unique(np.floor(np.logspace(3, 8, args.gate_points)).astype(np.int64))
     A = int(ns[-1])
-    host = olap.HostEngine(threads=args.serve_cpu_workers)
+    host = olap.HostEngine(threads=args.host_threads)
     arena = datagen.topk_keys(A, "uniform", "i64", seed=5)
     b = datagen.join_build(1 << 22, "unique", seed=5)
     table = ctx.join_build(b.keys)
@@ -604,8 +604,9 @@ def gate_leg(args, ctx, torch):
             ctx.topk_async(dev[:n], kk, olap.DESC, dok, dor)
             ctx.sync()
         t_ker = _median_ms(kern, args.gate_reps)
-        rows[olap.OP_TOPK].append((n, kk, 8.0 * n, min(kk, n), t_cpu, max(t_in - t_ker, 0.0), t_ker,
-                                   max(t_all - t_in, 0.0), t_all))
+        # transfer and post-processing as signed differences of the measured
+        # calls, so that the three terms add up to the end-to-end time
+        rows[olap.OP_TOPK].append((n, kk, 8.0 * n, min(kk, n), t_cpu, t_in - t_ker, t_ker, t_all - t_in, t_all))
         pk = p.keys[:n]
         need = int(cum[n])
         out = np.empty((need + 64, 2), dtype=np.uint32)
@@ -623,8 +624,8 @@ def gate_leg(args, ctx, torch):
             ctx.sync()
         t_ker = _median_ms(pkern, args.gate_reps)
         del dpk
-        rows[olap.OP_PROBE].append((n, 1.0 + need / n, 8.0 * n, need, t_cpu, max(t_in - t_ker, 0.0), t_ker,
-                                    max(t_all - t_in, 0.0), t_all))
+        rows[olap.OP_PROBE].append((n, 1.0 + need / n, 8.0 * n, need, t_cpu, t_in - t_ker, t_ker, t_all - t_in,
+                                    t_all))
     del dev
     table.free()
     host_split = {op: host.parallel_from(op) for op in (olap.OP_TOPK, olap.OP_PROBE)}
@@ -673,8 +674,9 @@ def gate_leg(args, ctx, torch):
     return {"metric": "gate break-even: predicted N* vs measured crossover", "unit": "relative error",
             "grid_points": len(ns),
             "calibration": "odd grid points, 1/y^2-weighted least squares, the CPU cost fitted per regime of the "
-                           "host engine (below and above the size it goes parallel at)",
-            "reps": args.gate_reps, "host_threads": args.serve_cpu_workers, **result}
+                           "host engine (below and above the size it goes parallel at); transfer and "
+                           "post-processing as signed differences of the measured calls",
+            "reps": args.gate_reps, "host_threads": args.host_threads, **result}
 
 
 def serving_leg(args, ctx, torch):
@@ -770,8 +772,7 @@ def serving_leg(args, ctx, torch):
             sctx.topk_async(dev_keys[:n], kcal, olap.DESC, dok, dor)
             sctx.sync()
         t_ker = _median_ms(kern)
-        samples[olap.OP_TOPK].append((n, kcal, 8.0 * n, min(kcal, n), t_cpu, max(t_in - t_ker, 0.0), t_ker,
-                                      max(t_all - t_in, 0.0)))
+        samples[olap.OP_TOPK].append((n, kcal, 8.0 * n, min(kcal, n), t_cpu, t_in - t_ker, t_ker, t_all - t_in))
         hit, pk, cum = arenas[1]
         pkeys = pk[:n]
         need = int(cum[n])
@@ -789,8 +790,8 @@ def serving_leg(args, ctx, torch):
             sctx.join_probe_async(tables[0], dpk[:n], dout, need + 64, cnt)
             sctx.sync()
         t_ker = _median_ms(pkern)
-        samples[olap.OP_PROBE].append((n, 1.0 + need / n, 8.0 * n, need, t_cpu, max(t_in - t_ker, 0.0), t_ker,
-                                       max(t_all - t_in, 0.0)))
+        samples[olap.OP_PROBE].append((n, 1.0 + need / n, 8.0 * n, need, t_cpu, t_in - t_ker, t_ker,
+                                       t_all - t_in))
         dev_keys[:n].copy_(torch.from_numpy(keys))
     del dev_keys
     torch.cuda.empty_cache()
@@ -1234,6 +1235,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-arena", type=int, default=100_000_000)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--host-threads", type=int, default=12,
+                    help="host engine threads of the gate and full-row legs (the engine alone on the host)")
     ap.add_argument("--serve-cpu-workers", type=int, default=4,
                     help="host engine workers (and its threads); the rest of the host's cores stage the GPU "
                          "requests' copies")

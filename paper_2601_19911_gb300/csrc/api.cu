@@ -385,8 +385,8 @@ olap_status olap_ctx_create(const olap_opts* opts, olap_ctx** out) {
     }
     ctx->topk_geom = g;
     if ((e = cudaMallocHost(reinterpret_cast<void**>(&ctx->host_status), 64)) != cudaSuccess) return bail(e);
-    if ((e = cudaMalloc(&ctx->aux, 4096)) != cudaSuccess) return bail(e);
-    if ((e = cudaMemset(ctx->aux, 0, 4096)) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&ctx->aux, OLAP_AUX_BYTES)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemset(ctx->aux, 0, OLAP_AUX_BYTES)) != cudaSuccess) return bail(e);
     *out = ctx;
     return OLAP_OK;
 }

@@ -12,6 +12,11 @@
 #include "olap.h"
 #include "topk.cuh"
 
+// The context's small device area: [0] probe count word, [256] row queue
+// counter, [1024] the probe's plan, [1536] the plan kernel's counters,
+// [2048] the self-test words, [16384] the plan kernel's packed sample.
+constexpr size_t OLAP_AUX_BYTES = 32768;
+
 struct olap_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -41,7 +46,7 @@ struct olap_ctx {
     // Small pinned words for device status read-back, and a small device
     // area for counters of blocking calls (4 KiB).
     int32_t* host_status = nullptr;
-    void* aux = nullptr;
+    void* aux = nullptr;               // small device area (OLAP_AUX_BYTES): counters, the probe's plan and sample
 
     // Control block of the last Top-K launched (diagnostics).
     void* last_topk_ctl = nullptr;

@@ -171,41 +171,78 @@ constexpr int PF_PER = 4;                      // keys per lane per step
 constexpr unsigned PF_WCAP = 256;              // rows staged per warp
 
 constexpr int PLAN_SLOTS = 2 * PF_SAMPLE;      // fingerprint set of the sample (32 KB)
+constexpr int PLAN_CTAS = PF_SAMPLE / PF_TPB;  // one sampled key per thread
+
+// The plan kernel's inputs, and its state in the context's device area.
+struct PlanArgs {
+    const int64_t* keys;
+    const uint32_t* rowids;
+    uint64_t n;
+    const uint32_t* bloom;                     // NULL: no pre-probe stage
+    uint64_t bmask;
+    int pf_mode;                               // 1 automatic, 2 forced (with a filter)
+    int skew_check;
+    int partitioned;
+    int skew_l1;
+    const int64_t* pf_keys;
+    const uint32_t* pf_rowids;
+    uint32_t* sample;                          // PF_SAMPLE packed entries
+    unsigned* counters;                        // [0] kept keys, [1] CTAs done; zero between calls
+    ProbeCtl* ctl;
+};
 
 // The probe's plan, decided on the device from a stratified sample of
 // PF_SAMPLE probe keys (n >= PF_SAMPLE; fewer rows are each taken once or
-// more).  With a Bloom filter (pf_mode 1 = automatic, 2 = forced) the
-// pre-probe runs when at most 60 % of the sample may be in the table, or
-// always when forced.  With `skew_check` the probe skips its partition passes
-// when the rows it will probe repeat: at least a fifth of the sampled keys
-// that reach the probe (those the filter keeps, when it runs) equal an
-// earlier sampled key.  Such a stream sends most probes to a few hot buckets,
-// which stay in cache, while the partition passes would cost two more passes
-// over the rows.  A key's repeats are found by a 32-bit fingerprint in a
-// shared-memory set; a fingerprint collision counts as a repeat (about
-// 2^-9 of one per sample).  Zeroes the kept-row count and tells the probe
-// kernel where its rows are: the partitioned rows (`partitioned` and not
-// direct, as launched), else the kept rows (pf_keys, pf_rowids) when the
+// more).  PLAN_CTAS CTAs load the sample, one key per thread (from one SM,
+// 4096 scattered loads wait on each other's latency: 38 us), test it
+// against the Bloom filter and store one packed word per key: a 30-bit
+// fingerprint of the key, bit 1 = kept by the filter, bit 0 = 1.  The last
+// CTA to finish decides.  With a Bloom filter (pf_mode 1 = automatic,
+// 2 = forced) the pre-probe runs when at most 60 % of the sample may be in
+// the table, or always when forced.  With `skew_check` the probe skips its
+// partition passes when the rows it will probe repeat: at least a fifth of
+// the sampled keys that reach the probe (those the filter keeps, when it
+// runs) equal an earlier sampled key.  Such a stream sends most probes to a
+// few hot buckets, which stay in cache, while the partition passes would
+// cost two more passes over the rows.  Repeats are found in a shared-memory
+// fingerprint set; a fingerprint collision counts as a repeat (about 2^-7
+// of one per sample).  The last CTA zeroes the kept-row count and tells the
+// probe kernel where its rows are: the partitioned rows (`partitioned` and
+// not direct, as launched), else the kept rows (pf_keys, pf_rowids) when the
 // pre-probe runs, else the input; a direct probe reads buckets through L1
-// when `skew_l1`.
-__global__ void __launch_bounds__(PF_TPB) join_probe_plan_kernel(const int64_t* keys, const uint32_t* rowids,
-                                                                 uint64_t n, const uint32_t* bloom, uint64_t bmask,
-                                                                 int pf_mode, int skew_check, int partitioned,
-                                                                 int skew_l1, const int64_t* pf_keys,
-                                                                 const uint32_t* pf_rowids, ProbeCtl* ctl) {
+// when `skew_l1`.  It also clears the counters for the next call.
+__global__ void __launch_bounds__(PF_TPB) join_probe_plan_kernel(PlanArgs a) {
     __shared__ uint32_t fset[PLAN_SLOTS];
-    __shared__ unsigned passes, dup_all, dup_kept;
-    for (int j = threadIdx.x; j < PLAN_SLOTS; j += PF_TPB) fset[j] = 0u;
-    if (threadIdx.x == 0) passes = dup_all = dup_kept = 0;
+    __shared__ unsigned kept_cta, dup_all, dup_kept;
+    __shared__ bool last;
+    if (threadIdx.x == 0) kept_cta = 0;
     __syncthreads();
-    unsigned m_pass = 0, m_dup = 0, m_dup_kept = 0;
-    for (int j = threadIdx.x; j < PF_SAMPLE; j += PF_TPB) {
-        const uint64_t key = static_cast<uint64_t>(keys[(static_cast<uint64_t>(j) * n) / PF_SAMPLE]);
-        const bool kept = bloom ? (key == JN_EMPTY || bloom_maybe(bloom, bmask, key)) : true;
-        m_pass += kept ? 1u : 0u;
-        if (skew_check) {
-            const uint32_t fp = static_cast<uint32_t>(fmix64(key) >> 32) | 1u;   // 0 marks a free slot
-            uint32_t slot = fp & (PLAN_SLOTS - 1);
+    {
+        const uint64_t j = static_cast<uint64_t>(blockIdx.x) * PF_TPB + threadIdx.x;     // < PF_SAMPLE
+        const uint64_t key = static_cast<uint64_t>(a.keys[(j * a.n) / PF_SAMPLE]);
+        const bool kept = a.bloom ? (key == JN_EMPTY || bloom_maybe(a.bloom, a.bmask, key)) : true;
+        const uint32_t fp = static_cast<uint32_t>(fmix64(key) >> 32) & ~3u;
+        a.sample[j] = fp | (kept ? 2u : 0u) | 1u;
+        if (kept) atomicAdd(&kept_cta, 1u);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&a.counters[0], kept_cta);
+        last = atomicAdd(&a.counters[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < PLAN_SLOTS; j += PF_TPB) fset[j] = 0u;
+    if (threadIdx.x == 0) dup_all = dup_kept = 0;
+    __syncthreads();
+    unsigned m_dup = 0, m_dup_kept = 0;
+    if (a.skew_check) {
+        for (int j = threadIdx.x; j < PF_SAMPLE; j += PF_TPB) {
+            const uint32_t w = __ldcg(a.sample + j);
+            const uint32_t fp = w & ~2u;                 // the fingerprint, with the set's non-zero bit
+            uint32_t slot = (fp >> 2) & (PLAN_SLOTS - 1);
             bool dup = false;
             for (int tries = 0; tries < PLAN_SLOTS; ++tries) {
                 const uint32_t prev = atomicCAS(&fset[slot], 0u, fp);
@@ -217,25 +254,28 @@ __global__ void __launch_bounds__(PF_TPB) join_probe_plan_kernel(const int64_t* 
                 slot = (slot + 1) & (PLAN_SLOTS - 1);
             }
             m_dup += dup ? 1u : 0u;
-            m_dup_kept += (dup && kept) ? 1u : 0u;
+            m_dup_kept += (dup && (w & 2u)) ? 1u : 0u;
         }
     }
-    atomicAdd(&passes, m_pass);
     atomicAdd(&dup_all, m_dup);
     atomicAdd(&dup_kept, m_dup_kept);
     __syncthreads();
     if (threadIdx.x == 0) {
-        const bool active = bloom && (pf_mode == 2 || passes * 10u <= static_cast<unsigned>(PF_SAMPLE) * 6u);
+        const unsigned passes = atomicAdd(&a.counters[0], 0u);
+        const bool active = a.bloom && (a.pf_mode == 2 || passes * 10u <= static_cast<unsigned>(PF_SAMPLE) * 6u);
         const unsigned reach = active ? passes : static_cast<unsigned>(PF_SAMPLE);
         const unsigned rep = active ? dup_kept : dup_all;
-        const bool direct = skew_check && reach >= 64u && rep * 5u >= reach;
+        const bool direct = a.skew_check && reach >= 64u && rep * 5u >= reach;
+        ProbeCtl* ctl = a.ctl;
         ctl->active = active ? 1 : 0;
         ctl->direct = direct ? 1 : 0;
         ctl->count = 0;
-        ctl->redirect = (!partitioned || direct) ? 1 : 0;
-        ctl->keys = active ? pf_keys : keys;
-        ctl->rowids = active ? pf_rowids : rowids;
-        ctl->l1 = (direct && skew_l1) ? 1 : 0;
+        ctl->redirect = (!a.partitioned || direct) ? 1 : 0;
+        ctl->keys = active ? a.pf_keys : a.keys;
+        ctl->rowids = active ? a.pf_rowids : a.rowids;
+        ctl->l1 = (direct && a.skew_l1) ? 1 : 0;
+        a.counters[0] = 0;
+        a.counters[1] = 0;
     }
 }
 
@@ -663,9 +703,22 @@ olap_status probe_enqueue(olap_ctx* ctx, const olap_join_table* t, const int64_t
     if (pf) {
         const int pf_mode = pre ? (ctx->opts.join_prefilter == OLAP_PREFILTER_ON ? 2 : 1) : 0;
         const int skew_l1 = ctx->opts.join_bucket_loads == OLAP_LOADS_AUTO ? 1 : 0;
-        join_probe_plan_kernel<<<1, PF_TPB, 0, s>>>(d_keys, d_rowids, n, pre ? t->bloom : nullptr, bmask, pf_mode,
-                                                    skew_check ? 1 : 0, parts > 1 ? 1 : 0, skew_l1, pf_keys,
-                                                    pf_rowids, pf);
+        PlanArgs pl;
+        pl.keys = d_keys;
+        pl.rowids = d_rowids;
+        pl.n = n;
+        pl.bloom = pre ? t->bloom : nullptr;
+        pl.bmask = bmask;
+        pl.pf_mode = pf_mode;
+        pl.skew_check = skew_check ? 1 : 0;
+        pl.partitioned = parts > 1 ? 1 : 0;
+        pl.skew_l1 = skew_l1;
+        pl.pf_keys = pf_keys;
+        pl.pf_rowids = pf_rowids;
+        pl.sample = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ctx->aux) + 16384);
+        pl.counters = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(ctx->aux) + 1536);
+        pl.ctl = pf;
+        join_probe_plan_kernel<<<PLAN_CTAS, PF_TPB, 0, s>>>(pl);
     }
     if (pre)
         join_prefilter_kernel<<<ctx->sm_count * 4, PF_TPB, 0, s>>>(d_keys, d_rowids, n, t->bloom, bmask, pf,
