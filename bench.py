@@ -243,13 +243,17 @@ def join_leg(args, ctx, torch, world):
     launches += ctx.launches() - l0
     kms = _kernel_pass(ctx, min(steps, 10), lambda: ctx.join_probe_async(table, dk, out, need, cnt))
     kern_ms = kms["join_probe_ms"]
-    # the kernels of one probe call, all bracketed by the events: the Bloom
-    # pre-probe's sample and filter (when the table has a filter), the
-    # partition count and scatter (when partitioned), and the probe
+    # the kernels of one probe call, all bracketed by the events: the plan
+    # (when the table has a filter or the probe is planned partitioned), the
+    # Bloom pre-probe (with a filter), the partition count and scatter (when
+    # planned partitioned; they return at once when the plan went direct),
+    # and the probe
     pinfo = ctx.join_probe_info()
     parts = pinfo["parts"]
-    kernels = (["olap::join_prefilter_sample_kernel", "olap::join_prefilter_kernel"] if table.has_bloom() else []) + \
-        (["olap::join_part_count_kernel", "olap::join_part_scatter_kernel"] if parts > 1 else []) + \
+    planned = ctx.join_probe_partitions(table, npr)
+    kernels = (["olap::join_probe_plan_kernel"] if table.has_bloom() or planned > 1 else []) + \
+        (["olap::join_prefilter_kernel"] if table.has_bloom() else []) + \
+        (["olap::join_part_count_kernel", "olap::join_part_scatter_kernel"] if planned > 1 else []) + \
         ["olap::join_probe_kernel"]
     peak, peak_kind = _peaks()
     m = need / npr
@@ -381,6 +385,64 @@ def join_cells_leg(args, ctx, torch, world):
             "honest_bytes_per_probe": "8 key + 32 table sector + 8 per pair",
             "timing": "CUDA events around each probe call (every kernel it launches)", "cells": cells,
             "gpu_launches": launches, "clocks": clk.summary()}
+
+
+def topk_cells_leg(args, ctx, torch, world):
+    """Every Top-K-at-scale cell: 2^log2n keys in int64 and float32, uniform,
+    already ascending and 1024 distinct values (seed 1), K in {10, 1000,
+    100000}, DESC, explicit u32 row-ids 0..n-1, device resident (the
+    full-size parity tests' inputs).  Per cell: the call's CUDA-event time
+    (mean of a few calls), keys/s, the filter kernel's own time, and both
+    fractions of the HBM roofline (key bytes read once)."""
+    from paper_2601_19911_gb300 import datagen, olap
+    n = 1 << args.log2n
+    peak, peak_kind = _peaks()
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    dr = torch.arange(n, dtype=torch.int64, device="cuda").to(torch.int32)
+    cells = []
+    launches = 0
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for kt in ("i64", "f32"):
+            for dist in ("uniform", "ascending", "dup1024"):
+                dk = torch.from_numpy(datagen.topk_keys(n, dist, kt, seed=1)).cuda()
+                w = dk.element_size()
+                for k in (10, 1000, 100_000):
+                    ok = torch.empty(k, dtype=dk.dtype, device="cuda")
+                    orow = torch.empty(k, dtype=torch.int32, device="cuda")
+                    for _ in range(2):
+                        ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
+                    ctx.sync()
+                    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                           for _ in range(args.topk_cell_steps)]
+                    _barrier(world)
+                    l0 = ctx.launches()
+                    for a, e in evs:
+                        a.record(stream)
+                        ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr)
+                        e.record(stream)
+                    ctx.sync()
+                    launches += ctx.launches() - l0
+                    ms = _max_over_ranks(float(np.mean([a.elapsed_time(e) for a, e in evs])), world)
+                    kms = _kernel_pass(ctx, args.topk_cell_steps,
+                                       lambda: ctx.topk_async(dk, k, olap.DESC, ok, orow, d_rowids=dr))
+                    info = ctx.topk_info()
+                    fms = kms.get("topk_filter_ms")
+                    cells.append({"key": kt, "dist": dist, "k": k, "ms": ms,
+                                  "gkeys_s": world * n / (ms * 1e-3) / 1e9,
+                                  "call_frac": n * w / (ms * 1e-3) / 1e9 / peak,
+                                  "filter_ms": fms,
+                                  "filter_frac": (n * w / (fms * 1e-3) / 1e9 / peak) if fms else None,
+                                  "select_ms": kms.get("topk_select_ms"), "path": info["path"],
+                                  "candidates": info["candidates"]})
+                del dk, ok, orow
+                torch.cuda.empty_cache()
+    del dr
+    torch.cuda.empty_cache()
+    return {"metric": "Top-K keys/s per cell", "unit": "Gkeys/s", "n": n, "order": "desc",
+            "rowids": "explicit", "steps": args.topk_cell_steps, "peak": peak, "peak_kind": peak_kind,
+            "bytes_per_key": "the key width, read once",
+            "timing": "CUDA events around each call on the library stream; the filter by per-kernel events",
+            "cells": cells, "gpu_launches": launches, "clocks": clk.summary()}
 
 
 def batched_leg(args, ctx, torch):
@@ -1164,6 +1226,9 @@ def run_ours(args):
     if "joincells" in workloads:
         torch.cuda.empty_cache()
         line["join_cells"] = join_cells_leg(args, ctx, torch, world)
+    if "topkcells" in workloads:
+        torch.cuda.empty_cache()
+        line["topk_cells"] = topk_cells_leg(args, ctx, torch, world)
     if "batched" in workloads:
         torch.cuda.empty_cache()
         line["batched"] = batched_leg(args, ctx, torch)
@@ -1205,10 +1270,12 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the timed kernel, if captured")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="topk,single,pair,link,join,joincells,batched,fullrow,gate,serving",
+    ap.add_argument("--workload",
+                    default="topk,single,pair,link,join,joincells,topkcells,batched,fullrow,gate,serving",
                     help="comma list: topk (the headline value), single (2^20-key query latency), link (pinned "
                          "copy bandwidth), join (probe sub-object), batched (executor), "
-                         "pair (two-column key Top-K), joincells (every join cell), fullrow (full-row vs "
+                         "pair (two-column key Top-K), joincells (every join cell), topkcells (every Top-K "
+                         "cell at 2^log2n), fullrow (full-row vs "
                          "key-only transfer), "
                          "gate (break-even validation), "
                          "serving (gated vs always-on stream)")
@@ -1218,6 +1285,7 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--join-log2p", type=int, default=28)
     ap.add_argument("--join-steps", type=int, default=50)
     ap.add_argument("--join-cell-steps", type=int, default=5, help="timed probes per cell of the joincells leg")
+    ap.add_argument("--topk-cell-steps", type=int, default=10, help="timed calls per cell of the topkcells leg")
     ap.add_argument("--join-traffic", type=float, default=None)
     ap.add_argument("--gate-points", type=int, default=16, help="N grid points of the gate leg (1e3..1e8)")
     ap.add_argument("--fullrow-payload", type=int, default=100, help="payload bytes per row of the full-row leg")

@@ -414,7 +414,9 @@ class Context:
         torch = _torch()
         cur = torch.cuda.current_stream()
         target = self.stream if stream is None else int(stream)
-        if target != cur.cuda_stream:
+        # nothing to wait for when torch's stream has finished its work (a
+        # host-side query; a wait on the GPU costs the call a few us)
+        if target != cur.cuda_stream and not cur.query():
             torch.cuda.ExternalStream(target).wait_stream(cur)
 
     # -- Top-K ---------------------------------------------------------------

@@ -96,8 +96,8 @@ def test_parser_defaults_follow_the_timing_rules():
     assert a.dist == "uniform"
     legs = a.workload.split(",")
     assert legs[0] == "topk"
-    assert set(legs) == {"topk", "single", "pair", "link", "join", "joincells", "batched", "fullrow", "gate",
-                         "serving"}
+    assert set(legs) == {"topk", "single", "pair", "link", "join", "joincells", "topkcells", "batched", "fullrow",
+                         "gate", "serving"}
     # the serving stream as configured: 100,000 requests
     assert a.serve_requests == 100_000
     # the keys at the default size exceed L2 (129 MB), so no flush is needed
