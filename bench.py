@@ -755,7 +755,15 @@ def serving_leg(args, ctx, torch):
     rng = np.random.default_rng(4)
     topk_arena = datagen.topk_keys(A, "uniform", "i64", seed=4)
     D = datagen.join_build(1 << 24, "unique", seed=4)
-    host = olap.HostEngine(threads=args.serve_cpu_workers)
+    # with --serve-pin the host engine computes on the last serve_cpu_workers
+    # host cores and the serving loop's own threads (GPU slots, staging
+    # copies) start on the others
+    cpus_all = sorted(os.sched_getaffinity(0))
+    w = args.serve_cpu_workers
+    pin = bool(args.serve_pin) and len(cpus_all) > w
+    host_cpus = cpus_all[-w:] if pin else None
+    gpu_cpus = cpus_all[:-w] if pin else None
+    host = olap.HostEngine(threads=w, cpus=host_cpus)
     sizes = np.sort(datagen.log_uniform(1 << 20, 1 << 24, datagen.stream_seed(4, 12), 8))
     tables, tbytes = [], 0
     for t in range(8):
@@ -868,6 +876,8 @@ def serving_leg(args, ctx, torch):
     budget = max(1, args.serve_budget_gb * (1 << 30) - tbytes)
     # closed-loop throughput on the first (at most 2000) requests of the trace
     cl_reqs, _cl_keep = make_requests(min(args.serve_requests, 2000), seed=4)
+    if pin:
+        os.sched_setaffinity(0, gpu_cpus)      # the threads olap.serve starts inherit it
     closed = olap.serve(cl_reqs, olap.SERVE_ALWAYS_GPU, gpu_slots=args.serve_slots, mem_budget_bytes=budget,
                         closed_loop=True, host_access=hacc)
     lam = 0.7 * closed.throughput_rps
@@ -883,6 +893,8 @@ def serving_leg(args, ctx, torch):
                      "max_ms": st.max_ms, "throughput_rps": st.throughput_rps, "wall_ms": st.wall_ms,
                      "offload_fraction": st.offload_fraction, "n_gpu": st.n_gpu, "n_host": st.n_host,
                      "failed": st.n_failed, "peak_reserved_gb": st.peak_reserved_bytes / 2**30}
+    if pin:
+        os.sched_setaffinity(0, cpus_all)
     def mdict(m):
         return {"cpu_form": ["n_log2_n", "n_k", "n_m", "max(n_log2_n, n_k)"][m.cpu_form], "a": m.a, "b": m.b,
                 "a2": m.a2, "b2": m.b2, "c_ms_per_byte": m.c,
@@ -898,6 +910,7 @@ def serving_leg(args, ctx, torch):
             "closed_loop_always_on_rps": closed.throughput_rps, "gpu_slots": args.serve_slots,
             "budget_gb": args.serve_budget_gb, "arena_keys": A, "tables": [int(x) for x in sizes],
             "host_path": "direct device access" if hdirect else "pinned staging",
+            "host_engine": {"workers": w, "cores": host_cpus or "any", "serving_threads_cores": gpu_cpus or "any"},
             "gated": out["gated"], "always_on": out["always_on"],
             "gate": {"topk": mdict(models[olap.OP_TOPK]), "probe": mdict(models[olap.OP_PROBE]),
                      "topk_n_star_k100": int(nstar), "calibration_points": len(cal_n)}}
@@ -1303,6 +1316,9 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--serve-requests", type=int, default=100_000)
     ap.add_argument("--serve-arena", type=int, default=100_000_000)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-pin", type=int, default=0,
+                    help="1: the serving host engine computes on its own cores (the last serve-cpu-workers), the "
+                         "GPU path's threads on the rest")
     ap.add_argument("--host-threads", type=int, default=12,
                     help="host engine threads of the gate and full-row legs (the engine alone on the host)")
     ap.add_argument("--serve-cpu-workers", type=int, default=4,

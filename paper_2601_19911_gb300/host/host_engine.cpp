@@ -11,6 +11,9 @@
 //   totalOrder.
 //   Probe: per table, rows sorted by key plus an open-addressing index from
 //   key to its run; threads probe chunks and the pairs are concatenated.
+#include <pthread.h>
+#include <sched.h>
+
 #include <algorithm>
 #include <condition_variable>
 #include <cstdint>
@@ -90,10 +93,24 @@ inline uint64_t mix(uint64_t h) {
 // Persistent worker threads: a request's chunks are queued to them, so a
 // parallel request costs a queue hand-off rather than thread creation.
 // Tasks never wait on other tasks, so concurrent requests cannot deadlock.
+// Pins the calling thread (or `th`) to the given host cores; an empty set
+// leaves it where it is.  Returns false if the system refuses.
+bool pin_to(pthread_t th, const std::vector<int>& cpus) {
+    if (cpus.empty()) return true;
+    cpu_set_t set;
+    CPU_ZERO(&set);
+    for (int c : cpus)
+        if (c >= 0 && c < CPU_SETSIZE) CPU_SET(c, &set);
+    return pthread_setaffinity_np(th, sizeof(set), &set) == 0;
+}
+
 class Pool {
 public:
-    explicit Pool(int n) {
-        for (int i = 0; i < n; ++i) th_.emplace_back([this] { loop(); });
+    Pool(int n, const std::vector<int>& cpus) {
+        for (int i = 0; i < n; ++i) {
+            th_.emplace_back([this] { loop(); });
+            pin_to(th_.back().native_handle(), cpus);
+        }
     }
     ~Pool() {
         {
@@ -134,10 +151,20 @@ private:
 
 struct Engine {
     int threads = 8;
+    std::vector<int> cpus;             // host cores the engine computes on (empty: anywhere)
     std::vector<Table> tables;
     Pool* pool = nullptr;
     ~Engine() { delete pool; }
 };
+
+// A request computes its first chunk on the calling thread (a serving loop's
+// host worker), so with a core set the caller is pinned to it as well, once.
+void pin_caller(const Engine* E) {
+    thread_local const Engine* pinned_for = nullptr;
+    if (E->cpus.empty() || pinned_for == E) return;
+    pin_to(pthread_self(), E->cpus);
+    pinned_for = E;
+}
 
 constexpr uint64_t TOPK_CHUNK = 65536;    // rows per thread at least: Top-K (streaming)
 constexpr uint64_t PROBE_CHUNK = 8192;    // probe (a random table access per row)
@@ -268,7 +295,19 @@ extern "C" {
 void* olap_host_engine_create(int threads) {
     Engine* e = new Engine();
     e->threads = threads > 0 ? threads : 8;
-    e->pool = new Pool(e->threads);
+    e->pool = new Pool(e->threads, e->cpus);
+    return e;
+}
+
+// The same, computing only on the given host cores (its pool threads, and
+// every thread that calls olap_host_engine_run), so that it leaves the other
+// cores to whatever else runs in the process (a GPU path's staging copies).
+void* olap_host_engine_create_on(int threads, const int* cpus, int ncpus) {
+    Engine* e = new Engine();
+    e->threads = threads > 0 ? threads : 8;
+    if (cpus)
+        for (int i = 0; i < ncpus; ++i) e->cpus.push_back(cpus[i]);
+    e->pool = new Pool(e->threads, e->cpus);
     return e;
 }
 
@@ -307,6 +346,7 @@ int olap_host_engine_add_table(void* eng, const int64_t* keys, const uint32_t* r
 
 int olap_host_engine_run(void* eng, olap_serve_request* r) {
     Engine* E = static_cast<Engine*>(eng);
+    pin_caller(E);
     if (r->op == OLAP_OP_TOPK) return run_topk(E, r);
     if (r->op == OLAP_OP_PROBE) return run_probe(E, r);
     return OLAP_E_INVALID;

@@ -756,13 +756,17 @@ class HostEngine:
     """The serving harness's CPU engine (libolap_host.so): the existing
     engine the GPU augments, used for requests the gate keeps on the host."""
 
-    def __init__(self, threads: int = 8):
+    def __init__(self, threads: int = 8, cpus=None):
+        """`threads` workers; with `cpus` (host core numbers), the engine
+        computes only on those cores, callers' threads included."""
         p = _build.HOST_LIB
         if not os.path.exists(p):
             raise ImportError(f"host engine not built: {p} is missing")
         self.lib = ctypes.CDLL(p)
         self.lib.olap_host_engine_create.restype = ctypes.c_void_p
         self.lib.olap_host_engine_create.argtypes = [ctypes.c_int]
+        self.lib.olap_host_engine_create_on.restype = ctypes.c_void_p
+        self.lib.olap_host_engine_create_on.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         self.lib.olap_host_engine_add_table.restype = ctypes.c_int
         self.lib.olap_host_engine_add_table.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                         ctypes.c_uint64]
@@ -772,7 +776,12 @@ class HostEngine:
                                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p]
         self.lib.olap_host_engine_parallel_from.restype = ctypes.c_uint64
         self.lib.olap_host_engine_parallel_from.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        self.h = self.lib.olap_host_engine_create(threads)
+        if cpus:
+            arr = (ctypes.c_int * len(cpus))(*[int(c) for c in cpus])
+            self.h = self.lib.olap_host_engine_create_on(threads, arr, len(cpus))
+        else:
+            self.h = self.lib.olap_host_engine_create(threads)
+        self.cpus = list(cpus) if cpus else None
         self._keep = []
 
     def parallel_from(self, op: int) -> int:

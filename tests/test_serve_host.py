@@ -131,3 +131,30 @@ def test_serve_rejects_bad_options(eng):
         olap.serve(arr, 7, host=eng)                                 # no such policy
     st = olap.serve((olap.olap_serve_request * 0)(), olap.SERVE_ALWAYS_HOST, host=eng)
     assert st.n_host == 0 and st.p99_ms == 0.0 and st.throughput_rps == 0.0
+
+
+def test_engine_on_a_core_set_gives_the_same_results_and_pins_its_callers():
+    """An engine created on a core set computes the same results as one that
+    is not, and pins the threads that call it to that set (run in a thread of
+    its own, so the test process keeps its cores)."""
+    import os
+    import threading
+    build.build()
+    cpus = sorted(os.sched_getaffinity(0))
+    mine = cpus[-2:] if len(cpus) > 2 else cpus
+    e = olap.HostEngine(threads=2, cpus=mine)
+    seen = {}
+
+    def work():
+        arr, keep = _requests(e, 24, seed=31, rate_per_ms=1.0, closed=True)
+        for r in arr:
+            r.status = e.run(r)
+        _check_results(arr, keep)
+        seen["affinity"] = sorted(os.sched_getaffinity(0))
+
+    t = threading.Thread(target=work)
+    t.start()
+    t.join()
+    e.close()
+    assert seen["affinity"] == mine
+    assert sorted(os.sched_getaffinity(0)) == cpus          # the test's own thread is untouched
