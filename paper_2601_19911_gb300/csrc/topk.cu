@@ -645,9 +645,14 @@ __device__ void hist_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_t
 // Split: entries below the prefix are selected (appended to out), entries
 // equal to it go to the small buffer, or straight to out when all of them
 // (or any `krem` identical ones) are taken.
+// With FOLD, the AND / OR of the entries it writes to out (those below the
+// prefix, and with take_all the equal ones it keeps) is merged into
+// ctl->fin for the larger-K finish, which then needs no pass of its own.
+template <bool FOLD>
 __device__ void split_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_t p0, uint64_t p1,
                            int L, int kb, bool take_all, uint64_t krem) {
     TopkCtl* ctl = a.ctl;
+    uint64_t acc[4] = {~0ull, ~0ull, 0ull, 0ull};
     const uint64_t stride = static_cast<uint64_t>(TK_TPB) * gridDim.x;
     const unsigned lane = threadIdx.x & 31u;
     const uint64_t eq_base = a.k - krem;
@@ -656,9 +661,9 @@ __device__ void split_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_
         const uint64_t i = wb + lane;
         int c = 1;
         Elem e{0, 0};
+        uint64_t w0 = 0, w1 = 0;
         if (i < src_n) {
             e = load_src(a, cand, i);
-            uint64_t w0, w1;
             comp_words(e.r, e.rid, kb, w0, w1);
             c = prefix_cmp(w0, w1, p0, p1, L);
         }
@@ -672,6 +677,7 @@ __device__ void split_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_
                 const uint64_t pos = base + __popc(lt & ((1u << lane) - 1u));
                 a.out_r0[pos] = e.r;
                 a.out_rid0[pos] = e.rid;
+                if (FOLD) and_or(w0, w1, acc);
             }
         }
         if (eq) {
@@ -685,6 +691,7 @@ __device__ void split_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_
                     if (pos < krem) {
                         a.out_r0[eq_base + pos] = e.r;
                         a.out_rid0[eq_base + pos] = e.rid;
+                        if (FOLD) and_or(w0, w1, acc);
                     }
                 } else if (pos < TK_SMALL) {
                     a.small_r[pos] = e.r;
@@ -693,6 +700,7 @@ __device__ void split_pass(const TopkArgs& a, bool cand, uint64_t src_n, uint64_
             }
         }
     }
+    if (FOLD) and_or_merge<TK_TPB>(acc, ctl->fin);
 }
 
 // Merge-path split: how many of the first `diag` outputs of the merge of
@@ -881,7 +889,12 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
 
     // Phase 3: split around the prefix.
     const bool take_all = (krem == bcnt) || (L >= TB);
-    split_pass(a, cand, src_n, p0, p1, L, kb, take_all, krem);
+    // the larger-K finish wants the AND / OR of the entries split writes out
+    const bool large = (take_all ? a.k : a.k - krem) + (take_all ? 0 : bcnt) > TK_RANK_MAX;
+    if (large)
+        split_pass<true>(a, cand, src_n, p0, p1, L, kb, take_all, krem);
+    else
+        split_pass<false>(a, cand, src_n, p0, p1, L, kb, take_all, krem);
     if (!grid_sync(a.bar, &ctl->err)) return report(a);
     if (stamp) ctl->ts[5] = gtimer();
 
@@ -969,22 +982,9 @@ __global__ void __launch_bounds__(TK_TPB, 2) topk_select_kernel(TopkArgs a) {
             __syncthreads();
         }
         // (b) partition histogram of the below entries, on the digit that
-        // starts at the first bit where they differ (AND / OR over the grid),
-        // so that clustered keys and ties on the key spread over the buckets.
-        {
-            uint64_t acc[4] = {~0ull, ~0ull, 0ull, 0ull};
-            const uint64_t gs = static_cast<uint64_t>(TK_TPB) * gridDim.x;
-            for (uint64_t wb = static_cast<uint64_t>(blockIdx.x) * TK_TPB + (threadIdx.x & ~31u); wb < nb; wb += gs) {
-                const uint64_t i = wb + lane;
-                if (i < nb) {
-                    uint64_t w0, w1;
-                    comp_words(__ldcg(a.out_r0 + i), __ldcg(a.out_rid0 + i), kb, w0, w1);
-                    and_or(w0, w1, acc);
-                }
-            }
-            and_or_merge<TK_TPB>(acc, ctl->fin);
-        }
-        if (!grid_sync(a.bar, &ctl->err)) return report(a);
+        // starts at the first bit where they differ (their AND / OR, folded
+        // by the split pass that wrote them), so that clustered keys and ties
+        // on the key spread over the buckets.
         const int L0 = min(first_diff(ctl->fin, TB), TB - 1);
         const int dp = min(a.digit, TB - L0);
         unsigned* ph = a.ghist + (pass % 3) * TK_BINS;          // clean (zeroed by the last pass or prepare)
