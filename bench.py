@@ -1163,6 +1163,10 @@ def run_ours(args):
     e2e_s = _max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     launches += ctx.launches() - l0
     e2e_value = replicas.whole_job_rate(n, world, e2e_s) / 1e9
+    e2e_info = ctx.topk_info()
+    # on the sampled path pinned row-ids stay in host memory: the kernels
+    # read the candidates' row-ids there, and only the keys are copied
+    rid_in_place = hr is not None and e2e_info["rowids_in_place"]
     e2e_keys_only = None
     if hr is not None:
         # the same call with implicit row-ids: only the keys cross the link
@@ -1217,9 +1221,13 @@ def run_ours(args):
                                f"{args.steps} further steps after the timed region",
                      "filter": args.filter, "last_launch": phases,
                      "geometry": {"tile": args.tile, "stages": args.stages, "ctas_per_sm": args.ctas_per_sm}},
-        "e2e": {"value": e2e_value, "unit": "Gkeys/s", "h2d_bytes_per_step": n * w + (4 * n if hr is not None else 0),
+        "e2e": {"value": e2e_value, "unit": "Gkeys/s",
+                "h2d_bytes_per_step": n * w + (4 * n if hr is not None and not rid_in_place else 0),
+                "rowid_bytes_read_in_place": 4 * int(e2e_info["candidates"]) if rid_in_place else 0,
                 "d2h_bytes_per_step": k * (w + 4) + 4, "ms_per_step": e2e_s * 1e3,
-                "rowids": "explicit (keys and row-ids cross the link)" if hr is not None else "implicit (keys only)",
+                "rowids": ("explicit, in pinned host memory: the keys are copied, the kernels read the "
+                           "candidates' row-ids in place" if rid_in_place else
+                           "explicit (keys and row-ids cross the link)") if hr is not None else "implicit (keys only)",
                 "keys_only": e2e_keys_only},
         # the library's own count over the timed regions of `value` and `e2e`
         "gpu_launches": launches,

@@ -190,6 +190,10 @@ olap_status olap_selftest_wait(olap_ctx* ctx, uint64_t limit_cycles, int32_t* ou
  * out_where   memory kind of both outputs.
  * out_count   (host) receives min(k, n).
  * Limits: n < 2^32.  k = 0 or n = 0 => OLAP_OK with count 0.
+ * With row-ids in page-locked host memory and the sampled path (n > 2^21,
+ * k <= n / 256), the row-ids are not copied: the kernels read the
+ * candidates' row-ids in place over the host link (olap_topk_info_last
+ * reports it); the keys are copied as usual.
  * The result is bit-exact: it equals a stable sort by (key, row-id) cut at k.
  * ------------------------------------------------------------------------ */
 olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const uint32_t* rowids,
@@ -228,12 +232,17 @@ olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type typ
  * or large k), 1 = sampled threshold + one streaming pass + refine over the
  * candidates, 2 = sample misjudged, refine over the input.  phase_ns:
  * sample, filter, refine, split, finish/sort, total, and within finish the
- * small-bucket sort and the survivor sort (device %globaltimer). */
+ * small-bucket sort and the survivor sort (device %globaltimer).
+ * rowids_in_place: 1 when the call (a blocking olap_topk on the sampled
+ * path with row-ids in page-locked host memory) read the candidates'
+ * row-ids in host memory instead of copying all n to the device. */
 typedef struct {
     int path;
     int refine_passes;
     uint64_t candidates;
     uint64_t phase_ns[8];
+    int rowids_in_place;
+    int reserved;
 } olap_topk_info;
 olap_status olap_topk_info_last(olap_ctx* ctx, olap_topk_info* out);
 

@@ -288,6 +288,7 @@ static olap_status topk_enqueue(olap_ctx* ctx, const void* d_keys, olap_key_type
     a.filter = ctx->opts.topk_filter == OLAP_FILTER_BULK ? TK_FILTER_BULK : TK_FILTER_REGS;
     a.digit = ctx->opts.topk_digit_bits ? ctx->opts.topk_digit_bits : TK_DIG;
     ctx->last_topk_ctl = a.ctl;
+    ctx->last_rowids_in_place = false;      // olap_topk sets it after this when it applies
     ctx->topk_timed = ctx->time_kernels;
     ctx->topk_filtered = plan.use_sample;
     cudaError_t e = topk_launch(a, ctx->topk_geom, stream, ctx->time_kernels ? ctx->kev : nullptr);
@@ -526,22 +527,38 @@ olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
     const size_t w = key_bytes(type);
 
-    // Key-only input: keys (and explicit row-ids) to the device.
+    // Key-only input: keys (and explicit row-ids) to the device.  On the
+    // sampled path only the candidates' row-ids are ever read (as the filter
+    // stages them), so row-ids in page-locked host memory stay there: the
+    // kernels read those few in place over the host link (NVLink-C2C), and
+    // the copy carries the keys alone.
     const void* dk = keys;
     const uint32_t* dr = rowids;
+    bool rowids_in_place = false;
+    if (rowids && in_where == OLAP_MEM_HOST_PINNED && topk_plan(n, kk).use_sample) {
+        void* mapped = nullptr;
+        if (cudaHostGetDevicePointer(&mapped, const_cast<uint32_t*>(rowids), 0) == cudaSuccess && mapped) {
+            dr = static_cast<const uint32_t*>(mapped);
+            rowids_in_place = true;
+        } else {
+            cudaGetLastError();
+        }
+    }
     if (in_where != OLAP_MEM_DEVICE) {
         const size_t kbytes = (n * w + 255) & ~static_cast<size_t>(255);
-        st = ensure_dev_in(ctx, kbytes + (rowids ? n * 4 : 0));
+        const bool copy_rowids = rowids && !rowids_in_place;
+        st = ensure_dev_in(ctx, kbytes + (copy_rowids ? n * 4 : 0));
         if (st != OLAP_OK) return st;
         st = copy_h2d(ctx, ctx->dev_in, keys, n * w, in_where);
         if (st != OLAP_OK) return st;
         dk = ctx->dev_in;
-        if (rowids) {
+        if (copy_rowids) {
             dr = reinterpret_cast<const uint32_t*>(static_cast<unsigned char*>(ctx->dev_in) + kbytes);
             st = copy_h2d(ctx, const_cast<uint32_t*>(dr), rowids, n * 4, in_where);
             if (st != OLAP_OK) return st;
         }
     }
+
     void* dok = out_keys;
     uint32_t* dor = out_rowids;
     const size_t okb = (kk * w + 255) & ~static_cast<size_t>(255);
@@ -554,6 +571,7 @@ olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const
     TopkCtl* ctl = nullptr;
     st = topk_enqueue(ctx, dk, type, dr, n, kk, order, dok, dor, nullptr, ctx->stream, &ctl);
     if (st != OLAP_OK) return st;
+    ctx->last_rowids_in_place = rowids_in_place;
     e = cudaMemcpyAsync(ctx->host_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
     if (out_where != OLAP_MEM_DEVICE) {
@@ -713,6 +731,7 @@ extern "C" olap_status olap_topk_info_last(olap_ctx* ctx, olap_topk_info* out) {
     out->path = c.path;
     out->refine_passes = c.passes;
     out->candidates = c.cand_count;
+    out->rowids_in_place = ctx->last_rowids_in_place ? 1 : 0;
     auto d = [&](int a, int b) { return c.ts[b] > c.ts[a] ? c.ts[b] - c.ts[a] : 0ull; };
     out->phase_ns[0] = d(0, 1);
     out->phase_ns[1] = d(1, 2);

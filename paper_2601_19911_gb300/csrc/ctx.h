@@ -78,6 +78,7 @@ struct olap_ctx {
     int last_probe_parts = 0;
     uint64_t last_probe_n = 0;
     const void* last_probe_pf = nullptr;
+    bool last_rowids_in_place = false;   // the last blocking Top-K read its row-ids in host memory
 
     // Device memory held by live join tables built through this context.
     uint64_t table_bytes = 0;

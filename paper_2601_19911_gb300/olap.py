@@ -151,6 +151,8 @@ class olap_topk_info(ctypes.Structure):
         ("refine_passes", ctypes.c_int),
         ("candidates", ctypes.c_uint64),
         ("phase_ns", ctypes.c_uint64 * 8),
+        ("rowids_in_place", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -561,6 +563,7 @@ class Context:
         self.check(self.lib.olap_topk_info_last(self.h, ctypes.byref(info)))
         names = ["sample", "filter", "refine", "split", "finish", "total", "finish_small", "finish_sort"]
         return {"path": info.path, "refine_passes": info.refine_passes, "candidates": info.candidates,
+                "rowids_in_place": bool(info.rowids_in_place),
                 "phase_us": {nm: info.phase_ns[i] / 1e3 for i, nm in enumerate(names)}}
 
     def autotune(self, topk_n: int = 0, topk_k: int = 100, key_type: int = KEY_I64, join_build_n: int = 0,

@@ -80,3 +80,43 @@ def test_bounded_wait_reports_timeout_and_context_survives():
             c.selftest_wait(0)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("kt", ["i64", "f32"])
+def test_pinned_rowids_are_read_in_place(kt):
+    """On the sampled path a blocking Top-K with row-ids in page-locked host
+    memory reads only the candidates' row-ids, in place: reversed row-ids,
+    1024 distinct keys (so the row-id tie-break decides), both orders and two
+    k, against the oracle; all-equal keys send the select back to the input
+    (every row-id then read in host memory); pageable and device row-ids are
+    still copied."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = olap.Context(0)
+    try:
+        n = 3_000_007
+        keys = datagen.topk_keys(n, "dup1024", kt, seed=81)
+        rid = np.arange(n - 1, -1, -1, dtype=np.int64).astype(np.uint32)
+        hk = torch.from_numpy(keys).pin_memory()
+        hr = torch.from_numpy(rid.view(np.int32)).pin_memory()
+        for k, order in ((1000, olap.DESC), (1000, olap.ASC), (10_000, olap.DESC)):
+            gk, gr = c.topk(hk, k, order, rowids=hr)
+            assert c.topk_info()["rowids_in_place"] and c.topk_info()["path"] == 1
+            wk, wr = oracle.topk(keys, k, order, rid)
+            np.testing.assert_array_equal(np.asarray(gr), wr)
+            np.testing.assert_array_equal(np.asarray(gk).view(np.uint8), wk.view(np.uint8))
+        same = np.full(n, 7, dtype=keys.dtype)
+        hs = torch.from_numpy(same).pin_memory()
+        gk, gr = c.topk(hs, 1000, olap.DESC, rowids=hr)
+        assert c.topk_info()["rowids_in_place"] and c.topk_info()["path"] == 2
+        np.testing.assert_array_equal(np.asarray(gr), oracle.topk(same, 1000, olap.DESC, rid)[1])
+        gk, gr = c.topk(keys, 1000, olap.DESC, rowids=rid)                  # pageable: copied
+        assert not c.topk_info()["rowids_in_place"]
+        np.testing.assert_array_equal(np.asarray(gr), oracle.topk(keys, 1000, olap.DESC, rid)[1])
+        dk = torch.from_numpy(keys).cuda()
+        dr = torch.from_numpy(rid.view(np.int32)).cuda()
+        gk, gr = c.topk(dk, 1000, olap.DESC, rowids=dr)                      # device: used as they are
+        assert not c.topk_info()["rowids_in_place"]
+        np.testing.assert_array_equal(np.asarray(gr), oracle.topk(keys, 1000, olap.DESC, rid)[1])
+    finally:
+        c.close()
