@@ -123,3 +123,36 @@ def test_exact_knife_edge_is_not_offloaded():
 def test_rejects_bad_input():
     with pytest.raises(olap.OlapError):
         olap.gate_calibrate(gate.TOPK, [1.0], [1.0], [1.0], [1.0], [1.0], [1.0], [1.0], [1.0])
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("weighting", [gate.ORDINARY, gate.RELATIVE])
+def test_signed_component_samples_match_oracle(seed, weighting):
+    """Transfer and post-processing measured as differences of calls can come
+    out zero or slightly negative near the break-even; both sides then weigh
+    such a sample, under 1/y^2 weights, like the smallest positive one."""
+    rng = np.random.default_rng(100 + seed)
+    n, km, tx, out, t_cpu, t_tx, t_ker, t_post = _noisy_samples(rng, gate.TOPK, gate.CPU_NLOGN)
+    t_post = t_post - 0.006                      # about half the samples at or below zero
+    t_tx = t_tx.copy()
+    t_tx[::7] = -0.001
+    t_post[3] = 0.0
+    assert (t_post <= 0).any() and (t_post > 0).any()
+    for margin in (0.0, 5.0):
+        want = gate.calibrate(gate.TOPK, n, km, tx, out, t_cpu, t_tx, t_ker, t_post, margin_ms=margin,
+                              weighting=weighting, cpu_split_n=131072.0)
+        got = olap.gate_calibrate(gate.TOPK, n, km, tx, out, t_cpu, t_tx, t_ker, t_post, margin_ms=margin,
+                                  weighting=weighting, cpu_split_n=131072.0)
+        for nm in ("a", "b", "c", "d", "e", "f", "g", "h", "a_hi", "b_hi"):
+            assert math.isclose(getattr(got, nm), getattr(want, nm), rel_tol=1e-9, abs_tol=1e-15), nm
+        d = olap.gate_estimate(got, gate.TOPK, 1 << 20, 100.0, 8.0 * (1 << 20), 100.0, 8.0)
+        assert abs(int(d.n_star) - gate.n_star(want, 100.0, 8.0, 0.0, 100.0)) <= 1
+
+
+def test_relative_weights_of_non_positive_samples():
+    """The weighting rule itself: 1 / y^2, with a sample at or below zero
+    weighted like the smallest positive one (and all ones when none is)."""
+    w = gate.weights([2.0, -1.0, 0.0, 4.0], gate.RELATIVE)
+    np.testing.assert_allclose(w, [0.25, 0.25, 0.25, 1.0 / 16.0])
+    np.testing.assert_allclose(gate.weights([-1.0, 0.0], gate.RELATIVE), [1.0, 1.0])
+    np.testing.assert_allclose(gate.weights([-1.0, 5.0], gate.ORDINARY), [1.0, 1.0])
