@@ -233,8 +233,8 @@ olap_status olap_topk_async(olap_ctx* ctx, const void* d_keys, olap_key_type typ
  * candidates, 2 = sample misjudged, refine over the input.  phase_ns:
  * sample, filter, refine, split, finish/sort, total, and within finish the
  * small-bucket sort and the survivor sort (device %globaltimer).
- * rowids_in_place: 1 when the call (a blocking olap_topk on the sampled
- * path with row-ids in page-locked host memory) read the candidates'
+ * rowids_in_place: 1 when the call (a blocking olap_topk or olap_topk_pair
+ * on the sampled path with row-ids in page-locked host memory) read the candidates'
  * row-ids in host memory instead of copying all n to the device. */
 typedef struct {
     int path;

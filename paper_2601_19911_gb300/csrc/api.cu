@@ -509,6 +509,22 @@ olap_status olap_topk_rows(olap_ctx* ctx, const void* rows, olap_mem in_where, u
     return OLAP_OK;
 }
 
+// On the sampled path only the candidates' row-ids are ever read (as the
+// filter stages them), so row-ids in page-locked host memory can stay there:
+// the kernels read those few in place over the host link (NVLink-C2C), and
+// the copy carries the keys alone.  True, with *dr set to the row-ids'
+// device-accessible address, when that applies.
+static bool rowids_in_host(const uint32_t* rowids, olap_mem where, uint64_t n, uint64_t kk, const uint32_t** dr) {
+    if (!rowids || where != OLAP_MEM_HOST_PINNED || !topk_plan(n, kk).use_sample) return false;
+    void* mapped = nullptr;
+    if (cudaHostGetDevicePointer(&mapped, const_cast<uint32_t*>(rowids), 0) != cudaSuccess || !mapped) {
+        cudaGetLastError();
+        return false;
+    }
+    *dr = static_cast<const uint32_t*>(mapped);
+    return true;
+}
+
 olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const uint32_t* rowids,
                       olap_mem in_where, uint64_t n, uint64_t k, olap_order order, void* out_keys,
                       uint32_t* out_rowids, olap_mem out_where, uint64_t* out_count) {
@@ -527,23 +543,11 @@ olap_status olap_topk(olap_ctx* ctx, const void* keys, olap_key_type type, const
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
     const size_t w = key_bytes(type);
 
-    // Key-only input: keys (and explicit row-ids) to the device.  On the
-    // sampled path only the candidates' row-ids are ever read (as the filter
-    // stages them), so row-ids in page-locked host memory stay there: the
-    // kernels read those few in place over the host link (NVLink-C2C), and
-    // the copy carries the keys alone.
+    // Key-only input: keys (and explicit row-ids) to the device; pinned
+    // row-ids on the sampled path stay where they are (rowids_in_host).
     const void* dk = keys;
     const uint32_t* dr = rowids;
-    bool rowids_in_place = false;
-    if (rowids && in_where == OLAP_MEM_HOST_PINNED && topk_plan(n, kk).use_sample) {
-        void* mapped = nullptr;
-        if (cudaHostGetDevicePointer(&mapped, const_cast<uint32_t*>(rowids), 0) == cudaSuccess && mapped) {
-            dr = static_cast<const uint32_t*>(mapped);
-            rowids_in_place = true;
-        } else {
-            cudaGetLastError();
-        }
-    }
+    const bool rowids_in_place = rowids_in_host(rowids, in_where, n, kk, &dr);
     if (in_where != OLAP_MEM_DEVICE) {
         const size_t kbytes = (n * w + 255) & ~static_cast<size_t>(255);
         const bool copy_rowids = rowids && !rowids_in_place;
@@ -611,19 +615,22 @@ olap_status olap_topk_pair(olap_ctx* ctx, const void* keys0, olap_key_type type0
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "set device");
 
-    // Key-only input: both key columns (and explicit row-ids) to the device.
+    // Key-only input: both key columns (and explicit row-ids) to the device;
+    // pinned row-ids on the sampled path stay where they are.
     const void* d0 = keys0;
     const void* d1 = keys1;
     const uint32_t* dr = rowids;
+    const bool rowids_in_place = rowids_in_host(rowids, in_where, n, kk, &dr);
     const size_t cb = (n * 4 + 255) & ~static_cast<size_t>(255);
     if (in_where != OLAP_MEM_DEVICE) {
-        if ((st = ensure_dev_in(ctx, 2 * cb + (rowids ? n * 4 : 0))) != OLAP_OK) return st;
+        const bool copy_rowids = rowids && !rowids_in_place;
+        if ((st = ensure_dev_in(ctx, 2 * cb + (copy_rowids ? n * 4 : 0))) != OLAP_OK) return st;
         unsigned char* m = static_cast<unsigned char*>(ctx->dev_in);
         if ((st = copy_h2d(ctx, m, keys0, n * 4, in_where)) != OLAP_OK) return st;
         if ((st = copy_h2d(ctx, m + cb, keys1, n * 4, in_where)) != OLAP_OK) return st;
         d0 = m;
         d1 = m + cb;
-        if (rowids) {
+        if (copy_rowids) {
             dr = reinterpret_cast<const uint32_t*>(m + 2 * cb);
             if ((st = copy_h2d(ctx, const_cast<uint32_t*>(dr), rowids, n * 4, in_where)) != OLAP_OK) return st;
         }
@@ -644,6 +651,7 @@ olap_status olap_topk_pair(olap_ctx* ctx, const void* keys0, olap_key_type type0
     if ((st = topk_enqueue(ctx, d0, type0, dr, n, kk, order0, do0, dor, nullptr, ctx->stream, &ctl, &ps)) !=
         OLAP_OK)
         return st;
+    ctx->last_rowids_in_place = rowids_in_place;
     e = cudaMemcpyAsync(ctx->host_status, &ctl->err, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status read-back");
     if (out_where != OLAP_MEM_DEVICE) {

@@ -95,6 +95,20 @@ def test_host_memory(ctx, where):
     c0, c1 = _cols(3_000_000, "f32", "i32", seed=11)
     rowids = datagen.identity_rowids(c0.shape[0])[::-1].copy()
     _check(ctx, c0, olap.DESC, c1, olap.DESC, 1000, rowids, where=where)
+    # pinned row-ids on the sampled path are read in place, pageable ones copied
+    assert ctx.topk_info()["rowids_in_place"] == (where == "pinned")
+
+
+def test_pinned_rowids_in_place_on_the_fallback_path(ctx):
+    # all rows tie on both columns: the selection runs on the input and
+    # reads every row-id in pinned host memory
+    n = 3_000_000
+    c0 = np.full(n, 7, dtype=np.int32)
+    c1 = np.full(n, -3, dtype=np.int32)
+    rowids = datagen.identity_rowids(n)[::-1].copy()
+    _check(ctx, c0, olap.DESC, c1, olap.ASC, 100, rowids, where="pinned")
+    info = ctx.topk_info()
+    assert info["rowids_in_place"] and info["path"] == 2
 
 
 def test_unequal_alignment_uses_row_loads(ctx):
